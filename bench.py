@@ -1,0 +1,394 @@
+#!/usr/bin/env python
+"""Benchmark of the projection-method hot path on GB300: PCG DOF*iterations/s and time to the homogenized
+coefficient a*.
+
+Default workload (the configuration the metric is quoted on): d = 2 lifted to n = 4,
+P = [[1, sqrt2, 0, 0], [0, 0, 1, sqrt3]], A = (5 + sum_j cos theta_j) I, 16^4 = 65,536 Fourier modes per field,
+both correctors (e_1, e_2) by Jacobi-PCG to a relative residual of 1e-10 in FP64, then the 2 x 2 a*.
+One step = corrector right-hand sides -> PCG solves -> a* reduction -> a* on the host, with the coefficient
+already on the device (time-to-a*). Inputs are synthetic (seeded); L2 is flushed before every timed step.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload cfg0..cfg4]
+For N > 1 launch with torch.distributed.run; every rank solves its own replica (independent units, no
+collective on the data path) and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import os
+
+# The CPU baseline is the single-threaded oracle; pin numpy's helper libraries to one thread so the reported
+# core count is what it used.
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse
+import json
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import qp_workloads as W  # noqa: E402
+
+WORKLOADS = {
+    "cfg0": ("d=1 n=2 P=(1,sqrt2) a=3+cos th1+cos th2, 32^2 modes, 1 corrector, Jacobi-PCG to 1e-12", "fp64"),
+    "cfg1": ("d=2 n=4 P=[[1,sqrt2,0,0],[0,0,1,sqrt3]] A=(5+sum cos th_j)I, 16^4 modes, 2 correctors, "
+             "Jacobi-PCG to 1e-10", "fp64"),
+    "cfg2": ("d=2 n=4 full SPD 2x2 grid coefficient (81-tap field, eigenvalues clamped to [0.5,5]), 32^4 modes, "
+             "2 correctors, FP32 PCG in FP64 refinement to 1e-10", "refine"),
+    "cfg4": ("d=3 n=6 diag A, a_i=4+sum_j 0.5cos(th_j+phi_ij), 16^6 modes, 3 correctors, FP32 PCG in FP64 "
+             "refinement to 1e-10", "refine"),
+}
+FP64_PEAK_TFLOPS = 1.25      # nominal GB300 FP64 rate (CUDA cores); the FMA-loop probe measured 1.196
+
+
+def instance(name, N=None):
+    return getattr(W, name)() if N is None else getattr(W, name)(N=N)
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "_fallback": True}
+
+
+# ---------------------------------------------------------------------------------------------- roofline model
+
+def apply_flops_per_dof(kind, d, ntaps, real, nrhs):
+    """Algorithmic flops of one stiffness apply per mode, taps backend: per tap the weight
+    lambda(k)^T C_t lambda(k -N m_t) (scalar: 2d, diag: 3d, sym: 3d^2; doubled for complex taps) and, per
+    right-hand side, the complex multiply-accumulate with h (4 flops real weight, 8 complex)."""
+    w = {"scalar": 2 * d, "diag": 3 * d, "sym": 3 * d * d}[kind] * (1 if real else 2)
+    return ntaps * (w + nrhs * (4 if real else 8))
+
+
+# ---------------------------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi sampled every 100 ms while the timed region runs."""
+    Q = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id=None):
+        self.bus_id = (bus_id or "").lower()
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                                          "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            if self.bus_id and self.bus_id[-12:] not in parts[1].lower():
+                continue
+            rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[6 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------------------------- our arm
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_2404_06841_gb300 as qp
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    name = args.workload
+    desc, default_mode = WORKLOADS[name]
+    mode_name = args.mode or default_mode
+    mode = qp.QP_MODE_FP64 if mode_name == "fp64" else qp.QP_MODE_FP32_REFINE
+    inst = instance(name, args.N)
+    tol = inst.tol
+    plan = qp.plan_from_instance(inst, exec_mode=qp.QP_EXEC_DIRECT if args.exec == "direct" else qp.QP_EXEC_GRAPH)
+    pinfo = qp.qp_plan_query(plan)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2 (129 MiB)
+
+    def step():
+        return qp.qp_homogenized(plan, tol=tol, mode=mode, maxit=2000)
+
+    for _ in range(max(args.warmup, 3)):
+        A, infos = step()
+    dof_iters_step = sum(inst.D * (i["iterations"] + i["outer_iterations"]) for i in infos)
+
+    sampler = ClockSampler(None)
+    sampler.start()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    launches0 = qp.qp_launch_count()
+    wall0 = time.perf_counter()
+    total_dof_iters = 0
+    max_rel = 0.0
+    for k in range(args.steps):
+        flush.zero_()
+        starts[k].record(stream)
+        A, infos = step()
+        ends[k].record(stream)
+        total_dof_iters += sum(inst.D * (i["iterations"] + i["outer_iterations"]) for i in infos)
+        max_rel = max(max_rel, max(i["rel_residual"] for i in infos))
+    torch.cuda.synchronize()
+    wall1 = time.perf_counter()
+    launches = qp.qp_launch_count() - launches0
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    t_sec = ms / 1e3
+    if world > 1:
+        t = torch.tensor([t_sec], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_sec = float(t.item())
+    value = world * total_dof_iters / t_sec
+
+    # ---- roofline of the dominant kernel: the stiffness apply, timed alone with CUDA events on this stream
+    nrhs = inst.d
+    prec = qp.QP_FP64 if mode_name == "fp64" else qp.QP_FP32
+    dt = torch.complex128 if prec == qp.QP_FP64 else torch.complex64
+    h = torch.randn((nrhs, inst.D), dtype=dt, device=dev)
+    w = torch.empty_like(h)
+    for _ in range(5):
+        qp.qp_apply_stiffness(plan, h, w, prec)
+    reps = 50
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        qp.qp_apply_stiffness(plan, h, w, prec)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    apply_ms = e0.elapsed_time(e1) / reps
+    c = inst.coeff
+    real = bool(np.all(np.asarray(c.taps_val).imag == 0)) if c.taps_k is not None else False
+    pk = peaks()
+    if prec == qp.QP_FP64 and c.taps_k is not None:
+        flops = apply_flops_per_dof(c.kind, inst.d, pinfo["ntaps"], real, nrhs) * inst.D
+        achieved = flops / (apply_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": None,
+                "kernel": "taps_apply_kernel<double> (FP64 CUDA cores)", "apply_us": round(apply_ms * 1e3, 2),
+                "flops_per_launch": flops, "peak_source": "nominal FP64 1.25 TFLOP/s (FMA probe: 1.196)"}
+    else:
+        bytes_ = 2 * nrhs * inst.D * (16 if prec == qp.QP_FP64 else 8)
+        achieved = bytes_ / (apply_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": round(achieved / pk["hbm_gbs"], 4), "traffic": None,
+                "kernel": "taps_apply_kernel<float>" if c.taps_k is not None else "fft passes",
+                "apply_us": round(apply_ms * 1e3, 2), "bytes_per_launch": bytes_,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs" + (" (fallback)" if pk.get("_fallback") else "")}
+
+    # ---- end to end through the public API with host inputs: plan from host taps -> a* on the host
+    e2e = None
+    if c.taps_k is not None:
+        kk = np.ascontiguousarray(c.taps_k, dtype=np.int32)
+        vv = np.ascontiguousarray(np.asarray(c.taps_val, dtype=np.complex128))
+        h2d = kk.nbytes + vv.nbytes + inst.P.nbytes + 4 * inst.n
+        d2h = 16 * inst.d * inst.d
+        e2e_steps = max(3, min(args.steps, 20))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            p2 = qp.qp_plan_create(inst.d, inst.n, inst.P, inst.N, W.Coefficient(c.kind, kk, vv))
+            qp.qp_homogenized(p2, tol=tol, mode=mode, maxit=2000)
+            qp.qp_plan_destroy(p2)
+        torch.cuda.synchronize()
+        e2e_t = (time.perf_counter() - t0) / e2e_steps
+        e2e = {"value": world * dof_iters_step / e2e_t, "unit": "DOF*iter/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": round(e2e_t * 1e3, 3),
+               "what": "qp_plan_create(host taps) + qp_homogenized + qp_plan_destroy per step"}
+
+    # ---- the other precision mode on the same workload (time-to-a*), for the FP64-vs-refinement comparison
+    variants = {}
+    other = "refine" if mode_name == "fp64" else "fp64"
+    if not args.no_variants:
+        om = qp.QP_MODE_FP32_REFINE if other == "refine" else qp.QP_MODE_FP64
+        for _ in range(3):
+            qp.qp_homogenized(plan, tol=tol, mode=om, maxit=2000)
+        ts = []
+        for _ in range(max(5, min(args.steps, 20))):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            A2, inf2 = qp.qp_homogenized(plan, tol=tol, mode=om, maxit=2000)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        di = sum(inst.D * (i["iterations"] + i["outer_iterations"]) for i in inf2)
+        variants[other] = {"time_to_astar_ms": round(statistics.median(ts), 4),
+                           "dof_iter_per_s": di / (statistics.median(ts) / 1e3),
+                           "iterations": [(i["iterations"], i["outer_iterations"]) for i in inf2],
+                           "max_abs_astar_diff_vs_main": float(np.abs(A2 - A).max())}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(name, max_seconds=args.cpu_seconds)
+
+    out = {
+        "metric": "PCG DOF*iter/s (time-to-a* at 1e-10)",
+        "value": value,
+        "unit": "DOF*iter/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64" if mode_name == "fp64" else "f32+f64-refine",
+        "data": "synthetic",
+        "config": {"workload": name + ": " + desc, "D": inst.D, "correctors": inst.d, "mode": mode_name,
+                   "backend": pinfo["backend"], "tol": tol, "l2": "flushed before every step (256 MiB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "time_to_astar_ms": ms / args.steps,
+        "iterations_per_step": [(i["iterations"], i["outer_iterations"]) for i in infos],
+        "max_rel_residual": max_rel,
+        "astar": np.round(A.real, 14).tolist(),
+        "wall_s_timed_region": wall1 - wall0,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clocks,
+        "gpu_launches": int(launches),
+        "variants": variants,
+    }
+    qp.qp_plan_destroy(plan)
+    return out
+
+
+def cpu_baseline(name, max_seconds=12.0):
+    """The FP64 oracle (numpy, one thread) on a bounded sample of the same workload: Algorithm 2 on corrector 1
+    for as many iterations as fit in about max_seconds."""
+    from oracle import qp_oracle as O
+    inst = instance(name)
+    dof_iters, secs, iters = O.timed_pcg_sample(inst, max_seconds=max_seconds)
+    return {"value": dof_iters / secs, "unit": "DOF*iter/s", "cores": 1, "kind": "oracle",
+            "sample": "%s corrector e_1: %d oracle PCG iterations (incl. initial and final true-residual applies), "
+                      "%.1f s, numpy FP64 single thread" % (name, iters, secs)}
+
+
+# ---------------------------------------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    """The oracle as it stands, on the host cores: each step is 2 oracle PCG iterations of corrector e_1 of the
+    same workload (a bounded sample); value in the same unit."""
+    from oracle import qp_oracle as O
+    inst = instance(args.workload)
+    op = O.Operator(inst)
+    M = O.jacobi_inverse(op.P, op.N, op.Ahat)
+    F = O.corrector_rhs(op.P, op.N, op.Ahat, 0)
+    for _ in range(max(args.warmup, 1)):
+        O.pcg(op, F, M, tol=0.0, maxit=1)
+    t0 = time.perf_counter()
+    its = 0
+    for _ in range(args.steps):
+        _, info = O.pcg(op, F, M, tol=0.0, maxit=2)
+        its += info["iterations"] + 2
+    secs = time.perf_counter() - t0
+    v = inst.D * its / secs
+    desc = WORKLOADS[args.workload][0]
+    return {"impl": "reference", "metric": "PCG DOF*iter/s (time-to-a* at 1e-10)", "value": v, "unit": "DOF*iter/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload + ": " + desc, "D": inst.D},
+            "cpu_baseline": {"value": v, "unit": "DOF*iter/s", "cores": 1, "kind": "oracle",
+                             "sample": "2 oracle PCG iterations (+2 applies) of corrector e_1 per step"},
+            "e2e": {"value": v, "unit": "DOF*iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def run_apply_only(args):
+    """Launches the stiffness apply of the workload's plan (all correctors as right-hand sides) --warmup + --steps
+    times; used to capture the kernel under a profiler."""
+    import torch
+    import paper_2404_06841_gb300 as qp
+    inst = instance(args.workload, args.N)
+    prec_name = args.precision or ("fp64" if WORKLOADS[args.workload][1] == "fp64" else "fp32")
+    prec = qp.QP_FP64 if prec_name == "fp64" else qp.QP_FP32
+    plan = qp.plan_from_instance(inst, precisions=1 if prec == qp.QP_FP64 else 2)
+    dt = torch.complex128 if prec == qp.QP_FP64 else torch.complex64
+    h = torch.randn((inst.d, inst.D), dtype=dt, device="cuda")
+    w = torch.empty_like(h)
+    for _ in range(args.warmup + args.steps):
+        qp.qp_apply_stiffness(plan, h, w, prec)
+    torch.cuda.synchronize()
+    print(json.dumps({"apply_only": args.workload, "N": inst.N, "D": inst.D, "precision": prec_name,
+                      "launches": args.warmup + args.steps}))
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cfg1", choices=sorted(WORKLOADS))
+    ap.add_argument("--mode", default=None, choices=["fp64", "refine"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--apply-only", action="store_true",
+                    help="profiling aid: build the plan and launch only the stiffness apply --steps times")
+    ap.add_argument("--N", type=int, default=None, help="modes per axis (overrides the workload's N)")
+    ap.add_argument("--precision", default=None, choices=["fp64", "fp32"], help="with --apply-only")
+    ap.add_argument("--exec", default="graph", choices=["graph", "direct"],
+                    help="graph: one CUDA-graph launch per solve (default); direct: kernel by kernel (profilers)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)))
+        return
+    if args.apply_only:
+        run_apply_only(args)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    out = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,170 @@
+/*
+ * qp.h - C ABI of the GB300 (sm_103a) projection-method solver for quasiperiodic elliptic problems and
+ * quasiperiodic homogenization (Jiang, Li, Zhang & Zhang, arXiv 2404.06841).
+ *
+ * A d-dimensional quasiperiodic coefficient A(x) = A(P^T x) is lifted to its parent function on the torus
+ * T^n (Sec. 2.1). On N_1 x .. x N_n Fourier modes k (storage index k mod N_j per axis, C order, last axis
+ * fastest: Sec. 3.1.2, eq. conversion) the discrete scheme (Sec. 3.1.1, eq. n-discrete_equation, and App. D
+ * for a matrix coefficient) is the linear system Q U = F with
+ *
+ *     (Q U)(k) = sum_ab lambda_a(k) sum_k' A~^{ab}_{k -N k'} lambda_b(k') U(k'),   lambda(k) = P k,
+ *
+ * which the library solves by preconditioned CG (Sec. 4.3, Algorithm 2) and turns into the homogenized
+ * coefficient A*_ij = M{ e_i^T A (e_j + grad u_j) } (Sec. 5.2, eq. homcoefficient).
+ *
+ * Conventions shared by every entry point:
+ *  - Complex vectors are interleaved (re, im): complex128 for QP_FP64, complex64 for QP_FP32. A set of
+ *    nrhs vectors is nrhs x D contiguous (vector r starts at element r*D). D = N_1 * .. * N_n.
+ *  - Pointers named "device" must be device memory of the current CUDA device (for example torch tensors);
+ *    pointers named "host" are ordinary host memory. The caller owns every pointer it passes.
+ *  - "stream" is a cudaStream_t (NULL = legacy default stream). Every call is asynchronous on that stream
+ *    unless it writes a host output (info, Astar), in which case it synchronises the stream before returning.
+ *  - The mode k = 0 is not an unknown (Sec. 3.1.1: the test space has zero mean): entry k = 0 of a
+ *    right-hand side is ignored and entry k = 0 of a solution is returned as 0. Row k = 0 of Q U is 0.
+ *  - Errors: no exception crosses the ABI. A non-zero qp_status is returned, qp_last_error() describes it
+ *    (per host thread), and outputs are unspecified. Arguments are validated before any device work.
+ */
+#ifndef QP_H
+#define QP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  QP_OK = 0,
+  QP_ERR_INVALID_ARG = 1,     /* bad d, n, N, pointer, tap list, option */
+  QP_ERR_SINGULAR_P = 2,      /* some k != 0 of K_N^n has |P k| below 1e-12 |P|: P is not a projection */
+  QP_ERR_NOT_ELLIPTIC = 3,    /* the coefficient's mean (Jacobi diagonal) is not positive */
+  QP_ERR_BREAKDOWN = 4,       /* PCG met (h, Q h) <= 0 or a NaN */
+  QP_ERR_NO_CONVERGENCE = 5,  /* maxit reached before the tolerance */
+  QP_ERR_TIMEOUT = 6,         /* a bounded device wait gave up */
+  QP_ERR_UNSUPPORTED = 7,     /* valid request that this build does not implement */
+  QP_ERR_OOM = 8,             /* device allocation failed */
+  QP_ERR_CUDA = 9             /* any other CUDA runtime error */
+} qp_status;
+
+enum { QP_COEF_SCALAR = 0, QP_COEF_DIAG = 1, QP_COEF_SYM = 2 };
+enum { QP_REPR_TAPS = 0, QP_REPR_GRID = 1 };
+enum { QP_BACKEND_AUTO = 0, QP_BACKEND_TAPS = 1, QP_BACKEND_FFT = 2 };
+enum { QP_FP64 = 0, QP_FP32 = 1 };
+enum { QP_PRECOND_JACOBI = 0, QP_PRECOND_FROBENIUS = 1 };
+enum { QP_MODE_FP64 = 0, QP_MODE_FP32_REFINE = 1 };
+enum { QP_EXEC_GRAPH = 0, QP_EXEC_DIRECT = 1 };
+enum { QP_MAX_N_AXES = 6, QP_MAX_D = 3, QP_MAX_RHS = 4, QP_MAX_TAPS = 256 };
+
+typedef struct qp_plan qp_plan;     /* opaque; owns every internal device buffer */
+typedef struct qp_batch qp_batch;   /* opaque; a set of plans solved together */
+
+/* The coefficient A(theta): real, d x d symmetric, uniformly elliptic (Sec. 2.2).
+ * kind: QP_COEF_SCALAR (A = a I, 1 component), QP_COEF_DIAG (d components a_11..a_dd),
+ *       QP_COEF_SYM (d(d+1)/2 components: the upper triangle row by row, 11, 12, .., 1d, 22, .., dd).
+ * repr: QP_REPR_TAPS - Fourier modes (taps): tap_k host int32 [ntaps x n], every |m_j| < N_j / 2;
+ *       tap_val host double [ntaps x ncomp x 2] (re, im) with A~_{-m} = conj(A~_m) (so A is real).
+ *       Values are the Fourier coefficients of Sec. 3.1.1; a mode listed twice is summed.
+ *       QP_REPR_GRID - samples A(y_j) at y_j = 2 pi j / N: grid is DEVICE double [ncomp x D], C order; the
+ *       plan copies it. Its Fourier coefficients are taken by the DFT with 1/D (Sec. 3.1.1). */
+typedef struct {
+  int kind;
+  int repr;
+  int ntaps;
+  const int32_t* tap_k;
+  const double* tap_val;
+  const double* grid;
+} qp_coeff;
+
+typedef struct {
+  int backend;      /* QP_BACKEND_*: AUTO picks TAPS for a tap coefficient, FFT for a grid one */
+  int max_rhs;      /* right-hand sides solved together, 1..QP_MAX_RHS; 0 = d */
+  int precisions;   /* workspace: bit 0 = FP64 solve, bit 1 = FP32 (refinement inner) solve; 0 = both */
+  int exec;         /* QP_EXEC_GRAPH (default): a solve is one CUDA-graph launch whose loops are conditional WHILE
+                       nodes; QP_EXEC_DIRECT: the same kernels launched one by one, the host polling convergence
+                       (for profilers and callers that cannot launch graphs) */
+} qp_options;
+
+typedef struct {
+  double tol;         /* stop when ||F - Q U||_2 <= tol ||F||_2 (Fourier coefficients; Parseval) */
+  int maxit;          /* PCG iteration cap (all inner iterations in refinement mode) */
+  int precond;        /* QP_PRECOND_JACOBI (diagonal of Q) or QP_PRECOND_FROBENIUS (eq. preconditioner) */
+  int mode;           /* QP_MODE_FP64: FP64 vectors and operator; QP_MODE_FP32_REFINE: FP32 inner PCG in an
+                         FP64 iterative-refinement loop (FP64 true residual, FP64 dot products) */
+  double inner_tol;   /* refinement: relative tolerance of each inner FP32 solve (0 = 1e-5) */
+  int max_outer;      /* refinement: outer-iteration cap (0 = 12) */
+} qp_solve_opts;
+
+typedef struct {
+  int status;            /* qp_status of this right-hand side */
+  int iterations;        /* PCG iterations (FP64 mode) or inner FP32 iterations (refinement) */
+  int outer_iterations;  /* FP64 true-residual evaluations in refinement mode (0 in FP64 mode) */
+  double rel_residual;   /* ||F - Q U||_2 / ||F||_2 recomputed in FP64 at exit (0 for F = 0) */
+} qp_solve_info;
+
+typedef struct {
+  int64_t D;             /* N_1 * .. * N_n */
+  int backend;           /* QP_BACKEND_TAPS or QP_BACKEND_FFT, as chosen */
+  int ntaps;             /* distinct Fourier modes of the coefficient (taps backend) */
+  int max_rhs;
+  double min_abs_lambda; /* min over k != 0 of |P k| */
+  int64_t device_bytes;  /* device memory the plan holds */
+} qp_plan_info;
+
+/* Creates a plan: validates d (1..3), n (d..6), P (host double d x n, row-major, Sec. 2.1 projection
+ * matrix), N (host int[n], 2..1024 each, products of 2 and 3 for the FFT backend), the coefficient, and builds
+ * the per-axis lambda tables, the coefficient representation, and the Jacobi and Frobenius diagonals
+ * (Sec. 4.3, eq. preconditioner; O(gD) for taps). Work runs on "stream"; the call synchronises it. */
+qp_status qp_plan_create(int d, int n, const double* P, const int* N, const qp_coeff* coeff,
+                         const qp_options* opt, void* stream, qp_plan** out);
+qp_status qp_plan_destroy(qp_plan* plan);
+qp_status qp_plan_query(const qp_plan* plan, qp_plan_info* info);
+
+/* QU = Q U (eq. n-discrete_equation; compressed mat-vec of Sec. 4.2 on the taps backend, or gradient ->
+ * inverse n-dim DFT -> pointwise A(y) -> forward DFT -> divergence on the FFT backend).
+ * U, QU: device, nrhs x D complex (complex128 for QP_FP64, complex64 for QP_FP32); must not overlap. */
+qp_status qp_apply_stiffness(qp_plan* plan, int nrhs, const void* U, void* QU, int precision, void* stream);
+
+/* F = the corrector right-hand sides F_j(k) = i sum_a lambda_a(k) A~^{aj}_k, F_j(0) = 0, for
+ * j = j0 .. j0+nrhs-1 (0-based; Sec. 5.2 eq. corrector, App. D f_1 = d alpha/dx_1). F: device complex128
+ * nrhs x D. */
+qp_status qp_corrector_rhs(qp_plan* plan, int j0, int nrhs, void* F, void* stream);
+
+/* Solves Q U = F for nrhs right-hand sides with PCG (Algorithm 2, z = M r). F: device complex128 nrhs x D.
+ * U: device complex128 nrhs x D, in: initial guess (warm start), out: solution. info: host, nrhs entries.
+ * Returns QP_OK only if every right-hand side met opts->tol; otherwise the worst status. */
+qp_status qp_pcg_solve(qp_plan* plan, int nrhs, const void* F, void* U, const qp_solve_opts* opts,
+                       qp_solve_info* info, void* stream);
+
+/* Astar = the torus average A*_ij = A~^{ij}_0 + i sum_k sum_b A~^{ib}_{-k} lambda_b(k) U_j(k)
+ * (eq. homcoefficient written in Fourier terms) from the d corrector solutions U (device complex128 d x D).
+ * Astar_re, Astar_im: host double d x d row-major (Astar_im may be NULL). FP64 throughout. */
+qp_status qp_homogenized_reduce(qp_plan* plan, const void* U, double* Astar_re, double* Astar_im, void* stream);
+
+/* The whole homogenization: the d corrector right-hand sides, their PCG solves (FP64 or FP32 + FP64
+ * refinement per opts->mode), and the reduction above. Astar_re/Astar_im: host d x d; infos: host, d entries. */
+qp_status qp_homogenized(qp_plan* plan, const qp_solve_opts* opts, double* Astar_re, double* Astar_im,
+                         qp_solve_info* infos, void* stream);
+
+/* Unnormalised in-place n-dimensional complex DFT of "count" contiguous arrays of shape N[0..n-1]:
+ * X(k) = sum_j x(j) exp(sign * 2 pi i k.j / N), sign = -1 (forward) or +1 (inverse, without 1/D).
+ * data: device complex128 (QP_FP64) or complex64 (QP_FP32). N_j products of 2 and 3, 2..1024. */
+qp_status qp_fft(int n, const int* N, int count, void* data, int sign, int precision, void* stream);
+
+/* Batched homogenization: every corrector of every plan is solved in the same launches (one unit per
+ * (plan, corrector)); plans may differ in d, n, N and coefficient. Astar_all: host, sum over plans of d*d
+ * doubles (plan order, row-major each); infos: host, one per unit in plan order. */
+qp_status qp_batch_create(int count, qp_plan* const* plans, qp_batch** out);
+qp_status qp_batch_homogenized(qp_batch* batch, const qp_solve_opts* opts, double* Astar_all,
+                               qp_solve_info* infos, void* stream);
+qp_status qp_batch_destroy(qp_batch* batch);
+
+/* Description of the last error on this host thread ("" if none). The string stays valid until the next call. */
+const char* qp_last_error(void);
+
+/* Number of CUDA kernels this library has launched in this process so far (all threads, all plans). */
+uint64_t qp_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QP_H */

@@ -221,6 +221,35 @@ def apply_fft(P, N, Agrid, h) -> np.ndarray:
     return w
 
 
+def apply_taps_at(P, N, taps_k, taps_val, kind, h, points) -> np.ndarray:
+    """w(k) of eq. n-discrete_equation at the given storage points only, one plain sum per point:
+    w(k) = sum over taps m of sum_ab lambda_a(k) A~^{ab}_m lambda_b(k -N m) h(k -N m), lambda = P k.
+    ``h`` may be any array indexable by storage tuples (e.g. a memory-mapped full-size vector); ``points`` is a
+    list of storage index tuples. For sampled checks at sizes the vectorised operator cannot hold."""
+    P = np.asarray(P, dtype=np.float64)
+    d = P.shape[0]
+    N = tuple(int(x) for x in N)
+    pairs = _pairs(kind, d)
+    mats = []
+    for val in taps_val:
+        Am = np.zeros((d, d), dtype=np.complex128)
+        for comp, entries in enumerate(pairs):
+            for (a, b) in entries:
+                Am[a, b] += val[comp]
+        mats.append(Am)
+    out = np.zeros(len(points), dtype=np.complex128)
+    for q, idx in enumerate(points):
+        k = np.array([signed_k(Nj)[i] for i, Nj in zip(idx, N)], dtype=np.float64)
+        lk = P @ k
+        s = 0.0 + 0.0j
+        for m, Am in zip(taps_k, mats):
+            idx2 = tuple((int(i) - int(mj)) % Nj for i, mj, Nj in zip(idx, m, N))
+            k2 = np.array([signed_k(Nj)[i] for i, Nj in zip(idx2, N)], dtype=np.float64)
+            s += (lk @ Am @ (P @ k2)) * h[idx2]
+        out[q] = s
+    return out
+
+
 class Operator:
     """The stiffness operator of one instance, applied by convolution (taps) or by the DFT (grid)."""
 

@@ -1,0 +1,169 @@
+// Device helpers shared by the stencil and PCG kernels: reductions, chunk arrivals, fast division,
+// mode digits and the tap weight lambda(k)^T C_t lambda(k -N m_t).
+#pragma once
+
+#include <cfloat>
+
+#include "qp_internal.cuh"
+
+namespace qp {
+
+template <typename T> __device__ __forceinline__ cplx<T> mk(T x, T y) {
+  cplx<T> r;
+  r.x = x;
+  r.y = y;
+  return r;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double warp_min(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Sum (or min) NV values over the block in a fixed tree; thread 0 holds the results afterwards.
+template <int NV, bool MIN = false>
+__device__ __forceinline__ void block_reduce(double (&v)[NV]) {
+  __shared__ double sm[NV][BLOCK / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) v[q] = MIN ? warp_min(v[q]) : warp_sum(v[q]);
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) sm[q][wid] = v[q];
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double x = lane < BLOCK / 32 ? sm[q][lane] : (MIN ? DBL_MAX : 0.0);
+      v[q] = MIN ? warp_min(x) : warp_sum(x);
+    }
+  }
+}
+
+__device__ __forceinline__ uint32_t fdiv(uint32_t x, const FastDiv& f) {
+  return (uint32_t)(((uint64_t)x * f.m) >> f.p);
+}
+
+// Storage digits ibar_j of linear index e (last axis fastest) and the signed modes k_j.
+__device__ __forceinline__ void mode_digits(const PlanDev& p, int e, int (&ib)[MAXN], int (&k)[MAXN]) {
+  uint32_t x = (uint32_t)e;
+#pragma unroll
+  for (int j = MAXN - 1; j >= 0; --j) {
+    if (j < p.n) {
+      const uint32_t q = fdiv(x, p.div[j]);
+      ib[j] = (int)(x - q * (uint32_t)p.N[j]);
+      k[j] = (2 * ib[j] < p.N[j]) ? ib[j] : ib[j] - p.N[j];
+      x = q;
+    } else {
+      ib[j] = 0;
+      k[j] = 0;
+    }
+  }
+}
+
+template <typename T> __device__ __forceinline__ T pcoef(const PlanDev& p, int a, int j);
+template <> __device__ __forceinline__ double pcoef<double>(const PlanDev& p, int a, int j) { return p.P[a][j]; }
+template <> __device__ __forceinline__ float pcoef<float>(const PlanDev& p, int a, int j) { return p.P32[a][j]; }
+
+__device__ __forceinline__ int sym_idx(int a, int b, int d) {
+  if (a > b) {
+    int t = a;
+    a = b;
+    b = t;
+  }
+  return a * d - (a * (a - 1)) / 2 + (b - a);
+}
+
+// lambda(k)^T C lambda' for a coefficient with stored components c (kind, d at run time).
+template <typename T>
+__device__ __forceinline__ cplx<T> weight_general(int kind, int d, const cplx<T>* c, const T (&lk)[MAXD],
+                                                  const T (&l2)[MAXD]) {
+  cplx<T> r = mk<T>(0, 0);
+  if (kind == QP_COEF_SCALAR) {
+    T s = 0;
+#pragma unroll
+    for (int a = 0; a < MAXD; ++a)
+      if (a < d) s = fma(lk[a], l2[a], s);
+    r.x = c[0].x * s;
+    r.y = c[0].y * s;
+  } else if (kind == QP_COEF_DIAG) {
+#pragma unroll
+    for (int a = 0; a < MAXD; ++a) {
+      if (a < d) {
+        const T s = lk[a] * l2[a];
+        r.x = fma(c[a].x, s, r.x);
+        r.y = fma(c[a].y, s, r.y);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int a = 0; a < MAXD; ++a) {
+#pragma unroll
+      for (int b = 0; b < MAXD; ++b) {
+        if (a < d && b < d) {
+          const cplx<T> cab = c[sym_idx(a, b, d)];
+          const T s = lk[a] * l2[b];
+          r.x = fma(cab.x, s, r.x);
+          r.y = fma(cab.y, s, r.y);
+        }
+      }
+    }
+  }
+  return r;
+}
+
+// Record this block's chunk partials (thread 0 holds them in v), count the chunk's arrival for its unit and
+// return true in the block that completes the unit (all its chunks are in).
+template <int NV>
+__device__ __forceinline__ bool chunk_arrive(const BatchDev& b, int c, int u, const double (&v)[NV]) {
+  __shared__ int s_last;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) b.partials[(size_t)q * b.nchunks + c] = v[q];
+    __threadfence();
+    s_last = (atomicAdd(&b.ucount[u], 1u) == (unsigned)b.units[u].nchunk - 1u);
+  }
+  __syncthreads();
+  const bool last = s_last != 0;
+  if (last) __threadfence();
+  return last;
+}
+
+// In the completing block: sums every slot over the unit's chunks in a fixed order; thread 0 gets the sums.
+template <int NV>
+__device__ __forceinline__ void unit_sums(const BatchDev& b, const UnitDev& un, double (&v)[NV]) {
+#pragma unroll
+  for (int q = 0; q < NV; ++q) v[q] = 0.0;
+  for (int i = threadIdx.x; i < un.nchunk; i += BLOCK) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[q] += __ldcg(b.partials + (size_t)q * b.nchunks + un.chunk0 + i);
+  }
+  block_reduce<NV>(v);
+}
+
+// Last block of the kernel to finish (one integer atomic per block).
+__device__ __forceinline__ bool kernel_arrive(const BatchDev& b) {
+  __shared__ int s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = (atomicAdd(b.kcount, 1u) == gridDim.x - 1u);
+  }
+  __syncthreads();
+  const bool last = s_last != 0;
+  if (last) __threadfence();
+  return last;
+}
+
+__device__ __forceinline__ int ld_int(const int* p) { return *((volatile const int*)p); }
+
+}  // namespace qp

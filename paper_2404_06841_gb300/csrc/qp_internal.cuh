@@ -1,0 +1,145 @@
+// Internal declarations shared by the CUDA translation units of libqp (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/qp.h"
+
+namespace qp {
+
+// Error carried from any translation unit to the C ABI boundary (converted to a qp_status there).
+struct QpError {
+  qp_status s;
+  std::string msg;
+};
+
+[[noreturn]] inline void raise(qp_status s, const std::string& msg) { throw QpError{s, msg}; }
+
+inline void ck(cudaError_t e, const char* what, int line) {
+  if (e == cudaSuccess) return;
+  const qp_status s = (e == cudaErrorMemoryAllocation) ? QP_ERR_OOM : QP_ERR_CUDA;
+  raise(s, std::string(what) + " (line " + std::to_string(line) + "): " + cudaGetErrorString(e));
+}
+#define CK(call) ::qp::ck((call), #call, __LINE__)
+#define CK_LAUNCH() ::qp::ck(cudaGetLastError(), "kernel launch", __LINE__)
+
+// Number of kernels this library has launched in the process (read through qp_launch_count()). Kernels that
+// run inside a CUDA graph are added by the host after each graph launch from the iteration counts.
+void count_launch(int n = 1);
+
+constexpr int MAXN = QP_MAX_N_AXES;
+constexpr int MAXD = QP_MAX_D;
+constexpr int MAXR = QP_MAX_RHS;
+constexpr int MAXT = QP_MAX_TAPS;
+constexpr int BLOCK = 256;           // threads per block of every elementwise / stencil kernel
+constexpr int NQ = 4;                // reduction quantities per right-hand side
+constexpr int NSLOT = MAXR * NQ;     // partial slots per chunk
+
+template <typename T> struct V2;
+template <> struct V2<double> { using type = double2; };
+template <> struct V2<float> { using type = float2; };
+template <typename T> using cplx = typename V2<T>::type;
+
+// Division by a runtime divisor d <= 2^30 of dividends x < 2^31 without a hardware divide: with
+// L = ceil(log2 d), p = 31 + L and m = ceil(2^p / d) (< 2^32), floor(x / d) = (x * m) >> p exactly
+// (Granlund & Montgomery, "Division by invariant integers using multiplication", PLDI 1994).
+struct FastDiv {
+  uint32_t d;
+  uint32_t m;
+  uint32_t p;
+};
+
+// Device description of one plan's geometry and (for the taps backend) its taps, sorted as
+// [mean tap][star taps of axis 0] .. [star taps of axis n-1][taps with several nonzero axes].
+struct alignas(16) PlanDev {
+  int n, d, D, kind;
+  int ncomp, ntaps, real_coef, backend;
+  int N[MAXN];
+  int stride[MAXN];
+  FastDiv div[MAXN];
+  int star_begin[MAXN + 1];   // star taps of axis j: [star_begin[j], star_begin[j+1]); multi-axis: [star_begin[n], ntaps)
+  double P[MAXD][MAXN];
+  float P32[MAXD][MAXN];
+  const double2* coef64;      // [ntaps][ncomp], sorted order
+  const float2* coef32;
+  signed char m[MAXT][MAXN];  // sorted tap modes
+};
+static_assert(sizeof(PlanDev) % 16 == 0, "PlanDev is copied to shared memory in 16-byte words");
+
+// One solve unit: a plan and its nrhs right-hand sides (contiguous nrhs x D vectors).
+struct UnitDev {
+  const PlanDev* plan;
+  int D, nrhs, chunk0, nchunk;
+  const double2* F;   // right-hand side (FP64)
+  double2* U;         // solution (FP64)
+  double2* r;         // FP64 PCG residual
+  double2* h;         // FP64 PCG direction
+  double2* w;         // FP64 Q h, or the FP64 true residual F - Q U
+  float2* F32;        // refinement: scaled FP32 right-hand side
+  float2* U32;        // refinement: FP32 correction
+  float2* r32;
+  float2* h32;
+  float2* w32;
+  const double* minv64;   // diagonal preconditioner M (z = M r)
+  const float* minv32;
+};
+
+// Per right-hand-side state (device).
+struct RhsSt {
+  double f2, rz, hw, rr, beta, alpha;     // PCG level (alpha = rz / hw, set once per iteration)
+  double of2, orr, scale, prev_rel;       // refinement outer level (FP64 true residual)
+  double inv_scale, pad0;                 // ||F - Q U|| of the last outer step (1 / scale)
+  int iters, done, status, inner_total;
+  int outer, odone, ostatus, pad1;
+};
+
+struct BatchDev {
+  int nunits, nchunks, chunk, nslots;   // chunk = elements per chunk (multiple of BLOCK)
+  const UnitDev* units;
+  RhsSt* st;                            // [nunits * MAXR]
+  const int* chunk_unit;                // [nchunks]
+  double* partials;                     // [NSLOT][nchunks]
+  unsigned* ucount;                     // [nunits] chunk arrivals per unit
+  unsigned* kcount;                     // [1] block arrivals per kernel
+  int* ndone;                           // [4]: right-hand sides done at the PCG level, at the outer level;
+                                        //      loop counts of the PCG and the outer loop
+  double tol2, otol2;                   // PCG-level and outer (refinement) tolerances, squared
+  int maxit, max_outer;
+};
+
+enum { EPI_DOT_HW = 0, EPI_RESIDUAL = 1, EPI_NONE = 2 };
+enum { LEVEL_FP64 = 0, LEVEL_FP32 = 1 };   // which vector set a PCG kernel works on
+
+// ---- taps backend kernels (qp_taps.cu)
+// Apply over every chunk of the batch (taps units only; FFT units get their w from the FFT passes and only
+// the epilogue here). level LEVEL_FP64: EPI_DOT_HW reads h and writes w; EPI_RESIDUAL reads U and writes
+// w = F - Q U; LEVEL_FP32: EPI_DOT_HW reads h32 and writes w32. refine: EPI_RESIDUAL runs the outer
+// (refinement) bookkeeping and sets the graph conditional cond (0 = none) while some rhs is not outer-done.
+// realc: every taps plan in the batch has real tap values; mc: largest ntaps * ncomp over its taps plans.
+// maxr: the largest nrhs of the batch's units.
+void launch_apply(const BatchDev& b, bool realc, int mc, int maxr, int level, int epi, bool refine,
+                  unsigned long long cond, int nblk, cudaStream_t s);
+// Standalone apply of one plan: w = Q h for nrhs vectors (no reductions).
+template <typename T>
+void launch_apply_plain(const PlanDev* plan_dev, bool realc, int mc, int D, int nrhs, const cplx<T>* h, cplx<T>* w,
+                        cudaStream_t s);
+void launch_diag(const PlanDev* plan_dev, int mc, int D, double* jac, double* frob, float* jac32, float* frob32,
+                 double* partials, unsigned* counter, double* out, int nblk, cudaStream_t s);
+void launch_rhs_taps(const PlanDev* plan_dev, int mc, int j0, int nrhs, int D, double2* F, cudaStream_t s);
+void launch_astar_taps(const PlanDev* plan_dev, int mc, int D, const double2* U, double* out, cudaStream_t s);
+
+// ---- PCG kernels (qp_pcg.cu)
+void launch_level_reset(const BatchDev& b, int which, cudaStream_t s);
+// maxr: the largest nrhs of the batch's units (selects the kernel instantiation).
+void launch_pcg_init(const BatchDev& b, int maxr, int level, bool warm, unsigned long long cond, int nblk,
+                     cudaStream_t s);
+void launch_pcg_update(const BatchDev& b, int maxr, int level, unsigned long long cond, int nblk, cudaStream_t s);
+void launch_pcg_hupdate(const BatchDev& b, int maxr, int level, int nblk, cudaStream_t s);
+void launch_refine_prep(const BatchDev& b, int nblk, cudaStream_t s);
+void launch_refine_accum(const BatchDev& b, int nblk, cudaStream_t s);
+
+}  // namespace qp

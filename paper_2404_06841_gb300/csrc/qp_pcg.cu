@@ -1,0 +1,343 @@
+// PCG update and reduction kernels of Algorithm 2 (C-PCG) over a batch of units, and the FP32/FP64
+// iterative-refinement steps around it.
+//
+// Per iteration: the stiffness apply (qp_taps.cu or the FFT passes) writes w = Q h and reduces (h, w); then
+//   pcg_update:  alpha = (r, z) / (h, Q h), U += alpha h, r -= alpha Q h, reduce (r, z') with z' = M r and
+//                ||r||^2; beta = (r', z') / (r, z); convergence ||r|| <= tol ||F||;
+//   pcg_hupdate: h = M r + beta h.
+// z = M r is recomputed where needed instead of stored (the preconditioner is diagonal). Dot products are
+// accumulated in FP64 whatever the vector precision. The update kernel's last block sets the CUDA-graph
+// conditional that keeps the iteration loop running while some right-hand side is not done.
+#include "qp_device.cuh"
+
+namespace qp {
+
+// ndone[which] = 0; which == 1 also resets the outer (refinement) state of every right-hand side.
+__global__ void k_level_reset(BatchDev b, int which) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    b.ndone[which] = 0;
+    b.ndone[2 + which] = 0;   // loop-iteration counter of this level (hard cap on the graph's WHILE loop)
+    *b.kcount = 0;
+  }
+  if (which == 1) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.nunits * MAXR; i += gridDim.x * blockDim.x) {
+      RhsSt& x = b.st[i];
+      x.outer = 0;
+      x.inner_total = 0;
+      x.iters = 0;
+      x.odone = (i % MAXR) < b.units[i / MAXR].nrhs ? 0 : 1;
+      x.ostatus = QP_ERR_NO_CONVERGENCE;
+      x.prev_rel = INFINITY;
+      x.scale = 0.0;
+      x.inv_scale = 0.0;
+    }
+  }
+}
+
+void launch_level_reset(const BatchDev& b, int which, cudaStream_t s) {
+  k_level_reset<<<1, BLOCK, 0, s>>>(b, which);
+  count_launch();
+}
+
+template <typename T> __device__ __forceinline__ const cplx<T>* vF(const UnitDev& u, int level);
+template <> __device__ __forceinline__ const double2* vF<double>(const UnitDev& u, int) { return u.F; }
+template <> __device__ __forceinline__ const float2* vF<float>(const UnitDev& u, int) { return u.F32; }
+template <typename T> __device__ __forceinline__ cplx<T>* vU(const UnitDev& u);
+template <> __device__ __forceinline__ double2* vU<double>(const UnitDev& u) { return u.U; }
+template <> __device__ __forceinline__ float2* vU<float>(const UnitDev& u) { return u.U32; }
+template <typename T> __device__ __forceinline__ cplx<T>* vR(const UnitDev& u);
+template <> __device__ __forceinline__ double2* vR<double>(const UnitDev& u) { return u.r; }
+template <> __device__ __forceinline__ float2* vR<float>(const UnitDev& u) { return u.r32; }
+template <typename T> __device__ __forceinline__ cplx<T>* vH(const UnitDev& u);
+template <> __device__ __forceinline__ double2* vH<double>(const UnitDev& u) { return u.h; }
+template <> __device__ __forceinline__ float2* vH<float>(const UnitDev& u) { return u.h32; }
+template <typename T> __device__ __forceinline__ cplx<T>* vW(const UnitDev& u);
+template <> __device__ __forceinline__ double2* vW<double>(const UnitDev& u) { return u.w; }
+template <> __device__ __forceinline__ float2* vW<float>(const UnitDev& u) { return u.w32; }
+template <typename T> __device__ __forceinline__ const T* vM(const UnitDev& u);
+template <> __device__ __forceinline__ const double* vM<double>(const UnitDev& u) { return u.minv64; }
+template <> __device__ __forceinline__ const float* vM<float>(const UnitDev& u) { return u.minv32; }
+
+// r = F - w (warm start: w = Q U) or r = F, r(0) = 0, h = M r; FP32 level: U32 = 0, and right-hand sides that
+// already meet the outer tolerance start from F = 0. Reduces ||F||^2, (r, M r), ||r||^2.
+template <typename T, int NR>
+__global__ void __launch_bounds__(BLOCK) k_pcg_init(BatchDev b, int level, int warm, unsigned long long cond) {
+  for (int c = blockIdx.x; c < b.nchunks; c += gridDim.x) {
+    const int u = b.chunk_unit[c];
+    const UnitDev& un = b.units[u];
+    RhsSt* st = b.st + (size_t)u * MAXR;
+    const int nrhs = un.nrhs, D = un.D;
+    const cplx<T>* F = vF<T>(un, level);
+    cplx<T>* U = vU<T>(un);
+    cplx<T>* r = vR<T>(un);
+    cplx<T>* h = vH<T>(un);
+    const cplx<T>* w = reinterpret_cast<const cplx<T>*>(vW<T>(un));
+    const T* M = vM<T>(un);
+    int zero_rhs[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) zero_rhs[k] = (k < nrhs && level == LEVEL_FP32) ? ld_int(&st[k].odone) : 0;
+    double v[3 * NR];
+#pragma unroll
+    for (int q = 0; q < 3 * NR; ++q) v[q] = 0.0;
+    const int base = (c - un.chunk0) * b.chunk, end = min(base + b.chunk, D);
+    for (int e = base + threadIdx.x; e < end; e += BLOCK) {
+      const T m = M[e];
+#pragma unroll
+      for (int k = 0; k < NR; ++k) {
+        if (k < nrhs) {
+          const size_t o = (size_t)k * D + e;
+          cplx<T> f = F[o];
+          if (e == 0 || zero_rhs[k]) f = mk<T>(0, 0);
+          cplx<T> rv = f;
+          if (warm && e != 0) {
+            const cplx<T> wv = w[o];
+            rv = mk<T>(f.x - wv.x, f.y - wv.y);
+          }
+          r[o] = rv;
+          h[o] = mk<T>(m * rv.x, m * rv.y);
+          if (level == LEVEL_FP32) U[o] = mk<T>(0, 0);
+          const double rr = (double)rv.x * rv.x + (double)rv.y * rv.y;
+          v[3 * k] += (double)f.x * f.x + (double)f.y * f.y;
+          v[3 * k + 1] += (double)m * rr;
+          v[3 * k + 2] += rr;
+        }
+      }
+    }
+    block_reduce<3 * NR>(v);
+    if (!chunk_arrive<3 * NR>(b, c, u, v)) continue;
+    unit_sums<3 * NR>(b, un, v);
+    for (int k = 0; k < nrhs && k < NR; ++k) {
+      const double f2 = v[3 * k], rz = v[3 * k + 1], rr = v[3 * k + 2];
+      if (threadIdx.x == 0) {
+        RhsSt& x = st[k];
+        x.f2 = f2;
+        x.rz = rz;
+        x.rr = rr;
+        x.iters = 0;
+        x.status = QP_OK;
+        x.done = (f2 == 0.0 || rr <= b.tol2 * f2) ? 1 : 0;
+        if (!isfinite(rr)) {
+          x.done = 1;
+          x.status = QP_ERR_BREAKDOWN;
+        }
+        if (x.done) atomicAdd(&b.ndone[0], 1);
+      }
+    }
+    if (threadIdx.x == 0) b.ucount[u] = 0;
+  }
+  if (kernel_arrive(b) && threadIdx.x == 0) {
+    if (cond != 0ull) cudaGraphSetConditional(cond, ld_int(&b.ndone[0]) < b.nslots ? 1u : 0u);
+    *b.kcount = 0;
+  }
+}
+
+// alpha step, residual update, and the reductions for beta and the convergence test.
+template <typename T, int NR>
+__global__ void __launch_bounds__(BLOCK) k_pcg_update(BatchDev b, int level, unsigned long long cond) {
+  for (int c = blockIdx.x; c < b.nchunks; c += gridDim.x) {
+    const int u = b.chunk_unit[c];
+    const UnitDev& un = b.units[u];
+    RhsSt* st = b.st + (size_t)u * MAXR;
+    const int nrhs = un.nrhs, D = un.D;
+    int done[NR];
+    T alpha[NR];
+    bool active = false;
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+      done[k] = k < nrhs ? ld_int(&st[k].done) : 1;
+      alpha[k] = done[k] ? T(0) : (T)__ldcg(&st[k].alpha);
+      active |= !done[k];
+    }
+    if (!active) continue;
+    cplx<T>* U = vU<T>(un);
+    cplx<T>* r = vR<T>(un);
+    const cplx<T>* h = vH<T>(un);
+    const cplx<T>* w = vW<T>(un);
+    const T* M = vM<T>(un);
+    double v[2 * NR];
+#pragma unroll
+    for (int q = 0; q < 2 * NR; ++q) v[q] = 0.0;
+    const int base = (c - un.chunk0) * b.chunk, end = min(base + b.chunk, D);
+    for (int e = base + threadIdx.x; e < end; e += BLOCK) {
+      const T m = M[e];
+#pragma unroll
+      for (int k = 0; k < NR; ++k) {
+        if (k < nrhs && !done[k]) {
+          const size_t o = (size_t)k * D + e;
+          const T al = alpha[k];
+          const cplx<T> hv = h[o], wv = w[o];
+          cplx<T> uv = U[o], rv = r[o];
+          uv.x = fma(al, hv.x, uv.x);
+          uv.y = fma(al, hv.y, uv.y);
+          rv.x = fma(-al, wv.x, rv.x);
+          rv.y = fma(-al, wv.y, rv.y);
+          U[o] = uv;
+          r[o] = rv;
+          const double rr = (double)rv.x * rv.x + (double)rv.y * rv.y;
+          v[2 * k] += (double)m * rr;
+          v[2 * k + 1] += rr;
+        }
+      }
+    }
+    block_reduce<2 * NR>(v);
+    if (!chunk_arrive<2 * NR>(b, c, u, v)) continue;
+    unit_sums<2 * NR>(b, un, v);
+    for (int k = 0; k < nrhs && k < NR; ++k) {
+      const double rz = v[2 * k], rr = v[2 * k + 1];
+      if (threadIdx.x == 0 && !done[k]) {
+        RhsSt& x = st[k];
+        x.iters += 1;
+        x.rr = rr;
+        int dn = 0;
+        if (!isfinite(rr)) {
+          dn = 1;
+          x.status = QP_ERR_BREAKDOWN;
+        } else if (rr <= b.tol2 * x.f2) {
+          dn = 1;
+        } else if (x.iters >= b.maxit) {
+          dn = 1;
+          x.status = QP_ERR_NO_CONVERGENCE;
+        }
+        x.beta = rz / x.rz;
+        x.rz = rz;
+        if (dn) {
+          x.done = 1;
+          atomicAdd(&b.ndone[0], 1);
+        }
+      }
+    }
+    if (threadIdx.x == 0) b.ucount[u] = 0;
+  }
+  if (kernel_arrive(b) && threadIdx.x == 0) {
+    // continue while some right-hand side is active; the loop counter bounds the WHILE node in any case
+    const int loops = ++b.ndone[2];
+    if (cond != 0ull)
+      cudaGraphSetConditional(cond, (ld_int(&b.ndone[0]) < b.nslots && loops < b.maxit + 2) ? 1u : 0u);
+    *b.kcount = 0;
+  }
+}
+
+template <typename T, int NR>
+__global__ void __launch_bounds__(BLOCK) k_pcg_hupdate(BatchDev b, int level) {
+  for (int c = blockIdx.x; c < b.nchunks; c += gridDim.x) {
+    const int u = b.chunk_unit[c];
+    const UnitDev& un = b.units[u];
+    RhsSt* st = b.st + (size_t)u * MAXR;
+    const int nrhs = un.nrhs, D = un.D;
+    int done[NR];
+    T beta[NR];
+    bool active = false;
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+      done[k] = k < nrhs ? ld_int(&st[k].done) : 1;
+      beta[k] = done[k] ? T(0) : (T)__ldcg(&st[k].beta);
+      active |= !done[k];
+    }
+    if (!active) continue;
+    const cplx<T>* r = vR<T>(un);
+    cplx<T>* h = vH<T>(un);
+    const T* M = vM<T>(un);
+    const int base = (c - un.chunk0) * b.chunk, end = min(base + b.chunk, D);
+    for (int e = base + threadIdx.x; e < end; e += BLOCK) {
+      const T m = M[e];
+#pragma unroll
+      for (int k = 0; k < NR; ++k) {
+        if (k < nrhs && !done[k]) {
+          const size_t o = (size_t)k * D + e;
+          const cplx<T> rv = r[o];
+          cplx<T> hv = h[o];
+          hv.x = fma(beta[k], hv.x, m * rv.x);
+          hv.y = fma(beta[k], hv.y, m * rv.y);
+          h[o] = hv;
+        }
+      }
+    }
+  }
+}
+
+// Refinement: F32 = scale * (F - Q64 U64) for the right-hand sides still refining (scale = 1 / ||F - Q U||).
+__global__ void __launch_bounds__(BLOCK) k_refine_prep(BatchDev b) {
+  for (int c = blockIdx.x; c < b.nchunks; c += gridDim.x) {
+    const int u = b.chunk_unit[c];
+    const UnitDev& un = b.units[u];
+    const RhsSt* st = b.st + (size_t)u * MAXR;
+    const int nrhs = un.nrhs, D = un.D;
+    const int base = (c - un.chunk0) * b.chunk, end = min(base + b.chunk, D);
+    for (int k = 0; k < nrhs; ++k) {
+      if (ld_int(&st[k].odone)) continue;
+      const double sc = __ldcg(&st[k].scale);
+      for (int e = base + threadIdx.x; e < end; e += BLOCK) {
+        const size_t o = (size_t)k * D + e;
+        const double2 v = un.w[o];
+        un.F32[o] = make_float2((float)(v.x * sc), (float)(v.y * sc));
+      }
+    }
+  }
+}
+
+// Refinement: U64 += c32 / scale for the right-hand sides still refining.
+__global__ void __launch_bounds__(BLOCK) k_refine_accum(BatchDev b) {
+  for (int c = blockIdx.x; c < b.nchunks; c += gridDim.x) {
+    const int u = b.chunk_unit[c];
+    const UnitDev& un = b.units[u];
+    const RhsSt* st = b.st + (size_t)u * MAXR;
+    const int nrhs = un.nrhs, D = un.D;
+    const int base = (c - un.chunk0) * b.chunk, end = min(base + b.chunk, D);
+    for (int k = 0; k < nrhs; ++k) {
+      if (ld_int(&st[k].odone)) continue;
+      const double inv = __ldcg(&st[k].inv_scale);
+      for (int e = base + threadIdx.x; e < end; e += BLOCK) {
+        const size_t o = (size_t)k * D + e;
+        const float2 cv = un.U32[o];
+        double2 uv = un.U[o];
+        uv.x = fma((double)cv.x, inv, uv.x);
+        uv.y = fma((double)cv.y, inv, uv.y);
+        un.U[o] = uv;
+      }
+    }
+  }
+}
+
+#define QP_NR_SWITCH(maxr, CALL) \
+  switch (maxr) {                  \
+    case 1: CALL(1); break;        \
+    case 2: CALL(2); break;        \
+    case 3: CALL(3); break;        \
+    default: CALL(4); break;       \
+  }
+
+void launch_pcg_init(const BatchDev& b, int maxr, int level, bool warm, unsigned long long cond, int nblk,
+                     cudaStream_t s) {
+#define QP_CALL(NR)                                                                                  \
+  if (level == LEVEL_FP32) k_pcg_init<float, NR><<<nblk, BLOCK, 0, s>>>(b, level, warm ? 1 : 0, cond); \
+  else k_pcg_init<double, NR><<<nblk, BLOCK, 0, s>>>(b, level, warm ? 1 : 0, cond)
+  QP_NR_SWITCH(maxr, QP_CALL)
+#undef QP_CALL
+  count_launch();
+}
+void launch_pcg_update(const BatchDev& b, int maxr, int level, unsigned long long cond, int nblk, cudaStream_t s) {
+#define QP_CALL(NR)                                                                      \
+  if (level == LEVEL_FP32) k_pcg_update<float, NR><<<nblk, BLOCK, 0, s>>>(b, level, cond); \
+  else k_pcg_update<double, NR><<<nblk, BLOCK, 0, s>>>(b, level, cond)
+  QP_NR_SWITCH(maxr, QP_CALL)
+#undef QP_CALL
+  count_launch();
+}
+void launch_pcg_hupdate(const BatchDev& b, int maxr, int level, int nblk, cudaStream_t s) {
+#define QP_CALL(NR)                                                                 \
+  if (level == LEVEL_FP32) k_pcg_hupdate<float, NR><<<nblk, BLOCK, 0, s>>>(b, level); \
+  else k_pcg_hupdate<double, NR><<<nblk, BLOCK, 0, s>>>(b, level)
+  QP_NR_SWITCH(maxr, QP_CALL)
+#undef QP_CALL
+  count_launch();
+}
+void launch_refine_prep(const BatchDev& b, int nblk, cudaStream_t s) {
+  k_refine_prep<<<nblk, BLOCK, 0, s>>>(b);
+  count_launch();
+}
+void launch_refine_accum(const BatchDev& b, int nblk, cudaStream_t s) {
+  k_refine_accum<<<nblk, BLOCK, 0, s>>>(b);
+  count_launch();
+}
+
+}  // namespace qp

@@ -1,0 +1,551 @@
+// Taps backend: the compressed mat-vec of Sec. 4.2 as a direct stencil over the coefficient's Fourier modes,
+//   (Q h)(k) = sum_t lambda(k)^T C_t lambda(k -N m_t) h(k -N m_t),   lambda(k) = P k,
+// (eq. n-discrete_equation; App. D for a matrix coefficient), the diagonal preconditioners (Sec. 4.3), the
+// corrector right-hand side (Sec. 5.2) and the a* reduction (eq. homcoefficient) on this representation.
+//
+// Work is split in chunks of consecutive modes of one unit (a plan and its right-hand sides); each chunk's
+// partial sums go to a fixed slot and the block that completes a unit sums them in a fixed order
+// (deterministic, no floating-point atomics). Modes are decoded with multiply-shift division; star taps (one
+// nonzero axis) are grouped per axis so that each costs one wrap test, one index update and, for a scalar
+// coefficient, one fused multiply-add for the weight: lambda(k).lambda(k') = |lambda(k)|^2 + dk (lambda(k).P_j).
+#include "qp_device.cuh"
+
+namespace qp {
+
+template <typename T>
+__device__ __forceinline__ void load_plan(const PlanDev* src, PlanDev& dst, cplx<T>* coef) {
+  __syncthreads();
+  const int4* s = reinterpret_cast<const int4*>(src);
+  int4* d = reinterpret_cast<int4*>(&dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(PlanDev) / sizeof(int4)); i += BLOCK) d[i] = s[i];
+  __syncthreads();
+  const int nc = dst.ntaps * dst.ncomp;
+  if (sizeof(T) == 8) {
+    const double2* c = dst.coef64;
+    for (int i = threadIdx.x; i < nc; i += BLOCK) reinterpret_cast<double2*>(coef)[i] = c[i];
+  } else {
+    const float2* c = dst.coef32;
+    for (int i = threadIdx.x; i < nc; i += BLOCK) reinterpret_cast<float2*>(coef)[i] = c[i];
+  }
+  __syncthreads();
+}
+
+template <typename T, bool REALC>
+__device__ __forceinline__ void mac(cplx<T>& acc, const cplx<T>& c, const cplx<T>& hv) {
+  if (REALC) {
+    acc.x = fma(c.x, hv.x, acc.x);
+    acc.y = fma(c.x, hv.y, acc.y);
+  } else {
+    acc.x = fma(c.x, hv.x, fma(-c.y, hv.y, acc.x));
+    acc.y = fma(c.x, hv.y, fma(c.y, hv.x, acc.y));
+  }
+}
+
+// acc[r] = (Q h_r)(e) for r < nrhs: the whole tap sum at one mode.
+template <typename T, bool REALC, int NR>
+__device__ __forceinline__ void apply_point(const PlanDev& p, const cplx<T>* __restrict__ sc, int e,
+                                            const cplx<T>* __restrict__ h, int D, int nrhs, cplx<T> (&acc)[NR]) {
+  int ib[MAXN], k[MAXN];
+  mode_digits(p, e, ib, k);
+  const int d = p.d, kind = p.kind, nc = p.ncomp;
+  T lk[MAXD];
+#pragma unroll
+  for (int a = 0; a < MAXD; ++a) {
+    lk[a] = T(0);
+#pragma unroll
+    for (int j = 0; j < MAXN; ++j)
+      if (a < d && j < p.n) lk[a] = fma(pcoef<T>(p, a, j), (T)k[j], lk[a]);
+  }
+  const bool scalar = (kind == QP_COEF_SCALAR);
+  T lam2 = T(0), lp[MAXN];
+#pragma unroll
+  for (int a = 0; a < MAXD; ++a)
+    if (a < d) lam2 = fma(lk[a], lk[a], lam2);
+#pragma unroll
+  for (int j = 0; j < MAXN; ++j) {
+    lp[j] = T(0);
+    if (scalar && j < p.n) {
+#pragma unroll
+      for (int a = 0; a < MAXD; ++a)
+        if (a < d) lp[j] = fma(lk[a], pcoef<T>(p, a, j), lp[j]);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < NR; ++r) acc[r] = mk<T>(0, 0);
+
+  // mean tap (sorted index 0): k' = k
+  {
+    cplx<T> c;
+    if (scalar) {
+      c.x = sc[0].x * lam2;
+      c.y = REALC ? T(0) : sc[0].y * lam2;
+    } else {
+      c = weight_general<T>(kind, d, sc, lk, lk);
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+      if (r < nrhs) mac<T, REALC>(acc[r], c, h[(size_t)r * D + e]);
+  }
+  // star taps, grouped by axis
+#pragma unroll
+  for (int j = 0; j < MAXN; ++j) {
+    if (j < p.n) {
+      const int Nj = p.N[j], sj = p.stride[j];
+      const int t1 = p.star_begin[j + 1];
+      for (int t = p.star_begin[j]; t < t1; ++t) {
+        int ib2 = ib[j] - (int)p.m[t][j];
+        ib2 += (ib2 < 0) ? Nj : 0;
+        ib2 -= (ib2 >= Nj) ? Nj : 0;
+        const int e2 = e + (ib2 - ib[j]) * sj;
+        const int k2 = (2 * ib2 < Nj) ? ib2 : ib2 - Nj;
+        const T dk = (T)(k2 - k[j]);
+        cplx<T> c;
+        if (scalar) {
+          const T s = fma(dk, lp[j], lam2);
+          c.x = sc[t].x * s;
+          c.y = REALC ? T(0) : sc[t].y * s;
+        } else {
+          T l2[MAXD];
+#pragma unroll
+          for (int a = 0; a < MAXD; ++a) l2[a] = (a < d) ? fma(dk, pcoef<T>(p, a, j), lk[a]) : T(0);
+          c = weight_general<T>(kind, d, sc + t * nc, lk, l2);
+        }
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+          if (r < nrhs) mac<T, REALC>(acc[r], c, h[(size_t)r * D + e2]);
+      }
+    }
+  }
+  // taps with several nonzero axes
+  for (int t = p.star_begin[p.n]; t < p.ntaps; ++t) {
+    int e2 = e;
+    T l2[MAXD];
+#pragma unroll
+    for (int a = 0; a < MAXD; ++a) l2[a] = lk[a];
+#pragma unroll
+    for (int j = 0; j < MAXN; ++j) {
+      const int mj = (j < p.n) ? (int)p.m[t][j] : 0;
+      if (mj != 0) {
+        const int Nj = p.N[j];
+        int ib2 = ib[j] - mj;
+        ib2 += (ib2 < 0) ? Nj : 0;
+        ib2 -= (ib2 >= Nj) ? Nj : 0;
+        e2 += (ib2 - ib[j]) * p.stride[j];
+        const int k2 = (2 * ib2 < Nj) ? ib2 : ib2 - Nj;
+        const T dk = (T)(k2 - k[j]);
+#pragma unroll
+        for (int a = 0; a < MAXD; ++a)
+          if (a < d) l2[a] = fma(dk, pcoef<T>(p, a, j), l2[a]);
+      }
+    }
+    const cplx<T> c = weight_general<T>(kind, d, sc + t * nc, lk, l2);
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+      if (r < nrhs) mac<T, REALC>(acc[r], c, h[(size_t)r * D + e2]);
+  }
+}
+
+// ------------------------------------------------------------------------------------------------ batch apply
+
+template <typename T, int EPI, bool REALC, int NR>
+__global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 3) k_apply(BatchDev b, int level, int refine,
+                                                                       unsigned long long cond) {
+  __shared__ __align__(16) PlanDev sp;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cplx<T>* scoef = reinterpret_cast<cplx<T>*>(smraw);
+  const PlanDev* cur = nullptr;
+  for (int c = blockIdx.x; c < b.nchunks; c += gridDim.x) {
+    const int u = b.chunk_unit[c];
+    const UnitDev& un = b.units[u];
+    RhsSt* st = b.st + (size_t)u * MAXR;
+    const int nrhs = un.nrhs;
+    // skip units with nothing left to do at this level (same decision for every chunk of the unit)
+    bool active = false;
+    for (int r = 0; r < nrhs; ++r) {
+      if (EPI == EPI_DOT_HW) active |= !ld_int(&st[r].done);
+      else if (EPI == EPI_RESIDUAL && refine) active |= !ld_int(&st[r].odone);
+      else active = true;
+    }
+    if (!active) continue;
+    if (un.plan != cur) {
+      cur = un.plan;
+      load_plan<T>(cur, sp, scoef);
+    }
+    const int D = un.D;
+    const cplx<T>* src;
+    cplx<T>* dst;
+    if (level == LEVEL_FP32) {
+      src = reinterpret_cast<const cplx<T>*>(un.h32);
+      dst = reinterpret_cast<cplx<T>*>(un.w32);
+    } else {
+      src = reinterpret_cast<const cplx<T>*>(EPI == EPI_DOT_HW ? (const double2*)un.h : (const double2*)un.U);
+      dst = reinterpret_cast<cplx<T>*>(un.w);
+    }
+    const cplx<T>* F = reinterpret_cast<const cplx<T>*>(un.F);
+    const bool fft_unit = (sp.backend == QP_BACKEND_FFT);
+    constexpr int NV = (EPI == EPI_RESIDUAL) ? 2 * NR : NR;   // reduced quantities: (h,w) or (|F-w|^2, |F|^2)
+    double v[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[q] = 0.0;
+    const int base = (c - un.chunk0) * b.chunk;
+    const int end = min(base + b.chunk, D);
+    for (int e = base + threadIdx.x; e < end; e += BLOCK) {
+      cplx<T> acc[NR];
+      if (fft_unit) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) acc[r] = (r < nrhs) ? dst[(size_t)r * D + e] : mk<T>(0, 0);
+      } else {
+        apply_point<T, REALC, NR>(sp, scoef, e, src, D, nrhs, acc);
+      }
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        if (r < nrhs) {
+          const size_t o = (size_t)r * D + e;
+          if (EPI == EPI_DOT_HW) {
+            if (!fft_unit) dst[o] = acc[r];
+            const cplx<T> hv = src[o];
+            v[r] += (double)hv.x * (double)acc[r].x + (double)hv.y * (double)acc[r].y;
+          } else if (EPI == EPI_RESIDUAL) {
+            const cplx<T> f = F[o];
+            const cplx<T> res = (e == 0) ? mk<T>(0, 0) : mk<T>(f.x - acc[r].x, f.y - acc[r].y);
+            dst[o] = res;
+            v[2 * r] += (double)res.x * res.x + (double)res.y * res.y;
+            if (e != 0) v[2 * r + 1] += (double)f.x * f.x + (double)f.y * f.y;
+          } else {
+            if (!fft_unit) dst[o] = acc[r];
+          }
+        }
+      }
+    }
+    if (EPI == EPI_NONE) continue;
+    block_reduce<NV>(v);
+    if (!chunk_arrive<NV>(b, c, u, v)) continue;
+    // this block completes unit u: finalize its right-hand sides
+    unit_sums<NV>(b, un, v);
+    for (int r = 0; r < nrhs && r < NR; ++r) {
+      const double s0 = (EPI == EPI_RESIDUAL) ? v[2 * r] : v[r];
+      const double s1 = (EPI == EPI_RESIDUAL) ? v[(2 * r + 1) % NV] : 0.0;
+      if (threadIdx.x == 0) {
+        RhsSt& x = st[r];
+        if (EPI == EPI_DOT_HW) {
+          if (!x.done) {
+            x.hw = s0;
+            if (!(s0 > 0.0) || !isfinite(s0)) {   // (h, Q h) <= 0 or NaN: breakdown
+              x.done = 1;
+              x.status = QP_ERR_BREAKDOWN;
+              atomicAdd(&b.ndone[0], 1);
+            } else {
+              x.alpha = x.rz / s0;
+            }
+          }
+        } else if (!refine) {
+          x.orr = s0;
+          x.of2 = s1;
+        } else if (!x.odone) {
+          x.orr = s0;
+          x.of2 = s1;
+          x.outer += 1;
+          x.inner_total += x.iters;
+          const double rel = s1 > 0.0 ? sqrt(s0 / s1) : 0.0;
+          int od = 0, os = QP_ERR_NO_CONVERGENCE;
+          if (s1 == 0.0 || s0 <= b.otol2 * s1) {
+            od = 1;
+            os = QP_OK;
+          } else if (!isfinite(rel)) {
+            od = 1;
+            os = QP_ERR_BREAKDOWN;
+          } else if (rel > 0.9 * x.prev_rel || x.outer > b.max_outer || x.inner_total >= b.maxit) {
+            od = 1;   // stagnation or cap
+          }
+          x.prev_rel = rel;
+          x.inv_scale = sqrt(s0);
+          x.scale = s0 > 0.0 ? 1.0 / x.inv_scale : 0.0;
+          x.ostatus = os;
+          if (od) {
+            x.odone = 1;
+            atomicAdd(&b.ndone[1], 1);
+          }
+        }
+      }
+    }
+    if (threadIdx.x == 0) b.ucount[u] = 0;
+  }
+  if (EPI == EPI_NONE) return;
+  if (kernel_arrive(b) && threadIdx.x == 0) {
+    if (EPI == EPI_RESIDUAL && refine) {
+      // the outer loop continues while some right-hand side refines; its counter bounds the WHILE node
+      const int loops = ++b.ndone[3];
+      if (cond != 0ull)
+        cudaGraphSetConditional(cond, (ld_int(&b.ndone[1]) < b.nslots && loops <= b.max_outer + 1) ? 1u : 0u);
+    }
+    *b.kcount = 0;
+  }
+}
+
+template <typename T, int EPI, int NR>
+static void apply_launch_nr(bool realc, const BatchDev& b, int level, int refine, unsigned long long cond, int nblk,
+                            size_t smem, cudaStream_t s) {
+  if (realc) k_apply<T, EPI, true, NR><<<nblk, BLOCK, smem, s>>>(b, level, refine, cond);
+  else k_apply<T, EPI, false, NR><<<nblk, BLOCK, smem, s>>>(b, level, refine, cond);
+}
+
+template <typename T, int EPI>
+static void apply_launch_real(bool realc, int maxr, const BatchDev& b, int level, int refine,
+                              unsigned long long cond, int nblk, size_t smem, cudaStream_t s) {
+  switch (maxr) {
+    case 1: apply_launch_nr<T, EPI, 1>(realc, b, level, refine, cond, nblk, smem, s); break;
+    case 2: apply_launch_nr<T, EPI, 2>(realc, b, level, refine, cond, nblk, smem, s); break;
+    case 3: apply_launch_nr<T, EPI, 3>(realc, b, level, refine, cond, nblk, smem, s); break;
+    default: apply_launch_nr<T, EPI, 4>(realc, b, level, refine, cond, nblk, smem, s); break;
+  }
+}
+
+// realc: every taps plan of the batch has real tap values; mc: the largest ntaps * ncomp of its plans (sizes
+// the shared coefficient table); maxr: the largest nrhs of its units.
+void launch_apply(const BatchDev& b, bool realc, int mc, int maxr, int level, int epi, bool refine,
+                  unsigned long long cond, int nblk, cudaStream_t s) {
+  if (level == LEVEL_FP32) {
+    const size_t smem = (size_t)mc * sizeof(float2);
+    apply_launch_real<float, EPI_DOT_HW>(realc, maxr, b, level, refine, cond, nblk, smem, s);
+  } else {
+    const size_t smem = (size_t)mc * sizeof(double2);
+    if (epi == EPI_DOT_HW) apply_launch_real<double, EPI_DOT_HW>(realc, maxr, b, level, refine, cond, nblk, smem, s);
+    else if (epi == EPI_RESIDUAL)
+      apply_launch_real<double, EPI_RESIDUAL>(realc, maxr, b, level, refine, cond, nblk, smem, s);
+    else apply_launch_real<double, EPI_NONE>(realc, maxr, b, level, refine, cond, nblk, smem, s);
+  }
+  count_launch();
+}
+
+// ------------------------------------------------------------------------------------------------ plain apply
+
+template <typename T, bool REALC, int NR>
+__global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 3) k_apply_plain(const PlanDev* plan, int D, int nrhs,
+                                                                             const cplx<T>* h, cplx<T>* w) {
+  __shared__ __align__(16) PlanDev sp;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cplx<T>* scoef = reinterpret_cast<cplx<T>*>(smraw);
+  load_plan<T>(plan, sp, scoef);
+  const int e = blockIdx.x * BLOCK + threadIdx.x;   // one mode per thread: blocks sweep memory in order
+  if (e >= D) return;
+  cplx<T> acc[NR];
+  apply_point<T, REALC, NR>(sp, scoef, e, h, D, nrhs, acc);
+#pragma unroll
+  for (int r = 0; r < NR; ++r)
+    if (r < nrhs) w[(size_t)r * D + e] = acc[r];
+}
+
+template <typename T, bool REALC>
+static void plain_nr(int nrhs, const PlanDev* plan_dev, int D, const cplx<T>* h, cplx<T>* w, int nblk, size_t smem,
+                     cudaStream_t s) {
+  switch (nrhs) {
+    case 1: k_apply_plain<T, REALC, 1><<<nblk, BLOCK, smem, s>>>(plan_dev, D, nrhs, h, w); break;
+    case 2: k_apply_plain<T, REALC, 2><<<nblk, BLOCK, smem, s>>>(plan_dev, D, nrhs, h, w); break;
+    case 3: k_apply_plain<T, REALC, 3><<<nblk, BLOCK, smem, s>>>(plan_dev, D, nrhs, h, w); break;
+    default: k_apply_plain<T, REALC, 4><<<nblk, BLOCK, smem, s>>>(plan_dev, D, nrhs, h, w); break;
+  }
+}
+
+template <typename T>
+void launch_apply_plain(const PlanDev* plan_dev, bool realc, int mc, int D, int nrhs, const cplx<T>* h, cplx<T>* w,
+                        cudaStream_t s) {
+  const size_t smem = (size_t)mc * sizeof(cplx<T>);
+  const int nblk = (D + BLOCK - 1) / BLOCK;
+  if (realc) plain_nr<T, true>(nrhs, plan_dev, D, h, w, nblk, smem, s);
+  else plain_nr<T, false>(nrhs, plan_dev, D, h, w, nblk, smem, s);
+  count_launch();
+}
+template void launch_apply_plain<double>(const PlanDev*, bool, int, int, int, const double2*, double2*, cudaStream_t);
+template void launch_apply_plain<float>(const PlanDev*, bool, int, int, int, const float2*, float2*, cudaStream_t);
+
+// ------------------------------------------------------------------------------------------------ set-up kernels
+
+// lambda(k + m) for the tap with mode m (any number of nonzero axes), from the digits of k.
+__device__ __forceinline__ void lambda_shift(const PlanDev& p, const int (&ib)[MAXN], const int (&k)[MAXN],
+                                             const signed char* m, int sign, const double (&lk)[MAXD],
+                                             double (&out)[MAXD]) {
+#pragma unroll
+  for (int a = 0; a < MAXD; ++a) out[a] = lk[a];
+#pragma unroll
+  for (int j = 0; j < MAXN; ++j) {
+    const int mj = (j < p.n) ? sign * (int)m[j] : 0;
+    if (mj != 0) {
+      const int Nj = p.N[j];
+      int ib2 = ib[j] + mj;
+      ib2 += (ib2 < 0) ? Nj : 0;
+      ib2 -= (ib2 >= Nj) ? Nj : 0;
+      const int k2 = (2 * ib2 < Nj) ? ib2 : ib2 - Nj;
+#pragma unroll
+      for (int a = 0; a < MAXD; ++a)
+        if (a < p.d) out[a] = fma((double)(k2 - k[j]), p.P[a][j], out[a]);
+    }
+  }
+}
+
+// Jacobi diagonal q(k) = lambda(k)^T A~_0 lambda(k) and the Frobenius-optimal diagonal q(k) / ||Q e_k||^2
+// (eq. preconditioner) with ||Q e_k||^2 = sum_t |lambda(k +N m_t)^T C_t lambda(k)|^2 (O(gD), Sec. 4.3).
+// Stored as M (z = M r), M(0) = 0. out[0] = min over k != 0 of |lambda(k)|^2, out[1] = min q / |lambda|^2.
+__global__ void __launch_bounds__(BLOCK) k_diag(const PlanDev* plan, int D, double* jac, double* frob, float* jac32,
+                                                float* frob32, double* partials, unsigned* counter, double* out) {
+  __shared__ __align__(16) PlanDev sp;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double2* scoef = reinterpret_cast<double2*>(smraw);
+  load_plan<double>(plan, sp, scoef);
+  const int d = sp.d;
+  double red[2] = {DBL_MAX, DBL_MAX};
+  for (int e = blockIdx.x * BLOCK + threadIdx.x; e < D; e += gridDim.x * BLOCK) {
+    int ib[MAXN], k[MAXN];
+    mode_digits(sp, e, ib, k);
+    double lk[MAXD] = {0, 0, 0};
+    for (int a = 0; a < d; ++a)
+      for (int j = 0; j < sp.n; ++j) lk[a] = fma(sp.P[a][j], (double)k[j], lk[a]);
+    double l2sum = 0.0;
+    for (int a = 0; a < d; ++a) l2sum += lk[a] * lk[a];
+    const double q = weight_general<double>(sp.kind, d, scoef, lk, lk).x;
+    double cn = 0.0;
+    for (int t = 0; t < sp.ntaps; ++t) {
+      double lv[MAXD];
+      lambda_shift(sp, ib, k, sp.m[t], +1, lk, lv);
+      const double2 c = weight_general<double>(sp.kind, d, scoef + t * sp.ncomp, lv, lk);
+      cn += c.x * c.x + c.y * c.y;
+    }
+    double mj = 0.0, mf = 0.0;
+    if (e != 0) {
+      mj = q != 0.0 ? 1.0 / q : 0.0;
+      mf = cn > 0.0 ? q / cn : 0.0;
+      red[0] = fmin(red[0], l2sum);
+      red[1] = fmin(red[1], l2sum > 0.0 ? q / l2sum : -1.0);
+    }
+    jac[e] = mj;
+    frob[e] = mf;
+    jac32[e] = (float)mj;
+    frob32[e] = (float)mf;
+  }
+  block_reduce<2, true>(red);
+  __shared__ int is_last;
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = red[0];
+    partials[gridDim.x + blockIdx.x] = red[1];
+    __threadfence();
+    is_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  for (int q = 0; q < 2; ++q) {
+    double v[1] = {DBL_MAX};
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += BLOCK) v[0] = fmin(v[0], __ldcg(partials + q * gridDim.x + i));
+    block_reduce<1, true>(v);
+    if (threadIdx.x == 0) out[q] = v[0];
+  }
+  if (threadIdx.x == 0) *counter = 0;
+}
+
+void launch_diag(const PlanDev* plan_dev, int mc, int D, double* jac, double* frob, float* jac32, float* frob32,
+                 double* partials, unsigned* counter, double* out, int nblk, cudaStream_t s) {
+  const size_t smem = (size_t)mc * sizeof(double2);
+  k_diag<<<nblk, BLOCK, smem, s>>>(plan_dev, D, jac, frob, jac32, frob32, partials, counter, out);
+  count_launch();
+}
+
+// Corrector right-hand sides on the taps backend: F_j = 0 except at the tap modes m != 0, where
+// F_j(m) = i sum_a lambda_a(m) A~^{aj}_m (Sec. 5.2 eq. corrector; App. D). F is zeroed beforehand.
+__global__ void __launch_bounds__(BLOCK) k_rhs_taps(const PlanDev* plan, int j0, int nrhs, int D, double2* F) {
+  __shared__ __align__(16) PlanDev sp;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double2* scoef = reinterpret_cast<double2*>(smraw);
+  load_plan<double>(plan, sp, scoef);
+  const PlanDev& p = sp;
+  for (int idx = threadIdx.x; idx < p.ntaps * nrhs; idx += BLOCK) {
+    const int t = idx % p.ntaps, jj = idx / p.ntaps, j = j0 + jj;
+    if (t == 0) continue;                      // the mean mode: F(0) = 0
+    int e = 0;
+    double lm[MAXD] = {0, 0, 0};
+    for (int ax = 0; ax < p.n; ++ax) {
+      const int mj = p.m[t][ax];
+      e += (mj < 0 ? mj + p.N[ax] : mj) * p.stride[ax];
+      for (int a = 0; a < p.d; ++a) lm[a] = fma(p.P[a][ax], (double)mj, lm[a]);
+    }
+    const double2* ct = scoef + (size_t)t * p.ncomp;
+    double2 z = mk<double>(0, 0);
+    for (int a = 0; a < p.d; ++a) {
+      double2 c;
+      if (p.kind == QP_COEF_SCALAR) c = (a == j) ? ct[0] : mk<double>(0, 0);
+      else if (p.kind == QP_COEF_DIAG) c = (a == j) ? ct[a] : mk<double>(0, 0);
+      else c = ct[sym_idx(a, j, p.d)];
+      z.x += lm[a] * c.x;
+      z.y += lm[a] * c.y;
+    }
+    F[(size_t)jj * D + e] = mk<double>(-z.y, z.x);   // i * z
+  }
+}
+
+void launch_rhs_taps(const PlanDev* plan_dev, int mc, int j0, int nrhs, int D, double2* F, cudaStream_t s) {
+  k_rhs_taps<<<1, BLOCK, (size_t)mc * sizeof(double2), s>>>(plan_dev, j0, nrhs, D, F);
+  count_launch();
+}
+
+// A*_ij = A~^{ij}_0 + i sum_k sum_b A~^{ib}_{-k} lambda_b(k) U_j(k): on the taps backend only k = -m_t
+// contribute. One thread per tap computes its d x d terms; a fixed-order block reduction sums them.
+// out: (re, im) per entry, row-major.
+__global__ void __launch_bounds__(BLOCK) k_astar_taps(const PlanDev* plan, int D, const double2* __restrict__ U,
+                                                      double* out) {
+  __shared__ __align__(16) PlanDev sp;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double2* scoef = reinterpret_cast<double2*>(smraw);
+  load_plan<double>(plan, sp, scoef);
+  const PlanDev& p = sp;
+  const int d = p.d;
+  auto cab = [&](int t, int a, int b) -> double2 {
+    const double2* ct = scoef + (size_t)t * p.ncomp;
+    if (p.kind == QP_COEF_SCALAR) return (a == b) ? ct[0] : mk<double>(0, 0);
+    if (p.kind == QP_COEF_DIAG) return (a == b) ? ct[a] : mk<double>(0, 0);
+    return ct[sym_idx(a, b, d)];
+  };
+  double v[2 * MAXD * MAXD];
+#pragma unroll
+  for (int q = 0; q < 2 * MAXD * MAXD; ++q) v[q] = 0.0;
+  for (int t = 1 + threadIdx.x; t < p.ntaps; t += BLOCK) {
+    int e = 0;
+    double lneg[MAXD] = {0, 0, 0};   // lambda(-m_t)
+    for (int ax = 0; ax < p.n; ++ax) {
+      const int mj = -(int)p.m[t][ax];
+      e += (mj < 0 ? mj + p.N[ax] : mj) * p.stride[ax];
+      for (int a = 0; a < d; ++a) lneg[a] = fma(p.P[a][ax], (double)mj, lneg[a]);
+    }
+#pragma unroll
+    for (int i = 0; i < MAXD; ++i) {
+#pragma unroll
+      for (int j = 0; j < MAXD; ++j) {
+        if (i < d && j < d) {
+          double2 sm = mk<double>(0, 0);
+          for (int b = 0; b < d; ++b) {
+            const double2 c = cab(t, i, b);
+            sm.x += c.x * lneg[b];
+            sm.y += c.y * lneg[b];
+          }
+          const double2 u = U[(size_t)j * D + e];
+          const double pr = sm.x * u.x - sm.y * u.y, pim = sm.x * u.y + sm.y * u.x;
+          v[2 * (i * MAXD + j)] += -pim;   // i * (s u)
+          v[2 * (i * MAXD + j) + 1] += pr;
+        }
+      }
+    }
+  }
+  block_reduce<2 * MAXD * MAXD>(v);
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < d; ++i)
+      for (int j = 0; j < d; ++j) {
+        const double2 c0 = cab(0, i, j);
+        out[2 * (i * d + j)] = c0.x + v[2 * (i * MAXD + j)];
+        out[2 * (i * d + j) + 1] = c0.y + v[2 * (i * MAXD + j) + 1];
+      }
+  }
+}
+
+void launch_astar_taps(const PlanDev* plan_dev, int mc, int D, const double2* U, double* out, cudaStream_t s) {
+  k_astar_taps<<<1, BLOCK, (size_t)mc * sizeof(double2), s>>>(plan_dev, D, U, out);
+  count_launch();
+}
+
+}  // namespace qp

@@ -388,3 +388,14 @@ def test_corrector_rhs_and_flux_formula_against_grid_definitions():
             grad = [np.fft.ifftn(1j * lam[b] * Us[j]) * D for b in range(2)]
             val = np.mean(Agrid[i, j] + sum(Agrid[i, b] * grad[b] for b in range(2)))
             assert abs(Ac[i, j] - val) <= 1e-12 * abs(val)
+
+
+def test_pointwise_apply_matches_vectorised_convolution():
+    """apply_taps_at (used for sampled checks at full size) agrees with the vectorised convolution."""
+    inst = W.random_instance(2, 3, (6, 4, 8), "sym", "taps", seed=17)
+    rng = np.random.default_rng(1)
+    h = rng.standard_normal(inst.N) + 1j * rng.standard_normal(inst.N)
+    w = O.apply_convolution(inst.P, inst.N, O.coefficient_modes(inst), h)
+    pts = [tuple(int(rng.integers(0, Nj)) for Nj in inst.N) for _ in range(20)] + [(0, 0, 0), (5, 3, 7), (3, 2, 4)]
+    wp = O.apply_taps_at(inst.P, inst.N, inst.coeff.taps_k, inst.coeff.taps_val, "sym", h, pts)
+    assert np.abs(wp - np.array([w[p] for p in pts])).max() <= 1e-12 * np.abs(w).max()
