@@ -448,7 +448,7 @@ void record_apply(const Units& us, const Entry& en, int level, int epi, bool ref
 }
 
 void body_pcg(const Units& us, const Entry& en, int level, unsigned long long cond, cudaStream_t s) {
-  record_apply(us, en, level, EPI_DOT_HW, false, 0, s);
+  record_apply(us, en, level, EPI_DOT_HW, false, cond, s);
   launch_pcg_update(en.bd, us.max_rhs, level, cond, en.nblk, s);
   launch_pcg_hupdate(en.bd, us.max_rhs, level, en.nblk, s);
   CK_LAUNCH();
@@ -632,10 +632,7 @@ Entry& get_entry(Solver* sv, const Units& us, const Key& key) {
     E += us.plans[u]->D;
     nslots += us.nrhs[u];
   }
-  // one chunk per block, blocks dispatched in index order so that the resident blocks cover a contiguous window
-  // of modes (neighbour reads along outer axes then hit L2); about 16 chunks per SM, 256 to 8192 modes each
-  int64_t chunk = (E / (152 * 16) + BLOCK - 1) / BLOCK * BLOCK;
-  chunk = std::max<int64_t>(BLOCK, std::min<int64_t>(chunk, 8192));
+  (void)E;
   std::vector<UnitDev> units(nu);
   std::vector<int> chunk_unit;
   for (int u = 0; u < nu; ++u) {
@@ -645,6 +642,11 @@ Entry& get_entry(Solver* sv, const Units& us, const Key& key) {
     x.plan = p->pd;
     x.D = p->D;
     x.nrhs = us.nrhs[u];
+    // one chunk per block, blocks dispatched in index order so that the resident blocks cover a contiguous
+    // window of modes (neighbour reads along outer axes then hit L2); the chunk depends on D only (about 8
+    // chunks per SM, 256 to 8192 modes), so the reduction order of a unit does not depend on its batch
+    const int64_t chunk = std::max<int64_t>(BLOCK, std::min<int64_t>(8192, (p->D / (152 * 8) + BLOCK - 1) / BLOCK * BLOCK));
+    x.chunk = (int)chunk;
     x.chunk0 = (int)chunk_unit.size();
     x.nchunk = (int)((p->D + chunk - 1) / chunk);
     for (int c = 0; c < x.nchunk; ++c) chunk_unit.push_back(u);
@@ -672,9 +674,10 @@ Entry& get_entry(Solver* sv, const Units& us, const Key& key) {
   BatchDev& bd = en->bd;
   bd.nunits = nu;
   bd.nchunks = nchunks;
-  bd.chunk = (int)chunk;
   bd.nslots = nslots;
   bd.units = (const UnitDev*)up(units.data(), units.size() * sizeof(UnitDev));
+  bd.single = nu == 1 ? 1 : 0;
+  bd.pu = units[0];
   bd.st = sv->st;
   bd.chunk_unit = (const int*)up(chunk_unit.data(), chunk_unit.size() * sizeof(int));
   {

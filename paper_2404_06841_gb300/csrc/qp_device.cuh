@@ -49,6 +49,37 @@ __device__ __forceinline__ void block_reduce(double (&v)[NV]) {
   }
 }
 
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block sum of per-thread partials held in the vector precision T: the 32 lanes of a warp are summed in T
+// (a fixed 5-level tree), the warp sums are converted to FP64 and summed in FP64 (fixed order); thread 0
+// gets the results in out. For T = float this keeps FP64 work to one conversion per warp and value while the
+// accumulation above the warp level stays FP64.
+template <typename T, int NV>
+__device__ __forceinline__ void block_reduce_mixed(T (&v)[NV], double (&out)[NV]) {
+  __shared__ double sm[NV][BLOCK / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    if (sizeof(T) == 4) v[q] = (T)warp_sum_f((float)v[q]);
+    else v[q] = (T)warp_sum((double)v[q]);
+  }
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) sm[q][wid] = (double)v[q];
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) out[q] = warp_sum(lane < BLOCK / 32 ? sm[q][lane] : 0.0);
+  }
+}
+
 __device__ __forceinline__ uint32_t fdiv(uint32_t x, const FastDiv& f) {
   return (uint32_t)(((uint64_t)x * f.m) >> f.p);
 }
@@ -121,6 +152,10 @@ __device__ __forceinline__ cplx<T> weight_general(int kind, int d, const cplx<T>
   return r;
 }
 
+// The unit a chunk belongs to, and its description (kernel parameter for a single unit, else the table).
+__device__ __forceinline__ int unit_of_chunk(const BatchDev& b, int c) { return b.single ? 0 : b.chunk_unit[c]; }
+__device__ __forceinline__ const UnitDev& unit_at(const BatchDev& b, int u) { return b.single ? b.pu : b.units[u]; }
+
 // Record this block's chunk partials (thread 0 holds them in v), count the chunk's arrival for its unit and
 // return true in the block that completes the unit (all its chunks are in).
 template <int NV>
@@ -130,7 +165,7 @@ __device__ __forceinline__ bool chunk_arrive(const BatchDev& b, int c, int u, co
 #pragma unroll
     for (int q = 0; q < NV; ++q) b.partials[(size_t)q * b.nchunks + c] = v[q];
     __threadfence();
-    s_last = (atomicAdd(&b.ucount[u], 1u) == (unsigned)b.units[u].nchunk - 1u);
+    s_last = (atomicAdd(&b.ucount[u], 1u) == (unsigned)unit_at(b, u).nchunk - 1u);
   }
   __syncthreads();
   const bool last = s_last != 0;
@@ -150,18 +185,12 @@ __device__ __forceinline__ void unit_sums(const BatchDev& b, const UnitDev& un, 
   block_reduce<NV>(v);
 }
 
-// Last block of the kernel to finish (one integer atomic per block).
-__device__ __forceinline__ bool kernel_arrive(const BatchDev& b) {
-  __shared__ int s_last;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    s_last = (atomicAdd(b.kcount, 1u) == gridDim.x - 1u);
-  }
-  __syncthreads();
-  const bool last = s_last != 0;
-  if (last) __threadfence();
-  return last;
+// Counts "n" newly finished right-hand sides into ndone[which]; when the count reaches every right-hand
+// side, ends the WHILE loop driven by "cond" (the one call that completes the count sets it).
+__device__ __forceinline__ void count_done(const BatchDev& b, int which, int n, unsigned long long cond) {
+  if (n == 0) return;
+  const int before = atomicAdd(&b.ndone[which], n);
+  if (cond != 0ull && before + n >= b.nslots) cudaGraphSetConditional(cond, 0u);
 }
 
 __device__ __forceinline__ int ld_int(const int* p) { return *((volatile const int*)p); }

@@ -74,6 +74,7 @@ static_assert(sizeof(PlanDev) % 16 == 0, "PlanDev is copied to shared memory in 
 struct UnitDev {
   const PlanDev* plan;
   int D, nrhs, chunk0, nchunk;
+  int chunk, pad_[3];  // modes per chunk: a function of D only, so a unit reduces in the same order alone or batched
   const double2* F;   // right-hand side (FP64)
   double2* U;         // solution (FP64)
   double2* r;         // FP64 PCG residual
@@ -98,15 +99,16 @@ struct RhsSt {
 };
 
 struct BatchDev {
-  int nunits, nchunks, chunk, nslots;   // chunk = elements per chunk (multiple of BLOCK)
+  int nunits, nchunks, nslots, pad0_;
+  int single, pad_[3];                  // single: one unit, whose description is "pu" (kernel parameter)
+  UnitDev pu;
   const UnitDev* units;
   RhsSt* st;                            // [nunits * MAXR]
   const int* chunk_unit;                // [nchunks]
   double* partials;                     // [NSLOT][nchunks]
   unsigned* ucount;                     // [nunits] chunk arrivals per unit
-  unsigned* kcount;                     // [1] block arrivals per kernel
-  int* ndone;                           // [4]: right-hand sides done at the PCG level, at the outer level;
-                                        //      loop counts of the PCG and the outer loop
+  unsigned* kcount;                     // [1] units finalized by the current kernel
+  int* ndone;                           // [2]: right-hand sides done at the PCG level, at the outer level
   double tol2, otol2;                   // PCG-level and outer (refinement) tolerances, squared
   int maxit, max_outer;
 };
@@ -118,7 +120,8 @@ enum { LEVEL_FP64 = 0, LEVEL_FP32 = 1 };   // which vector set a PCG kernel work
 // Apply over every chunk of the batch (taps units only; FFT units get their w from the FFT passes and only
 // the epilogue here). level LEVEL_FP64: EPI_DOT_HW reads h and writes w; EPI_RESIDUAL reads U and writes
 // w = F - Q U; LEVEL_FP32: EPI_DOT_HW reads h32 and writes w32. refine: EPI_RESIDUAL runs the outer
-// (refinement) bookkeeping and sets the graph conditional cond (0 = none) while some rhs is not outer-done.
+// (refinement) bookkeeping. cond (0 = none): the graph conditional of the loop this apply belongs to; it is
+// set to 0 by the call that completes the count of finished right-hand sides.
 // realc: every taps plan in the batch has real tap values; mc: largest ntaps * ncomp over its taps plans.
 // maxr: the largest nrhs of the batch's units.
 void launch_apply(const BatchDev& b, bool realc, int mc, int maxr, int level, int epi, bool refine,

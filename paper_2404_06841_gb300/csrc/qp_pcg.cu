@@ -6,7 +6,8 @@
 //                ||r||^2; beta = (r', z') / (r, z); convergence ||r|| <= tol ||F||;
 //   pcg_hupdate: h = M r + beta h.
 // z = M r is recomputed where needed instead of stored (the preconditioner is diagonal). Dot products are
-// accumulated in FP64 whatever the vector precision. The update kernel's last block sets the CUDA-graph
+// accumulated in FP64 above the warp level whatever the vector precision (FP32 vectors: products and the
+// 32-lane warp tree in FP32, every sum above it in FP64). The update kernel's last block sets the CUDA-graph
 // conditional that keeps the iteration loop running while some right-hand side is not done.
 #include "qp_device.cuh"
 
@@ -16,7 +17,6 @@ namespace qp {
 __global__ void k_level_reset(BatchDev b, int which) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     b.ndone[which] = 0;
-    b.ndone[2 + which] = 0;   // loop-iteration counter of this level (hard cap on the graph's WHILE loop)
     *b.kcount = 0;
   }
   if (which == 1) {
@@ -25,7 +25,7 @@ __global__ void k_level_reset(BatchDev b, int which) {
       x.outer = 0;
       x.inner_total = 0;
       x.iters = 0;
-      x.odone = (i % MAXR) < b.units[i / MAXR].nrhs ? 0 : 1;
+      x.odone = (i % MAXR) < unit_at(b, i / MAXR).nrhs ? 0 : 1;
       x.ostatus = QP_ERR_NO_CONVERGENCE;
       x.prev_rel = INFINITY;
       x.scale = 0.0;
@@ -63,8 +63,8 @@ template <> __device__ __forceinline__ const float* vM<float>(const UnitDev& u) 
 template <typename T, int NR>
 __global__ void __launch_bounds__(BLOCK) k_pcg_init(BatchDev b, int level, int warm, unsigned long long cond) {
   for (int c = blockIdx.x; c < b.nchunks; c += gridDim.x) {
-    const int u = b.chunk_unit[c];
-    const UnitDev& un = b.units[u];
+    const int u = unit_of_chunk(b, c);
+    const UnitDev& un = unit_at(b, u);
     RhsSt* st = b.st + (size_t)u * MAXR;
     const int nrhs = un.nrhs, D = un.D;
     const cplx<T>* F = vF<T>(un, level);
@@ -76,10 +76,11 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_init(BatchDev b, int level, int w
     int zero_rhs[NR];
 #pragma unroll
     for (int k = 0; k < NR; ++k) zero_rhs[k] = (k < nrhs && level == LEVEL_FP32) ? ld_int(&st[k].odone) : 0;
+    T vt[3 * NR];
     double v[3 * NR];
 #pragma unroll
-    for (int q = 0; q < 3 * NR; ++q) v[q] = 0.0;
-    const int base = (c - un.chunk0) * b.chunk, end = min(base + b.chunk, D);
+    for (int q = 0; q < 3 * NR; ++q) vt[q] = T(0);
+    const int base = (c - un.chunk0) * un.chunk, end = min(base + un.chunk, D);
     for (int e = base + threadIdx.x; e < end; e += BLOCK) {
       const T m = M[e];
 #pragma unroll
@@ -96,19 +97,20 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_init(BatchDev b, int level, int w
           r[o] = rv;
           h[o] = mk<T>(m * rv.x, m * rv.y);
           if (level == LEVEL_FP32) U[o] = mk<T>(0, 0);
-          const double rr = (double)rv.x * rv.x + (double)rv.y * rv.y;
-          v[3 * k] += (double)f.x * f.x + (double)f.y * f.y;
-          v[3 * k + 1] += (double)m * rr;
-          v[3 * k + 2] += rr;
+          const T rr = fma(rv.x, rv.x, rv.y * rv.y);
+          vt[3 * k] = fma(f.x, f.x, fma(f.y, f.y, vt[3 * k]));
+          vt[3 * k + 1] = fma(m, rr, vt[3 * k + 1]);
+          vt[3 * k + 2] += rr;
         }
       }
     }
-    block_reduce<3 * NR>(v);
+    block_reduce_mixed<T, 3 * NR>(vt, v);
     if (!chunk_arrive<3 * NR>(b, c, u, v)) continue;
     unit_sums<3 * NR>(b, un, v);
-    for (int k = 0; k < nrhs && k < NR; ++k) {
-      const double f2 = v[3 * k], rz = v[3 * k + 1], rr = v[3 * k + 2];
-      if (threadIdx.x == 0) {
+    if (threadIdx.x == 0) {
+      int nd = 0;
+      for (int k = 0; k < nrhs && k < NR; ++k) {
+        const double f2 = v[3 * k], rz = v[3 * k + 1], rr = v[3 * k + 2];
         RhsSt& x = st[k];
         x.f2 = f2;
         x.rz = rz;
@@ -120,14 +122,17 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_init(BatchDev b, int level, int w
           x.done = 1;
           x.status = QP_ERR_BREAKDOWN;
         }
-        if (x.done) atomicAdd(&b.ndone[0], 1);
+        nd += x.done;
+      }
+      atomicAdd(&b.ndone[0], nd);
+      b.ucount[u] = 0;
+      // every unit is initialised here: the last one to finish sets the loop condition once
+      __threadfence();
+      if (atomicAdd(b.kcount, 1u) == (unsigned)b.nunits - 1u) {
+        *b.kcount = 0;
+        if (cond != 0ull) cudaGraphSetConditional(cond, ld_int(&b.ndone[0]) < b.nslots ? 1u : 0u);
       }
     }
-    if (threadIdx.x == 0) b.ucount[u] = 0;
-  }
-  if (kernel_arrive(b) && threadIdx.x == 0) {
-    if (cond != 0ull) cudaGraphSetConditional(cond, ld_int(&b.ndone[0]) < b.nslots ? 1u : 0u);
-    *b.kcount = 0;
   }
 }
 
@@ -135,8 +140,8 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_init(BatchDev b, int level, int w
 template <typename T, int NR>
 __global__ void __launch_bounds__(BLOCK) k_pcg_update(BatchDev b, int level, unsigned long long cond) {
   for (int c = blockIdx.x; c < b.nchunks; c += gridDim.x) {
-    const int u = b.chunk_unit[c];
-    const UnitDev& un = b.units[u];
+    const int u = unit_of_chunk(b, c);
+    const UnitDev& un = unit_at(b, u);
     RhsSt* st = b.st + (size_t)u * MAXR;
     const int nrhs = un.nrhs, D = un.D;
     int done[NR];
@@ -154,10 +159,11 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_update(BatchDev b, int level, uns
     const cplx<T>* h = vH<T>(un);
     const cplx<T>* w = vW<T>(un);
     const T* M = vM<T>(un);
+    T vt[2 * NR];
     double v[2 * NR];
 #pragma unroll
-    for (int q = 0; q < 2 * NR; ++q) v[q] = 0.0;
-    const int base = (c - un.chunk0) * b.chunk, end = min(base + b.chunk, D);
+    for (int q = 0; q < 2 * NR; ++q) vt[q] = T(0);
+    const int base = (c - un.chunk0) * un.chunk, end = min(base + un.chunk, D);
     for (int e = base + threadIdx.x; e < end; e += BLOCK) {
       const T m = M[e];
 #pragma unroll
@@ -173,18 +179,20 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_update(BatchDev b, int level, uns
           rv.y = fma(-al, wv.y, rv.y);
           U[o] = uv;
           r[o] = rv;
-          const double rr = (double)rv.x * rv.x + (double)rv.y * rv.y;
-          v[2 * k] += (double)m * rr;
-          v[2 * k + 1] += rr;
+          const T rr = fma(rv.x, rv.x, rv.y * rv.y);
+          vt[2 * k] = fma(m, rr, vt[2 * k]);
+          vt[2 * k + 1] += rr;
         }
       }
     }
-    block_reduce<2 * NR>(v);
+    block_reduce_mixed<T, 2 * NR>(vt, v);
     if (!chunk_arrive<2 * NR>(b, c, u, v)) continue;
     unit_sums<2 * NR>(b, un, v);
-    for (int k = 0; k < nrhs && k < NR; ++k) {
-      const double rz = v[2 * k], rr = v[2 * k + 1];
-      if (threadIdx.x == 0 && !done[k]) {
+    if (threadIdx.x == 0) {
+      int nd = 0;
+      for (int k = 0; k < nrhs && k < NR; ++k) {
+        if (done[k]) continue;
+        const double rz = v[2 * k], rr = v[2 * k + 1];
         RhsSt& x = st[k];
         x.iters += 1;
         x.rr = rr;
@@ -194,34 +202,26 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_update(BatchDev b, int level, uns
           x.status = QP_ERR_BREAKDOWN;
         } else if (rr <= b.tol2 * x.f2) {
           dn = 1;
-        } else if (x.iters >= b.maxit) {
+        } else if (x.iters >= b.maxit) {   // iteration cap: also bounds the graph's WHILE loop
           dn = 1;
           x.status = QP_ERR_NO_CONVERGENCE;
         }
         x.beta = rz / x.rz;
         x.rz = rz;
-        if (dn) {
-          x.done = 1;
-          atomicAdd(&b.ndone[0], 1);
-        }
+        if (dn) x.done = 1;
+        nd += dn;
       }
+      b.ucount[u] = 0;
+      count_done(b, 0, nd, cond);   // the right-hand side that completes the count ends the loop
     }
-    if (threadIdx.x == 0) b.ucount[u] = 0;
-  }
-  if (kernel_arrive(b) && threadIdx.x == 0) {
-    // continue while some right-hand side is active; the loop counter bounds the WHILE node in any case
-    const int loops = ++b.ndone[2];
-    if (cond != 0ull)
-      cudaGraphSetConditional(cond, (ld_int(&b.ndone[0]) < b.nslots && loops < b.maxit + 2) ? 1u : 0u);
-    *b.kcount = 0;
   }
 }
 
 template <typename T, int NR>
 __global__ void __launch_bounds__(BLOCK) k_pcg_hupdate(BatchDev b, int level) {
   for (int c = blockIdx.x; c < b.nchunks; c += gridDim.x) {
-    const int u = b.chunk_unit[c];
-    const UnitDev& un = b.units[u];
+    const int u = unit_of_chunk(b, c);
+    const UnitDev& un = unit_at(b, u);
     RhsSt* st = b.st + (size_t)u * MAXR;
     const int nrhs = un.nrhs, D = un.D;
     int done[NR];
@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_hupdate(BatchDev b, int level) {
     const cplx<T>* r = vR<T>(un);
     cplx<T>* h = vH<T>(un);
     const T* M = vM<T>(un);
-    const int base = (c - un.chunk0) * b.chunk, end = min(base + b.chunk, D);
+    const int base = (c - un.chunk0) * un.chunk, end = min(base + un.chunk, D);
     for (int e = base + threadIdx.x; e < end; e += BLOCK) {
       const T m = M[e];
 #pragma unroll
@@ -258,11 +258,11 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_hupdate(BatchDev b, int level) {
 // Refinement: F32 = scale * (F - Q64 U64) for the right-hand sides still refining (scale = 1 / ||F - Q U||).
 __global__ void __launch_bounds__(BLOCK) k_refine_prep(BatchDev b) {
   for (int c = blockIdx.x; c < b.nchunks; c += gridDim.x) {
-    const int u = b.chunk_unit[c];
-    const UnitDev& un = b.units[u];
+    const int u = unit_of_chunk(b, c);
+    const UnitDev& un = unit_at(b, u);
     const RhsSt* st = b.st + (size_t)u * MAXR;
     const int nrhs = un.nrhs, D = un.D;
-    const int base = (c - un.chunk0) * b.chunk, end = min(base + b.chunk, D);
+    const int base = (c - un.chunk0) * un.chunk, end = min(base + un.chunk, D);
     for (int k = 0; k < nrhs; ++k) {
       if (ld_int(&st[k].odone)) continue;
       const double sc = __ldcg(&st[k].scale);
@@ -278,11 +278,11 @@ __global__ void __launch_bounds__(BLOCK) k_refine_prep(BatchDev b) {
 // Refinement: U64 += c32 / scale for the right-hand sides still refining.
 __global__ void __launch_bounds__(BLOCK) k_refine_accum(BatchDev b) {
   for (int c = blockIdx.x; c < b.nchunks; c += gridDim.x) {
-    const int u = b.chunk_unit[c];
-    const UnitDev& un = b.units[u];
+    const int u = unit_of_chunk(b, c);
+    const UnitDev& un = unit_at(b, u);
     const RhsSt* st = b.st + (size_t)u * MAXR;
     const int nrhs = un.nrhs, D = un.D;
-    const int base = (c - un.chunk0) * b.chunk, end = min(base + b.chunk, D);
+    const int base = (c - un.chunk0) * un.chunk, end = min(base + un.chunk, D);
     for (int k = 0; k < nrhs; ++k) {
       if (ld_int(&st[k].odone)) continue;
       const double inv = __ldcg(&st[k].inv_scale);

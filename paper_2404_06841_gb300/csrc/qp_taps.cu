@@ -155,8 +155,8 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 3) k_apply(BatchDe
   cplx<T>* scoef = reinterpret_cast<cplx<T>*>(smraw);
   const PlanDev* cur = nullptr;
   for (int c = blockIdx.x; c < b.nchunks; c += gridDim.x) {
-    const int u = b.chunk_unit[c];
-    const UnitDev& un = b.units[u];
+    const int u = unit_of_chunk(b, c);
+    const UnitDev& un = unit_at(b, u);
     RhsSt* st = b.st + (size_t)u * MAXR;
     const int nrhs = un.nrhs;
     // skip units with nothing left to do at this level (same decision for every chunk of the unit)
@@ -184,11 +184,12 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 3) k_apply(BatchDe
     const cplx<T>* F = reinterpret_cast<const cplx<T>*>(un.F);
     const bool fft_unit = (sp.backend == QP_BACKEND_FFT);
     constexpr int NV = (EPI == EPI_RESIDUAL) ? 2 * NR : NR;   // reduced quantities: (h,w) or (|F-w|^2, |F|^2)
+    T vt[NV];                                                   // per-thread partials in the vector precision
     double v[NV];
 #pragma unroll
-    for (int q = 0; q < NV; ++q) v[q] = 0.0;
-    const int base = (c - un.chunk0) * b.chunk;
-    const int end = min(base + b.chunk, D);
+    for (int q = 0; q < NV; ++q) vt[q] = T(0);
+    const int base = (c - un.chunk0) * un.chunk;
+    const int end = min(base + un.chunk, D);
     for (int e = base + threadIdx.x; e < end; e += BLOCK) {
       cplx<T> acc[NR];
       if (fft_unit) {
@@ -204,13 +205,13 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 3) k_apply(BatchDe
           if (EPI == EPI_DOT_HW) {
             if (!fft_unit) dst[o] = acc[r];
             const cplx<T> hv = src[o];
-            v[r] += (double)hv.x * (double)acc[r].x + (double)hv.y * (double)acc[r].y;
+            vt[r] = fma(hv.x, acc[r].x, fma(hv.y, acc[r].y, vt[r]));
           } else if (EPI == EPI_RESIDUAL) {
             const cplx<T> f = F[o];
             const cplx<T> res = (e == 0) ? mk<T>(0, 0) : mk<T>(f.x - acc[r].x, f.y - acc[r].y);
             dst[o] = res;
-            v[2 * r] += (double)res.x * res.x + (double)res.y * res.y;
-            if (e != 0) v[2 * r + 1] += (double)f.x * f.x + (double)f.y * f.y;
+            vt[2 * r] = fma(res.x, res.x, fma(res.y, res.y, vt[2 * r]));
+            if (e != 0) vt[2 * r + 1] = fma(f.x, f.x, fma(f.y, f.y, vt[2 * r + 1]));
           } else {
             if (!fft_unit) dst[o] = acc[r];
           }
@@ -218,7 +219,7 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 3) k_apply(BatchDe
       }
     }
     if (EPI == EPI_NONE) continue;
-    block_reduce<NV>(v);
+    block_reduce_mixed<T, NV>(vt, v);
     if (!chunk_arrive<NV>(b, c, u, v)) continue;
     // this block completes unit u: finalize its right-hand sides
     unit_sums<NV>(b, un, v);
@@ -233,7 +234,7 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 3) k_apply(BatchDe
             if (!(s0 > 0.0) || !isfinite(s0)) {   // (h, Q h) <= 0 or NaN: breakdown
               x.done = 1;
               x.status = QP_ERR_BREAKDOWN;
-              atomicAdd(&b.ndone[0], 1);
+              count_done(b, 0, 1, cond);           // completing the count here ends the PCG loop
             } else {
               x.alpha = x.rz / s0;
             }
@@ -263,22 +264,12 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 3) k_apply(BatchDe
           x.ostatus = os;
           if (od) {
             x.odone = 1;
-            atomicAdd(&b.ndone[1], 1);
+            count_done(b, 1, 1, cond);             // the right-hand side that completes the count ends the loop
           }
         }
       }
     }
     if (threadIdx.x == 0) b.ucount[u] = 0;
-  }
-  if (EPI == EPI_NONE) return;
-  if (kernel_arrive(b) && threadIdx.x == 0) {
-    if (EPI == EPI_RESIDUAL && refine) {
-      // the outer loop continues while some right-hand side refines; its counter bounds the WHILE node
-      const int loops = ++b.ndone[3];
-      if (cond != 0ull)
-        cudaGraphSetConditional(cond, (ld_int(&b.ndone[1]) < b.nslots && loops <= b.max_outer + 1) ? 1u : 0u);
-    }
-    *b.kcount = 0;
   }
 }
 
