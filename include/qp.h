@@ -158,6 +158,26 @@ qp_status qp_batch_homogenized(qp_batch* batch, const qp_solve_opts* opts, doubl
                                qp_solve_info* infos, void* stream);
 qp_status qp_batch_destroy(qp_batch* batch);
 
+/* Size in bytes of the device scratch that qp_pcg_solve_taps_static works in. */
+#define QP_STATIC_SCRATCH_BYTES (16u * 1024u * 1024u)
+
+/* FP64 PCG solve of Q U = F for a tap coefficient without a plan and without allocating device memory; the
+ * paper has no counterpart (it concerns how a caller provides GPU memory, not the method). For callers that
+ * cannot call cudaMalloc, for example because another component owns the device-memory budget. All of its
+ * intermediates (coefficient tables, the diagonal preconditioner, the PCG vectors r, h, Q h, reduction
+ * partials and solver state) live in one static device array of QP_STATIC_SCRATCH_BYTES that every GPU that
+ * loads this library holds until the process exits; it never calls cudaMalloc, cudaFree or an allocating
+ * library routine. Arguments as qp_plan_create (d, n, P, N, coeff; taps only) and qp_pcg_solve (nrhs, F, U
+ * with U as the initial guess, opts with mode QP_MODE_FP64, info). Needs about (24 + 48 nrhs) D bytes plus
+ * the tap tables; larger problems return QP_ERR_INVALID_ARG ("too large for the static scratch") before any
+ * device work. The first call on a device looks up the array's device address (cudaGetSymbolAddress), so
+ * make that first call before any stream capture. All calls share the one array: calls whose GPU work
+ * overlaps (other streams or threads) race and give wrong results; serialise them. Each call clears what
+ * must start at zero, so a call never depends on what the previous call left there. Synchronises stream. */
+qp_status qp_pcg_solve_taps_static(int d, int n, const double* P, const int* N, const qp_coeff* coeff, int nrhs,
+                                   const void* F, void* U, const qp_solve_opts* opts, qp_solve_info* info,
+                                   void* stream);
+
 /* Description of the last error on this host thread ("" if none). The string stays valid until the next call. */
 const char* qp_last_error(void);
 

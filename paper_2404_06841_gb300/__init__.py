@@ -33,7 +33,8 @@ KIND_CODES = {"scalar": QP_COEF_SCALAR, "diag": QP_COEF_DIAG, "sym": QP_COEF_SYM
 # Every symbol include/qp.h declares (checked by the test suite).
 EXPORTS = ("qp_plan_create", "qp_plan_destroy", "qp_plan_query", "qp_apply_stiffness", "qp_corrector_rhs",
            "qp_pcg_solve", "qp_homogenized_reduce", "qp_homogenized", "qp_fft", "qp_batch_create",
-           "qp_batch_homogenized", "qp_batch_destroy", "qp_last_error", "qp_launch_count")
+           "qp_batch_homogenized", "qp_batch_destroy", "qp_last_error", "qp_launch_count",
+           "qp_pcg_solve_taps_static")
 
 
 class qp_coeff(C.Structure):
@@ -89,6 +90,8 @@ def load_library(path: str = LIB_PATH):
         "qp_batch_create": [i, C.POINTER(vp), C.POINTER(vp)],
         "qp_batch_homogenized": [vp, C.POINTER(qp_solve_opts), dp, C.POINTER(qp_solve_info), vp],
         "qp_batch_destroy": [vp],
+        "qp_pcg_solve_taps_static": [i, i, dp, ip, C.POINTER(qp_coeff), i, vp, vp, C.POINTER(qp_solve_opts),
+                                     C.POINTER(qp_solve_info), vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -303,6 +306,25 @@ def qp_batch_destroy(batch: Batch):
         h = batch.handle
         batch.handle = None
         _check(_lib.qp_batch_destroy(h))
+
+
+def qp_pcg_solve_taps_static(d, n, P, N, coeff, F, U, tol=1e-10, maxit=1000, precond=QP_PRECOND_JACOBI,
+                             nrhs=None, stream=None, raise_on_error=True):
+    """The allocation-free FP64 solve (no plan; all intermediates in the library's static device scratch)."""
+    P = np.ascontiguousarray(P, dtype=np.float64).reshape(-1)
+    Narr = np.ascontiguousarray(N, dtype=np.int32).reshape(-1)
+    keep = [P, Narr]
+    c = _coeff_struct(coeff, d, keep)
+    if nrhs is None:
+        nrhs = F.numel() // int(np.prod(Narr))
+    infos = (qp_solve_info * nrhs)()
+    o = _opts(tol, maxit, precond, QP_MODE_FP64, 0.0, 0)
+    st = _lib.qp_pcg_solve_taps_static(d, n, P.ctypes.data_as(C.POINTER(C.c_double)),
+                                       Narr.ctypes.data_as(C.POINTER(C.c_int)), C.byref(c), int(nrhs), _ptr(F),
+                                       _ptr(U), C.byref(o), infos, _stream(stream))
+    if raise_on_error:
+        _check(st)
+    return [x.as_dict() for x in infos]
 
 
 def qp_last_error() -> str:

@@ -34,6 +34,12 @@ namespace {
 
 thread_local std::string g_err;
 
+}  // namespace
+
+void qp::set_last_error(const std::string& msg) { g_err = msg; }
+
+namespace {
+
 template <typename T> struct Vecs {
   cplx<T>* r = nullptr;
   cplx<T>* h = nullptr;

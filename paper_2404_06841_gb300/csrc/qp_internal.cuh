@@ -31,6 +31,9 @@ inline void ck(cudaError_t e, const char* what, int line) {
 // run inside a CUDA graph are added by the host after each graph launch from the iteration counts.
 void count_launch(int n = 1);
 
+// Sets the text qp_last_error() returns on this host thread.
+void set_last_error(const std::string& msg);
+
 constexpr int MAXN = QP_MAX_N_AXES;
 constexpr int MAXD = QP_MAX_D;
 constexpr int MAXR = QP_MAX_RHS;
