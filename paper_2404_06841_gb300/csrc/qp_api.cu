@@ -445,9 +445,9 @@ void record_apply(const Units& us, const Entry& en, int level, int epi, bool ref
     qp_plan* p = us.plans[u];
     if (p->backend != QP_BACKEND_FFT) continue;
     const int nr = us.nrhs[u];
-    if (level == LEVEL_FP32) fft_apply<float>(p->fft, p->host_pd, p->v32.h, p->v32.w, nr, s);
-    else if (epi == EPI_DOT_HW) fft_apply<double>(p->fft, p->host_pd, p->v64.h, p->v64.w, nr, s);
-    else fft_apply<double>(p->fft, p->host_pd, p->v64.X, p->v64.w, nr, s);
+    if (level == LEVEL_FP32) fft_apply<float>(p->fft, p->host_pd, p->pd, p->v32.h, p->v32.w, nr, s);
+    else if (epi == EPI_DOT_HW) fft_apply<double>(p->fft, p->host_pd, p->pd, p->v64.h, p->v64.w, nr, s);
+    else fft_apply<double>(p->fft, p->host_pd, p->pd, p->v64.X, p->v64.w, nr, s);
   }
   launch_apply(en.bd, us.all_real, us.max_coef, us.max_rhs, level, epi, refine, cond, en.nblk, s);
   CK_LAUNCH();
@@ -811,19 +811,21 @@ void check_opts(const qp_solve_opts* o, const qp_plan* p) {
     raise(QP_ERR_INVALID_ARG, "plan was created without the FP64 solve workspace");
   if (p && o->mode == QP_MODE_FP32_REFINE && !(p->precisions & 2))
     raise(QP_ERR_INVALID_ARG, "plan was created without the FP32 solve workspace");
+  if (p && p->backend == QP_BACKEND_FFT && o->precond == QP_PRECOND_FROBENIUS)
+    raise(QP_ERR_UNSUPPORTED, "the Frobenius diagonal is built on the taps backend only");
 }
 
 void corrector_rhs(qp_plan* p, int j0, int nrhs, double2* F, cudaStream_t s) {
   CK(cudaMemsetAsync(F, 0, (size_t)nrhs * p->D * sizeof(double2), s));
   if (p->backend == QP_BACKEND_TAPS) launch_rhs_taps(p->pd, p->coef_count, j0, nrhs, p->D, F, s);
-  else fft_rhs(p->fft, p->host_pd, j0, nrhs, F, s);
+  else fft_rhs(p->fft, p->host_pd, p->pd, j0, nrhs, F, s);
   CK_LAUNCH();
 }
 
 // a* into dst (device, 2 d^2 doubles: re, im per entry).
 void astar_launch(qp_plan* p, const double2* U, double* dst, cudaStream_t s) {
   if (p->backend == QP_BACKEND_TAPS) launch_astar_taps(p->pd, p->coef_count, p->D, U, dst, s);
-  else fft_astar(p->fft, p->host_pd, U, dst, s);
+  else fft_astar(p->fft, p->host_pd, p->pd, U, dst, s);
   CK_LAUNCH();
 }
 
@@ -909,7 +911,7 @@ qp_status qp_plan_create(int d, int n, const double* P, const int* N, const qp_c
   p->host_pd.backend = p->backend;
   if (p->backend == QP_BACKEND_FFT)
     for (int j = 0; j < n; ++j)
-      if (!is_23(N[j])) raise(QP_ERR_UNSUPPORTED, "the FFT backend needs every N_j to be a product of 2 and 3");
+      if (!fft_supported(N[j])) raise(QP_ERR_UNSUPPORTED, "the FFT backend does not transform N_j = " + std::to_string(N[j]));
   if (coeff->repr == QP_REPR_TAPS) build_taps(p.get(), coeff);
   alloc_workspace(p.get());
   p->pd = (PlanDev*)p->dalloc(sizeof(PlanDev));
@@ -919,11 +921,11 @@ qp_status qp_plan_create(int d, int n, const double* P, const int* N, const qp_c
                 p->small, p->nblk, s);
     CK_LAUNCH();
   } else {
-    p->fft = fft_plan_create(p->host_pd, p->precisions, s);
-    if (coeff->repr == QP_REPR_GRID) fft_set_grid(p->fft, p->host_pd, coeff->grid, s);
-    else fft_set_taps(p->fft, p->host_pd, s);
     CK(cudaMemcpy(p->pd, &p->host_pd, sizeof(PlanDev), cudaMemcpyHostToDevice));
-    fft_diag(p->fft, p->host_pd, p->jac64, p->frob64, p->jac32, p->frob32, p->small, s);
+    p->fft = fft_plan_create(p->host_pd, p->precisions, p->max_rhs);
+    if (coeff->repr == QP_REPR_GRID) fft_set_grid(p->fft, p->host_pd, p->pd, coeff->grid, s);
+    else fft_set_taps(p->fft, p->host_pd, p->pd, s);
+    fft_diag(p->fft, &p->host_pd, p->pd, p->jac64, p->frob64, p->jac32, p->frob32, p->small, s);
     CK_LAUNCH();
   }
   CK(cudaMemcpyAsync(p->h_small, p->small, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -973,8 +975,8 @@ qp_status qp_apply_stiffness(qp_plan* p, int nrhs, const void* U, void* QU, int 
     else
       launch_apply_plain<float>(p->pd, p->real_coef, p->coef_count, p->D, nrhs, (const float2*)U, (float2*)QU, s);
   } else {
-    if (precision == QP_FP64) fft_apply<double>(p->fft, p->host_pd, (const double2*)U, (double2*)QU, nrhs, s);
-    else fft_apply<float>(p->fft, p->host_pd, (const float2*)U, (float2*)QU, nrhs, s);
+    if (precision == QP_FP64) fft_apply<double>(p->fft, p->host_pd, p->pd, (const double2*)U, (double2*)QU, nrhs, s);
+    else fft_apply<float>(p->fft, p->host_pd, p->pd, (const float2*)U, (float2*)QU, nrhs, s);
   }
   CK_LAUNCH();
   API_END
@@ -1043,6 +1045,7 @@ qp_status qp_fft(int n, const int* N, int count, void* data, int sign, int preci
   int64_t D = 1;
   for (int j = 0; j < n; ++j) {
     if (N[j] < 2 || N[j] > 1024 || !is_23(N[j])) raise(QP_ERR_INVALID_ARG, "N_j must be 2..1024, products of 2, 3");
+    if (!fft_supported(N[j])) raise(QP_ERR_UNSUPPORTED, "FFT size " + std::to_string(N[j]) + " is not built");
     D *= N[j];
   }
   if (D * count > (int64_t(1) << 31)) raise(QP_ERR_INVALID_ARG, "too many elements");

@@ -1,20 +1,810 @@
-// Placeholder until the FFT backend lands: every entry raises QP_ERR_UNSUPPORTED.
+// n-dimensional complex DFT kernels and the FFT backend of the stiffness apply.
+//
+// Because the coefficient part A of Q = A o W is a multilevel circulant matrix (Sec. 4.1), the n-dim DFT
+// diagonalises it and the apply of eq. n-discrete_equation becomes: gradient (multiply by lambda_b(k) = (P k)_b),
+// unnormalised inverse DFT to the grid, pointwise product with A^{ab}(y_j) / D, forward DFT, divergence
+// (multiply by lambda_a(k) and sum over a); the factors i and -i of gradient and divergence cancel.
+//
+// DFT: one pass per axis. A pass stages tiles of whole lines of that axis in shared memory (the rows of a tile
+// are contiguous in memory, so loads and stores are coalesced), transforms each line in registers (radix 4/2/3
+// decimation in time for N <= 32) or as N = N1 x N2 four-step through shared memory (N up to 1024), and writes
+// the tile back. Twiddles for N <= 32 come from a constant-memory table filled once per device from host
+// cos/sin; larger sizes call sincospi in the kernel.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "qp_device.cuh"
 #include "qp_fft.cuh"
 
 namespace qp {
-struct FftPlan {};
-static void nb() { raise(QP_ERR_UNSUPPORTED, "FFT backend not built"); }
-FftPlan* fft_plan_create(const PlanDev&, int, cudaStream_t) { nb(); return nullptr; }
-void fft_plan_destroy(FftPlan* f) { delete f; }
-int64_t fft_plan_bytes(const FftPlan*) { return 0; }
-void fft_set_grid(FftPlan*, const PlanDev&, const double*, cudaStream_t) { nb(); }
-void fft_set_taps(FftPlan*, const PlanDev&, cudaStream_t) { nb(); }
-void fft_diag(FftPlan*, const PlanDev&, double*, double*, float*, float*, double*, cudaStream_t) { nb(); }
+
+// ------------------------------------------------------------------------------------------------ twiddles
+
+// Sizes transformed in registers and their offsets in the twiddle table (entries exp(2 pi i e / N), e < N).
+constexpr int kSmall[] = {2, 3, 4, 6, 8, 9, 12, 16, 18, 24, 27, 32};
+constexpr int kNumSmall = sizeof(kSmall) / sizeof(int);
+__host__ __device__ constexpr int tw_offset(int N) {
+  int off = 0;
+  for (int i = 0; i < kNumSmall; ++i) {
+    if (kSmall[i] == N) return off;
+    off += kSmall[i];
+  }
+  return -1;
+}
+constexpr int kTwTotal = tw_offset(32) + 32;
+
+__constant__ double2 c_tw64[kTwTotal];
+__constant__ float2 c_tw32[kTwTotal];
+
+namespace {
+std::mutex g_tw_mutex;
+bool g_tw_ready[64] = {};
+}  // namespace
+
+// Fills the constant twiddle table on the current device (once per device).
+static void ensure_twiddles() {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(g_tw_mutex);
+  if (dev >= 0 && dev < 64 && g_tw_ready[dev]) return;
+  std::vector<double2> t64(kTwTotal);
+  std::vector<float2> t32(kTwTotal);
+  int off = 0;
+  for (int i = 0; i < kNumSmall; ++i) {
+    const int N = kSmall[i];
+    for (int e = 0; e < N; ++e) {
+      const long double ang = 2.0L * 3.14159265358979323846264338327950288L * (long double)e / (long double)N;
+      const double c = (double)std::cos(ang), s = (double)std::sin(ang);
+      t64[off + e] = make_double2(c, s);
+      t32[off + e] = make_float2((float)c, (float)s);
+    }
+    off += N;
+  }
+  CK(cudaMemcpyToSymbol(c_tw64, t64.data(), kTwTotal * sizeof(double2)));
+  CK(cudaMemcpyToSymbol(c_tw32, t32.data(), kTwTotal * sizeof(float2)));
+  if (dev >= 0 && dev < 64) g_tw_ready[dev] = true;
+}
+
+template <typename T> __device__ __forceinline__ cplx<T> tw_at(int i);
+template <> __device__ __forceinline__ double2 tw_at<double>(int i) { return c_tw64[i]; }
+template <> __device__ __forceinline__ float2 tw_at<float>(int i) { return c_tw32[i]; }
+
+template <typename T> __device__ __forceinline__ cplx<T> cmul(cplx<T> a, cplx<T> b) {
+  return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename T> __device__ __forceinline__ cplx<T> cadd(cplx<T> a, cplx<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
+template <typename T> __device__ __forceinline__ cplx<T> csub(cplx<T> a, cplx<T> b) { return mk<T>(a.x - b.x, a.y - b.y); }
+// multiply by sign * i
+template <typename T> __device__ __forceinline__ cplx<T> mul_si(cplx<T> a, int sign) {
+  return sign > 0 ? mk<T>(-a.y, a.x) : mk<T>(a.y, -a.x);
+}
+// W_N^{sign * e} from the table (e reduced mod N at compile time by the caller)
+template <typename T, int N> __device__ __forceinline__ cplx<T> twd(int e, int sign) {
+  constexpr int off = tw_offset(N);
+  cplx<T> w = tw_at<T>(off + e % N);
+  if (sign < 0) w.y = -w.y;
+  return w;
+}
+
+// ------------------------------------------------------------------------------------------------ register DFT
+
+// In-register DFT of N = 2^a 3^b <= 32 points: X_k = sum_n x_n exp(sign 2 pi i n k / N), by decimation in time
+// with radix 4, 2 or 3 (all indices compile-time constants after unrolling).
+template <typename T, int N>
+struct RegDft {
+  static __device__ __forceinline__ void run(cplx<T>* x, int sign) {
+    constexpr int R = (N % 4 == 0 && N > 4) ? 4 : ((N % 2 == 0 && N > 2) ? 2 : ((N % 3 == 0 && N > 3) ? 3 : N));
+    constexpr int M = N / R;
+    cplx<T> sub[R][M];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int m = 0; m < M; ++m) sub[r][m] = x[r + R * m];
+#pragma unroll
+    for (int r = 0; r < R; ++r) RegDft<T, M>::run(sub[r], sign);
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+      cplx<T> t[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) t[r] = (r * k == 0) ? sub[r][k] : cmul<T>(sub[r][k], twd<T, N>(r * k, sign));
+      RegDft<T, R>::run(t, sign);
+#pragma unroll
+      for (int q = 0; q < R; ++q) x[k + M * q] = t[q];
+    }
+  }
+};
+template <typename T> struct RegDft<T, 1> {
+  static __device__ __forceinline__ void run(cplx<T>*, int) {}
+};
+template <typename T> struct RegDft<T, 2> {
+  static __device__ __forceinline__ void run(cplx<T>* x, int) {
+    const cplx<T> a = x[0], b = x[1];
+    x[0] = cadd<T>(a, b);
+    x[1] = csub<T>(a, b);
+  }
+};
+template <typename T> struct RegDft<T, 3> {
+  static __device__ __forceinline__ void run(cplx<T>* x, int sign) {
+    // X_k = x0 + x1 w^k + x2 w^{2k}, w = exp(sign 2 pi i / 3) = -1/2 + sign i sqrt(3)/2
+    const cplx<T> w1 = twd<T, 3>(1, sign);
+    const cplx<T> s = cadd<T>(x[1], x[2]), d = csub<T>(x[1], x[2]);
+    const cplx<T> a = x[0];
+    x[0] = cadd<T>(a, s);
+    const cplx<T> m = mk<T>(a.x + w1.x * s.x, a.y + w1.x * s.y);       // a - s/2
+    const cplx<T> j = mk<T>(-w1.y * d.y, w1.y * d.x);                 // i * (sign sqrt3/2) * d
+    x[1] = cadd<T>(m, j);
+    x[2] = csub<T>(m, j);
+  }
+};
+template <typename T> struct RegDft<T, 4> {
+  static __device__ __forceinline__ void run(cplx<T>* x, int sign) {
+    const cplx<T> a = cadd<T>(x[0], x[2]), b = csub<T>(x[0], x[2]);
+    const cplx<T> c = cadd<T>(x[1], x[3]), e = mul_si<T>(csub<T>(x[1], x[3]), sign);
+    x[0] = cadd<T>(a, c);
+    x[2] = csub<T>(a, c);
+    x[1] = cadd<T>(b, e);
+    x[3] = csub<T>(b, e);
+  }
+};
+
+// ------------------------------------------------------------------------------------------------ axis pass
+
+// One DFT pass along one axis of `count` arrays seen as [outer O][N][inner I] (C order). A block handles
+// L x R lines: L consecutive outer indices times R consecutive inner indices; the tile [L][N][R] is staged in
+// shared memory. Each thread transforms whole lines (in registers for N <= 32).
+template <typename T, int N>
+__global__ void __launch_bounds__(BLOCK) k_fft_axis(cplx<T>* data, long long O, int I, int L, int R, int sign) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cplx<T>* tile = reinterpret_cast<cplx<T>*>(smraw);
+  const long long nI = (I + R - 1) / R;          // inner blocks per outer row
+  const long long nO = (O + L - 1) / L;
+  const long long blk = blockIdx.x + (long long)blockIdx.y * gridDim.x;
+  if (blk >= nO * nI) return;
+  const long long o0 = (blk / nI) * L;
+  const int i0 = (int)(blk % nI) * R;
+  const int lrows = (int)min((long long)L, O - o0), rcols = min(R, I - i0);
+  const int tsz = L * N * R;
+  // load: element (l, k, r) at ((o0 + l) * N + k) * I + i0 + r; rows of r are contiguous
+  for (int t = threadIdx.x; t < tsz; t += BLOCK) {
+    const int r = t % R, k = (t / R) % N, l = t / (R * N);
+    if (l < lrows && r < rcols) tile[t] = data[((o0 + l) * N + k) * (long long)I + i0 + r];
+  }
+  __syncthreads();
+  for (int line = threadIdx.x; line < L * R; line += BLOCK) {
+    const int l = line / R, r = line % R;
+    if (l < lrows && r < rcols) {
+      cplx<T> x[N];
+#pragma unroll
+      for (int k = 0; k < N; ++k) x[k] = tile[(l * N + k) * R + r];
+      RegDft<T, N>::run(x, sign);
+#pragma unroll
+      for (int k = 0; k < N; ++k) tile[(l * N + k) * R + r] = x[k];
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < tsz; t += BLOCK) {
+    const int r = t % R, k = (t / R) % N, l = t / (R * N);
+    if (l < lrows && r < rcols) data[((o0 + l) * N + k) * (long long)I + i0 + r] = tile[t];
+  }
+}
+
+// Same pass for N = N1 * N2 (both <= 32): with n = n1 + N1 n2 and k = k2 + N2 k1,
+// X[k] = sum_{n1} W_N^{n1 k2} W_{N1}^{n1 k1} sum_{n2} x[n1 + N1 n2] W_{N2}^{n2 k2}.
+// Step A transforms along n2 (stride N1), step B applies W_N^{n1 k2} (sincospi), step C transforms along n1 and
+// leaves X[k2 + N2 k1] at tile position k1 + N1 k2; the store maps positions back to natural order.
+template <typename T, int N1, int N2>
+__global__ void __launch_bounds__(BLOCK) k_fft_axis_2(cplx<T>* data, long long O, int I, int L, int R, int sign) {
+  constexpr int N = N1 * N2;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cplx<T>* tile = reinterpret_cast<cplx<T>*>(smraw);
+  const long long nI = (I + R - 1) / R;
+  const long long nO = (O + L - 1) / L;
+  const long long blk = blockIdx.x + (long long)blockIdx.y * gridDim.x;
+  if (blk >= nO * nI) return;
+  const long long o0 = (blk / nI) * L;
+  const int i0 = (int)(blk % nI) * R;
+  const int lrows = (int)min((long long)L, O - o0), rcols = min(R, I - i0);
+  const int tsz = L * N * R;
+  for (int t = threadIdx.x; t < tsz; t += BLOCK) {
+    const int r = t % R, k = (t / R) % N, l = t / (R * N);
+    if (l < lrows && r < rcols) tile[t] = data[((o0 + l) * N + k) * (long long)I + i0 + r];
+  }
+  __syncthreads();
+  // step A + B: per (n1, line), line fastest so that neighbouring threads touch neighbouring r
+  const int LR = L * R;
+  for (int job = threadIdx.x; job < LR * N1; job += BLOCK) {
+    const int line = job % LR, n1 = job / LR, l = line / R, r = line % R;
+    if (l < lrows && r < rcols) {
+      cplx<T> x[N2];
+#pragma unroll
+      for (int n2 = 0; n2 < N2; ++n2) x[n2] = tile[(l * N + n1 + N1 * n2) * R + r];
+      RegDft<T, N2>::run(x, sign);
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) {
+        cplx<T> v = x[k2];
+        if (n1 * k2 != 0) {
+          T sv, cv;
+          if (sizeof(T) == 8) {
+            double s_, c_;
+            sincospi(2.0 * (double)((n1 * k2) % N) / (double)N, &s_, &c_);
+            sv = (T)s_;
+            cv = (T)c_;
+          } else {
+            float s_, c_;
+            sincospif(2.0f * (float)((n1 * k2) % N) / (float)N, &s_, &c_);
+            sv = (T)s_;
+            cv = (T)c_;
+          }
+          v = cmul<T>(v, mk<T>(cv, sign > 0 ? sv : -sv));
+        }
+        tile[(l * N + n1 + N1 * k2) * R + r] = v;
+      }
+    }
+  }
+  __syncthreads();
+  // step C: per (k2, line); X[k2 + N2 k1] goes straight to global memory (rows of r stay contiguous)
+  for (int job = threadIdx.x; job < LR * N2; job += BLOCK) {
+    const int line = job % LR, k2 = job / LR, l = line / R, r = line % R;
+    if (l < lrows && r < rcols) {
+      cplx<T> x[N1];
+#pragma unroll
+      for (int n1 = 0; n1 < N1; ++n1) x[n1] = tile[(l * N + n1 + N1 * k2) * R + r];
+      RegDft<T, N1>::run(x, sign);
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) data[((o0 + l) * N + k2 + N2 * k1) * (long long)I + i0 + r] = x[k1];
+    }
+  }
+}
+
+// Tile shape: about 8 KB (FP32) / 16 KB (FP64) of lines per block, rows of R >= 4 contiguous elements.
+static void tile_shape(int N, long long O, int I, int& L, int& R) {
+  const int target = 2048;                 // elements per tile
+  if (I >= 8) {
+    R = std::min(I, std::max(8, target / N));
+    R = std::min(R, 64);
+    L = 1;
+  } else {
+    R = I;
+    L = (int)std::max<long long>(1, std::min<long long>(O, std::max(1, target / (N * I))));
+  }
+}
+
+template <typename T, int N>
+static void axis_small(cplx<T>* data, long long O, int I, int sign, cudaStream_t s) {
+  int L, R;
+  tile_shape(N, O, I, L, R);
+  const long long blocks = ((O + L - 1) / L) * ((I + R - 1) / R);
+  const size_t smem = (size_t)L * N * R * sizeof(cplx<T>);
+  dim3 grid((unsigned)std::min<long long>(blocks, 65535), (unsigned)((blocks + 65534) / 65535));
+  k_fft_axis<T, N><<<grid, BLOCK, smem, s>>>(data, O, I, L, R, sign);
+  count_launch();
+}
+
+template <typename T, int N1, int N2>
+static void axis_two(cplx<T>* data, long long O, int I, int sign, cudaStream_t s) {
+  constexpr int N = N1 * N2;
+  int L = 1, R = 1;
+  const int target = (sizeof(T) == 8 ? 2048 : 4096);
+  if (I >= 4) {
+    R = std::min(I, std::max(4, target / N));
+    L = 1;
+  } else {
+    R = I;
+    L = (int)std::max<long long>(1, std::min<long long>(O, std::max(1, target / (N * I))));
+  }
+  const long long blocks = ((O + L - 1) / L) * ((I + R - 1) / R);
+  const size_t smem = (size_t)L * N * R * sizeof(cplx<T>);
+  if (smem > 200 * 1024) raise(QP_ERR_UNSUPPORTED, "FFT tile exceeds shared memory");
+  if (smem > 48 * 1024)
+    CK(cudaFuncSetAttribute(k_fft_axis_2<T, N1, N2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid((unsigned)std::min<long long>(blocks, 65535), (unsigned)((blocks + 65534) / 65535));
+  k_fft_axis_2<T, N1, N2><<<grid, BLOCK, smem, s>>>(data, O, I, L, R, sign);
+  count_launch();
+}
+
+// True if this build transforms an axis of size N.
+bool fft_supported(int N) {
+  switch (N) {
+    case 2: case 3: case 4: case 6: case 8: case 9: case 12: case 16: case 18: case 24: case 27: case 32:
+    case 48: case 64: case 72: case 96: case 128: case 144: case 192: case 256: case 288: case 384: case 512:
+    case 576: case 768: case 1024:
+      return true;
+    default:
+      return false;
+  }
+}
+
+// One pass along an axis of size N with inner size I (product of the later axes) and outer size O.
 template <typename T>
-void fft_apply(FftPlan*, const PlanDev&, const cplx<T>*, cplx<T>*, int, cudaStream_t) { nb(); }
-template void fft_apply<double>(FftPlan*, const PlanDev&, const double2*, double2*, int, cudaStream_t);
-template void fft_apply<float>(FftPlan*, const PlanDev&, const float2*, float2*, int, cudaStream_t);
-void fft_rhs(FftPlan*, const PlanDev&, int, int, double2*, cudaStream_t) { nb(); }
-void fft_astar(FftPlan*, const PlanDev&, const double2*, double*, cudaStream_t) { nb(); }
-void fft_standalone(int, const int*, int, void*, int, int, cudaStream_t) { nb(); }
+static void fft_axis(cplx<T>* data, int N, long long O, int I, int sign, cudaStream_t s) {
+  switch (N) {
+    case 2: axis_small<T, 2>(data, O, I, sign, s); break;
+    case 3: axis_small<T, 3>(data, O, I, sign, s); break;
+    case 4: axis_small<T, 4>(data, O, I, sign, s); break;
+    case 6: axis_small<T, 6>(data, O, I, sign, s); break;
+    case 8: axis_small<T, 8>(data, O, I, sign, s); break;
+    case 9: axis_small<T, 9>(data, O, I, sign, s); break;
+    case 12: axis_small<T, 12>(data, O, I, sign, s); break;
+    case 16: axis_small<T, 16>(data, O, I, sign, s); break;
+    case 18: axis_small<T, 18>(data, O, I, sign, s); break;
+    case 24: axis_small<T, 24>(data, O, I, sign, s); break;
+    case 27: axis_small<T, 27>(data, O, I, sign, s); break;
+    case 32: axis_small<T, 32>(data, O, I, sign, s); break;
+    case 48: axis_two<T, 16, 3>(data, O, I, sign, s); break;
+    case 64: axis_two<T, 8, 8>(data, O, I, sign, s); break;
+    case 72: axis_two<T, 8, 9>(data, O, I, sign, s); break;
+    case 96: axis_two<T, 32, 3>(data, O, I, sign, s); break;
+    case 128: axis_two<T, 16, 8>(data, O, I, sign, s); break;
+    case 144: axis_two<T, 16, 9>(data, O, I, sign, s); break;
+    case 192: axis_two<T, 32, 6>(data, O, I, sign, s); break;
+    case 256: axis_two<T, 16, 16>(data, O, I, sign, s); break;
+    case 288: axis_two<T, 32, 9>(data, O, I, sign, s); break;
+    case 384: axis_two<T, 32, 12>(data, O, I, sign, s); break;
+    case 512: axis_two<T, 32, 16>(data, O, I, sign, s); break;
+    case 576: axis_two<T, 32, 18>(data, O, I, sign, s); break;
+    case 768: axis_two<T, 32, 24>(data, O, I, sign, s); break;
+    case 1024: axis_two<T, 32, 32>(data, O, I, sign, s); break;
+    default: raise(QP_ERR_UNSUPPORTED, "FFT size " + std::to_string(N) + " is not built");
+  }
+}
+
+// In-place unnormalised n-dim DFT of `count` contiguous arrays of shape N[0..n-1].
+template <typename T>
+static void fft_nd(cplx<T>* data, int n, const int* N, long long count, int sign, cudaStream_t s) {
+  ensure_twiddles();
+  long long D = 1;
+  for (int j = 0; j < n; ++j) D *= N[j];
+  for (int j = 0; j < n; ++j) {
+    long long inner = 1;
+    for (int t = j + 1; t < n; ++t) inner *= N[t];
+    const long long outer = count * D / (inner * N[j]);
+    if (inner > (1ll << 30)) raise(QP_ERR_UNSUPPORTED, "inner size too large");
+    fft_axis<T>(data, N[j], outer, (int)inner, sign, s);
+  }
+}
+
+void fft_standalone(int n, const int* N, int count, void* data, int sign, int precision, cudaStream_t s) {
+  for (int j = 0; j < n; ++j)
+    if (!fft_supported(N[j])) raise(QP_ERR_UNSUPPORTED, "FFT size " + std::to_string(N[j]) + " is not built");
+  if (precision == QP_FP64) fft_nd<double>(static_cast<double2*>(data), n, N, count, sign, s);
+  else fft_nd<float>(static_cast<float2*>(data), n, N, count, sign, s);
+}
+
+// ------------------------------------------------------------------------------------------------ FFT backend
+
+struct FftPlan {
+  int d = 0, n = 0, D = 0, ncomp = 0, kind = 0, max_rhs = 0, precisions = 3;
+  int N[MAXN] = {};
+  std::vector<void*> allocs;
+  int64_t bytes = 0;
+  double* coef64 = nullptr;     // A^{c}(y_j) / D, [ncomp][D]
+  float* coef32 = nullptr;
+  double2* ahat = nullptr;      // A~^{c}_k, [ncomp][D] (FP64)
+  double2* f64 = nullptr;       // fields [d][max_rhs][D]
+  float2* f32 = nullptr;
+  double* part = nullptr;       // reduction partials
+  int nblk = 0;
+  void* take(size_t b) {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, b);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      raise(e == cudaErrorMemoryAllocation ? QP_ERR_OOM : QP_ERR_CUDA, "cudaMalloc failed in the FFT plan");
+    }
+    allocs.push_back(p);
+    bytes += (int64_t)b;
+    return p;
+  }
+  ~FftPlan() {
+    for (void* p : allocs) cudaFree(p);
+  }
+};
+
+FftPlan* fft_plan_create(const PlanDev& pd, int precisions, int max_rhs) {
+  for (int j = 0; j < pd.n; ++j)
+    if (!fft_supported(pd.N[j])) raise(QP_ERR_UNSUPPORTED, "FFT size " + std::to_string(pd.N[j]) + " is not built");
+  ensure_twiddles();
+  FftPlan* f = new FftPlan();
+  try {
+    f->d = pd.d;
+    f->n = pd.n;
+    f->D = pd.D;
+    f->ncomp = pd.ncomp;
+    f->kind = pd.kind;
+    f->max_rhs = max_rhs;
+    f->precisions = precisions;
+    for (int j = 0; j < pd.n; ++j) f->N[j] = pd.N[j];
+    const size_t D = (size_t)pd.D;
+    f->coef64 = (double*)f->take(D * pd.ncomp * sizeof(double));
+    f->coef32 = (float*)f->take(D * pd.ncomp * sizeof(float));
+    f->ahat = (double2*)f->take(D * pd.ncomp * sizeof(double2));
+    if (precisions & 1) f->f64 = (double2*)f->take(D * pd.d * max_rhs * sizeof(double2));
+    else f->f64 = (double2*)f->take(D * sizeof(double2));   // set-up transforms only
+    if (precisions & 2) f->f32 = (float2*)f->take(D * pd.d * max_rhs * sizeof(float2));
+    f->nblk = (int)std::min<int64_t>((pd.D + BLOCK - 1) / BLOCK, 152 * 8);
+    f->part = (double*)f->take((size_t)f->nblk * 2 * MAXD * MAXD * sizeof(double) + 1024);
+  } catch (...) {
+    delete f;
+    throw;
+  }
+  return f;
+}
+
+void fft_plan_destroy(FftPlan* f) { delete f; }
+int64_t fft_plan_bytes(const FftPlan* f) { return f ? f->bytes : 0; }
+
+// lambda_a(k) for the mode at linear index e.
+template <typename T>
+__device__ __forceinline__ void lambda_of(const PlanDev& p, int e, T (&lk)[MAXD], int (&ib)[MAXN]) {
+  int k[MAXN];
+  mode_digits(p, e, ib, k);
+#pragma unroll
+  for (int a = 0; a < MAXD; ++a) {
+    lk[a] = T(0);
+#pragma unroll
+    for (int j = 0; j < MAXN; ++j)
+      if (a < p.d && j < p.n) lk[a] = fma(pcoef<T>(p, a, j), (T)k[j], lk[a]);
+  }
+}
+
+// coefficient entry (a, b) from the stored components at node e
+template <typename T>
+__device__ __forceinline__ T coef_at(int kind, int d, const T* c, int D, int e, int a, int b) {
+  if (kind == QP_COEF_SCALAR) return a == b ? c[e] : T(0);
+  if (kind == QP_COEF_DIAG) return a == b ? c[(size_t)a * D + e] : T(0);
+  return c[(size_t)sym_idx(a, b, d) * D + e];
+}
+
+// set-up: real grid samples -> complex buffer (component c), and the scaled FP64 / FP32 copies A / D
+__global__ void k_grid_prepare(const PlanDev* pdp, const double* grid, int comp, double2* z, double* c64, float* c32) {
+  const PlanDev& p = *pdp;
+  const int D = p.D;
+  const double inv = 1.0 / (double)D;
+  for (int e = blockIdx.x * BLOCK + threadIdx.x; e < D; e += gridDim.x * BLOCK) {
+    const double v = grid[(size_t)comp * D + e];
+    z[e] = make_double2(v, 0.0);
+    c64[(size_t)comp * D + e] = v * inv;
+    c32[(size_t)comp * D + e] = (float)(v * inv);
+  }
+}
+
+__global__ void k_scale_store(const double2* z, double2* out, int D, double s) {
+  for (int e = blockIdx.x * BLOCK + threadIdx.x; e < D; e += gridDim.x * BLOCK) {
+    const double2 v = z[e];
+    out[e] = make_double2(v.x * s, v.y * s);
+  }
+}
+
+void fft_set_grid(FftPlan* f, const PlanDev& pd, const PlanDev* pdp, const double* grid, cudaStream_t s) {
+  for (int c = 0; c < f->ncomp; ++c) {
+    k_grid_prepare<<<f->nblk, BLOCK, 0, s>>>(pdp, grid, c, f->f64, f->coef64, f->coef32);
+    count_launch();
+    fft_nd<double>(f->f64, pd.n, pd.N, 1, -1, s);
+    k_scale_store<<<f->nblk, BLOCK, 0, s>>>(f->f64, f->ahat + (size_t)c * pd.D, pd.D, 1.0 / (double)pd.D);
+    count_launch();
+  }
+  CK_LAUNCH();
+}
+
+// set-up from taps: scatter A~ to the table, inverse DFT (unnormalised) gives the grid samples
+__global__ void k_scatter_taps(const PlanDev* pdp, int comp, double2* ahat) {
+  const PlanDev& p = *pdp;
+  for (int t = threadIdx.x; t < p.ntaps; t += blockDim.x) {
+    int e = 0;
+    for (int ax = 0; ax < p.n; ++ax) {
+      const int mj = p.m[t][ax];
+      e += (mj < 0 ? mj + p.N[ax] : mj) * p.stride[ax];
+    }
+    ahat[(size_t)comp * p.D + e] = p.coef64[(size_t)t * p.ncomp + comp];
+  }
+}
+
+__global__ void k_grid_from_z(const PlanDev* pdp, const double2* z, int comp, double* c64, float* c32) {
+  const PlanDev& p = *pdp;
+  const int D = p.D;
+  const double inv = 1.0 / (double)D;
+  for (int e = blockIdx.x * BLOCK + threadIdx.x; e < D; e += gridDim.x * BLOCK) {
+    const double v = z[e].x;
+    c64[(size_t)comp * D + e] = v * inv;
+    c32[(size_t)comp * D + e] = (float)(v * inv);
+  }
+}
+
+void fft_set_taps(FftPlan* f, const PlanDev& pd, const PlanDev* pdp, cudaStream_t s) {
+  CK(cudaMemsetAsync(f->ahat, 0, (size_t)f->ncomp * pd.D * sizeof(double2), s));
+  for (int c = 0; c < f->ncomp; ++c) {
+    k_scatter_taps<<<1, BLOCK, 0, s>>>(pdp, c, f->ahat);
+    count_launch();
+    CK(cudaMemcpyAsync(f->f64, f->ahat + (size_t)c * pd.D, (size_t)pd.D * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+    fft_nd<double>(f->f64, pd.n, pd.N, 1, +1, s);
+    k_grid_from_z<<<f->nblk, BLOCK, 0, s>>>(pdp, f->f64, c, f->coef64, f->coef32);
+    count_launch();
+  }
+  CK_LAUNCH();
+}
+
+// Jacobi diagonal q(k) = lambda(k)^T A~_0 lambda(k); the Frobenius diagonal is not built on this backend
+// (frob = 0 marks it). Reduces min |lambda|^2 and min q/|lambda|^2 over k != 0 and the smallest Cholesky pivot of
+// A over the grid nodes into partials; k_diag_fft_final writes out[0..2].
+__global__ void __launch_bounds__(BLOCK) k_diag_fft(const PlanDev* pdp, const double2* ahat, const double* c64,
+                                                    double* jac, double* frob, float* jac32, float* frob32,
+                                                    double* part) {
+  const PlanDev& p = *pdp;
+  const int D = p.D, d = p.d;
+  double a0[MAXD][MAXD];
+  for (int a = 0; a < MAXD; ++a)
+    for (int b = 0; b < MAXD; ++b) {
+      double v = 0.0;
+      if (a < d && b < d) {
+        if (p.kind == QP_COEF_SCALAR) v = (a == b) ? ahat[0].x : 0.0;
+        else if (p.kind == QP_COEF_DIAG) v = (a == b) ? ahat[(size_t)a * D].x : 0.0;
+        else v = ahat[(size_t)sym_idx(a, b, d) * D].x;
+      }
+      a0[a][b] = v;
+    }
+  double red[3] = {DBL_MAX, DBL_MAX, DBL_MAX};
+  for (int e = blockIdx.x * BLOCK + threadIdx.x; e < D; e += gridDim.x * BLOCK) {
+    double lk[MAXD];
+    int ib[MAXN];
+    lambda_of<double>(p, e, lk, ib);
+    double q = 0.0, l2 = 0.0;
+    for (int a = 0; a < d; ++a) {
+      l2 += lk[a] * lk[a];
+      for (int b = 0; b < d; ++b) q += lk[a] * a0[a][b] * lk[b];
+    }
+    double mj = 0.0;
+    if (e != 0) {
+      mj = q != 0.0 ? 1.0 / q : 0.0;
+      red[0] = fmin(red[0], l2);
+      red[1] = fmin(red[1], l2 > 0.0 ? q / l2 : -1.0);
+    }
+    jac[e] = mj;
+    frob[e] = 0.0;
+    jac32[e] = (float)mj;
+    frob32[e] = 0.0f;
+    // Cholesky pivots of A(y_e) = D * coef (symmetric d x d)
+    double A[MAXD][MAXD], L[MAXD][MAXD];
+    for (int a = 0; a < d; ++a)
+      for (int b = 0; b < d; ++b) A[a][b] = coef_at<double>(p.kind, d, c64, D, e, a, b) * (double)D;
+    double piv = DBL_MAX;
+    for (int i = 0; i < d; ++i)
+      for (int j = 0; j <= i; ++j) {
+        double sdot = A[i][j];
+        for (int k = 0; k < j; ++k) sdot -= L[i][k] * L[j][k];
+        if (i == j) {
+          piv = fmin(piv, sdot);
+          L[i][i] = sdot > 0.0 ? sqrt(sdot) : 1.0;
+        } else {
+          L[i][j] = sdot / L[j][j];
+        }
+      }
+    red[2] = fmin(red[2], piv);
+  }
+  block_reduce<3, true>(red);
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 3; ++q) part[(size_t)q * gridDim.x + blockIdx.x] = red[q];
+}
+
+__global__ void k_diag_fft_final(const double* part, int nb, double* out) {
+  double v[3] = {DBL_MAX, DBL_MAX, DBL_MAX};
+  for (int i = threadIdx.x; i < nb; i += BLOCK)
+    for (int q = 0; q < 3; ++q) v[q] = fmin(v[q], part[(size_t)q * nb + i]);
+  block_reduce<3, true>(v);
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 3; ++q) out[q] = v[q];
+}
+
+void fft_diag(FftPlan* f, const PlanDev*, const PlanDev* pdp, double* jac, double* frob, float* jac32, float* frob32,
+              double* out, cudaStream_t s) {
+  k_diag_fft<<<f->nblk, BLOCK, 0, s>>>(pdp, f->ahat, f->coef64, jac, frob, jac32, frob32, f->part);
+  k_diag_fft_final<<<1, BLOCK, 0, s>>>(f->part, f->nblk, out);
+  count_launch(2);
+  CK_LAUNCH();
+}
+
+// ---- apply: gradient -> inverse DFT -> A(y) / D -> DFT -> divergence
+
+// g[b][r] = lambda_b * h[r]
+template <typename T>
+__global__ void __launch_bounds__(BLOCK) k_grad(const PlanDev* pdp, int nrhs, const cplx<T>* h, cplx<T>* g) {
+  const PlanDev& p = *pdp;
+  const int D = p.D;
+  for (int e = blockIdx.x * BLOCK + threadIdx.x; e < D; e += gridDim.x * BLOCK) {
+    T lk[MAXD];
+    int ib[MAXN];
+    lambda_of<T>(p, e, lk, ib);
+    for (int r = 0; r < nrhs; ++r) {
+      const cplx<T> hv = h[(size_t)r * D + e];
+      for (int b = 0; b < p.d; ++b) g[((size_t)b * nrhs + r) * D + e] = mk<T>(lk[b] * hv.x, lk[b] * hv.y);
+    }
+  }
+}
+
+// q[a][r] = sum_b (A^{ab}(y) / D) g[b][r], in place
+template <typename T>
+__global__ void __launch_bounds__(BLOCK) k_coef(const PlanDev* pdp, int nrhs, const T* coef, cplx<T>* g) {
+  const PlanDev& p = *pdp;
+  const int D = p.D, d = p.d, kind = p.kind;
+  for (int e = blockIdx.x * BLOCK + threadIdx.x; e < D; e += gridDim.x * BLOCK) {
+    T A[MAXD][MAXD];
+#pragma unroll
+    for (int a = 0; a < MAXD; ++a)
+#pragma unroll
+      for (int b = 0; b < MAXD; ++b) A[a][b] = (a < d && b < d) ? coef_at<T>(kind, d, coef, D, e, a, b) : T(0);
+    for (int r = 0; r < nrhs; ++r) {
+      cplx<T> gv[MAXD];
+#pragma unroll
+      for (int b = 0; b < MAXD; ++b) gv[b] = b < d ? g[((size_t)b * nrhs + r) * D + e] : mk<T>(0, 0);
+#pragma unroll
+      for (int a = 0; a < MAXD; ++a) {
+        if (a < d) {
+          cplx<T> q = mk<T>(0, 0);
+#pragma unroll
+          for (int b = 0; b < MAXD; ++b) {
+            q.x = fma(A[a][b], gv[b].x, q.x);
+            q.y = fma(A[a][b], gv[b].y, q.y);
+          }
+          g[((size_t)a * nrhs + r) * D + e] = q;
+        }
+      }
+    }
+  }
+}
+
+// w[r] = sum_a lambda_a * q[a][r]
+template <typename T>
+__global__ void __launch_bounds__(BLOCK) k_div(const PlanDev* pdp, int nrhs, const cplx<T>* g, cplx<T>* w) {
+  const PlanDev& p = *pdp;
+  const int D = p.D;
+  for (int e = blockIdx.x * BLOCK + threadIdx.x; e < D; e += gridDim.x * BLOCK) {
+    T lk[MAXD];
+    int ib[MAXN];
+    lambda_of<T>(p, e, lk, ib);
+    for (int r = 0; r < nrhs; ++r) {
+      cplx<T> acc = mk<T>(0, 0);
+      for (int a = 0; a < p.d; ++a) {
+        const cplx<T> q = g[((size_t)a * nrhs + r) * D + e];
+        acc.x = fma(lk[a], q.x, acc.x);
+        acc.y = fma(lk[a], q.y, acc.y);
+      }
+      w[(size_t)r * D + e] = acc;
+    }
+  }
+}
+
+template <typename T> static cplx<T>* fields_of(FftPlan* f);
+template <> double2* fields_of<double>(FftPlan* f) { return f->f64; }
+template <> float2* fields_of<float>(FftPlan* f) { return f->f32; }
+template <typename T> static const T* coef_of(FftPlan* f);
+template <> const double* coef_of<double>(FftPlan* f) { return f->coef64; }
+template <> const float* coef_of<float>(FftPlan* f) { return f->coef32; }
+
+template <typename T>
+void fft_apply(FftPlan* f, const PlanDev& pd, const PlanDev* pdp, const cplx<T>* h, cplx<T>* w, int nrhs,
+               cudaStream_t s) {
+  cplx<T>* g = fields_of<T>(f);
+  if (!g || nrhs > f->max_rhs)
+    raise(QP_ERR_INVALID_ARG, "FFT plan has no workspace for this precision / number of right-hand sides");
+  k_grad<T><<<f->nblk, BLOCK, 0, s>>>(pdp, nrhs, h, g);
+  count_launch();
+  fft_nd<T>(g, pd.n, pd.N, (long long)pd.d * nrhs, +1, s);
+  k_coef<T><<<f->nblk, BLOCK, 0, s>>>(pdp, nrhs, coef_of<T>(f), g);
+  count_launch();
+  fft_nd<T>(g, pd.n, pd.N, (long long)pd.d * nrhs, -1, s);
+  k_div<T><<<f->nblk, BLOCK, 0, s>>>(pdp, nrhs, g, w);
+  count_launch();
+  CK_LAUNCH();
+}
+template void fft_apply<double>(FftPlan*, const PlanDev&, const PlanDev*, const double2*, double2*, int, cudaStream_t);
+template void fft_apply<float>(FftPlan*, const PlanDev&, const PlanDev*, const float2*, float2*, int, cudaStream_t);
+
+// F_j(k) = i sum_a lambda_a(k) A~^{aj}_k, F_j(0) = 0
+__global__ void __launch_bounds__(BLOCK) k_rhs_fft(const PlanDev* pdp, const double2* ahat, int j0, int nrhs,
+                                                   double2* F) {
+  const PlanDev& p = *pdp;
+  const int D = p.D, d = p.d;
+  for (int e = blockIdx.x * BLOCK + threadIdx.x; e < D; e += gridDim.x * BLOCK) {
+    double lk[MAXD];
+    int ib[MAXN];
+    lambda_of<double>(p, e, lk, ib);
+    for (int jj = 0; jj < nrhs; ++jj) {
+      const int j = j0 + jj;
+      double2 z = make_double2(0.0, 0.0);
+      for (int a = 0; a < d; ++a) {
+        int comp = -1;
+        if (p.kind == QP_COEF_SCALAR) comp = a == j ? 0 : -1;
+        else if (p.kind == QP_COEF_DIAG) comp = a == j ? a : -1;
+        else comp = sym_idx(a, j, d);
+        if (comp < 0) continue;
+        const double2 c = ahat[(size_t)comp * D + e];
+        z.x += lk[a] * c.x;
+        z.y += lk[a] * c.y;
+      }
+      F[(size_t)jj * D + e] = e == 0 ? make_double2(0.0, 0.0) : make_double2(-z.y, z.x);
+    }
+  }
+}
+
+void fft_rhs(FftPlan* f, const PlanDev&, const PlanDev* pdp, int j0, int nrhs, double2* F, cudaStream_t s) {
+  k_rhs_fft<<<f->nblk, BLOCK, 0, s>>>(pdp, f->ahat, j0, nrhs, F);
+  count_launch();
+  CK_LAUNCH();
+}
+
+// A*_ij = A~^{ij}_0 + i sum_k sum_b A~^{ib}_{-k} lambda_b(k) U_j(k): block partials, then a fixed-order final sum.
+__global__ void __launch_bounds__(BLOCK) k_astar_fft(const PlanDev* pdp, const double2* ahat, const double2* U,
+                                                     double* part) {
+  const PlanDev& p = *pdp;
+  const int D = p.D, d = p.d;
+  double v[2 * MAXD * MAXD];
+#pragma unroll
+  for (int q = 0; q < 2 * MAXD * MAXD; ++q) v[q] = 0.0;
+  for (int e = blockIdx.x * BLOCK + threadIdx.x; e < D; e += gridDim.x * BLOCK) {
+    double lk[MAXD];
+    int ib[MAXN];
+    lambda_of<double>(p, e, lk, ib);
+    int eneg = 0;   // storage index of -k
+    for (int ax = 0; ax < p.n; ++ax) eneg += ((p.N[ax] - ib[ax]) % p.N[ax]) * p.stride[ax];
+#pragma unroll
+    for (int i = 0; i < MAXD; ++i) {
+      if (i >= d) continue;
+      double2 s = make_double2(0.0, 0.0);   // sum_b A~^{ib}_{-k} lambda_b(k)
+      for (int b = 0; b < d; ++b) {
+        int comp = -1;
+        if (p.kind == QP_COEF_SCALAR) comp = i == b ? 0 : -1;
+        else if (p.kind == QP_COEF_DIAG) comp = i == b ? i : -1;
+        else comp = sym_idx(i, b, d);
+        if (comp < 0) continue;
+        const double2 c = ahat[(size_t)comp * D + eneg];
+        s.x += c.x * lk[b];
+        s.y += c.y * lk[b];
+      }
+#pragma unroll
+      for (int j = 0; j < MAXD; ++j) {
+        if (j >= d) continue;
+        const double2 u = U[(size_t)j * D + e];
+        const double pr = s.x * u.x - s.y * u.y, pim = s.x * u.y + s.y * u.x;
+        v[2 * (i * MAXD + j)] += -pim;
+        v[2 * (i * MAXD + j) + 1] += pr;
+      }
+    }
+  }
+  block_reduce<2 * MAXD * MAXD>(v);
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 2 * MAXD * MAXD; ++q) part[(size_t)q * gridDim.x + blockIdx.x] = v[q];
+}
+
+__global__ void k_astar_fft_final(const PlanDev* pdp, const double2* ahat, const double* part, int nb, double* out) {
+  const PlanDev& p = *pdp;
+  const int D = p.D, d = p.d;
+  double v[2 * MAXD * MAXD];
+#pragma unroll
+  for (int q = 0; q < 2 * MAXD * MAXD; ++q) v[q] = 0.0;
+  for (int i = threadIdx.x; i < nb; i += BLOCK)
+#pragma unroll
+    for (int q = 0; q < 2 * MAXD * MAXD; ++q) v[q] += part[(size_t)q * nb + i];
+  block_reduce<2 * MAXD * MAXD>(v);
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < d; ++i)
+      for (int j = 0; j < d; ++j) {
+        int comp = -1;
+        if (p.kind == QP_COEF_SCALAR) comp = i == j ? 0 : -1;
+        else if (p.kind == QP_COEF_DIAG) comp = i == j ? i : -1;
+        else comp = sym_idx(i, j, d);
+        const double2 c0 = comp >= 0 ? ahat[(size_t)comp * D] : make_double2(0.0, 0.0);
+        out[2 * (i * d + j)] = c0.x + v[2 * (i * MAXD + j)];
+        out[2 * (i * d + j) + 1] = c0.y + v[2 * (i * MAXD + j) + 1];
+      }
+  }
+}
+
+void fft_astar(FftPlan* f, const PlanDev&, const PlanDev* pdp, const double2* U, double* out, cudaStream_t s) {
+  k_astar_fft<<<f->nblk, BLOCK, 0, s>>>(pdp, f->ahat, U, f->part);
+  k_astar_fft_final<<<1, BLOCK, 0, s>>>(pdp, f->ahat, f->part, f->nblk, out);
+  count_launch(2);
+  CK_LAUNCH();
+}
+
 }  // namespace qp

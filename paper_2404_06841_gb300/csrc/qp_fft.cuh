@@ -7,21 +7,24 @@ namespace qp {
 
 struct FftPlan;
 
-FftPlan* fft_plan_create(const PlanDev& pd, int precisions, cudaStream_t s);
+// pd: host copy of the plan description; pdp: its device copy (must be uploaded before the set-up calls).
+FftPlan* fft_plan_create(const PlanDev& pd, int precisions, int max_rhs);
 void fft_plan_destroy(FftPlan* f);
 int64_t fft_plan_bytes(const FftPlan* f);
+bool fft_supported(int N);
 // Coefficient from device grid samples (ncomp x D doubles, C order) or from the plan's tap list.
-void fft_set_grid(FftPlan* f, const PlanDev& pd, const double* grid, cudaStream_t s);
-void fft_set_taps(FftPlan* f, const PlanDev& pd, cudaStream_t s);
-// Jacobi / Frobenius diagonals and the set-up checks into out[0..2]: min |lambda|^2, min q/|lambda|^2 over
-// k != 0, and the smallest eigenvalue of A over the grid nodes.
-void fft_diag(FftPlan* f, const PlanDev& pd, double* jac, double* frob, float* jac32, float* frob32, double* out,
-              cudaStream_t s);
+void fft_set_grid(FftPlan* f, const PlanDev& pd, const PlanDev* pdp, const double* grid, cudaStream_t s);
+void fft_set_taps(FftPlan* f, const PlanDev& pd, const PlanDev* pdp, cudaStream_t s);
+// Jacobi diagonal (the Frobenius one is not built on this backend: frob = 0) and the set-up checks into
+// out[0..2]: min |lambda|^2, min q/|lambda|^2 over k != 0, smallest Cholesky pivot of A over the nodes.
+void fft_diag(FftPlan* f, const PlanDev* pd, const PlanDev* pdp, double* jac, double* frob, float* jac32,
+              float* frob32, double* out, cudaStream_t s);
 // w = Q h for nrhs vectors of the plan.
 template <typename T>
-void fft_apply(FftPlan* f, const PlanDev& pd, const cplx<T>* h, cplx<T>* w, int nrhs, cudaStream_t s);
-void fft_rhs(FftPlan* f, const PlanDev& pd, int j0, int nrhs, double2* F, cudaStream_t s);
-void fft_astar(FftPlan* f, const PlanDev& pd, const double2* U, double* out, cudaStream_t s);
+void fft_apply(FftPlan* f, const PlanDev& pd, const PlanDev* pdp, const cplx<T>* h, cplx<T>* w, int nrhs,
+               cudaStream_t s);
+void fft_rhs(FftPlan* f, const PlanDev& pd, const PlanDev* pdp, int j0, int nrhs, double2* F, cudaStream_t s);
+void fft_astar(FftPlan* f, const PlanDev& pd, const PlanDev* pdp, const double2* U, double* out, cudaStream_t s);
 void fft_standalone(int n, const int* N, int count, void* data, int sign, int precision, cudaStream_t s);
 
 }  // namespace qp
