@@ -41,6 +41,8 @@ WORKLOADS = {
              "Jacobi-PCG to 1e-10", "fp64"),
     "cfg2": ("d=2 n=4 full SPD 2x2 grid coefficient (81-tap field, eigenvalues clamped to [0.5,5]), 32^4 modes, "
              "2 correctors, FP32 PCG in FP64 refinement to 1e-10", "refine"),
+    "cfg3": ("64 instances in one batched solve: 32 with d=1 n=2 P=(1,alpha) N in {64..512}, 32 with d=2 n=4 "
+             "N in {8..24}; scalar cosine coefficients; 96 correctors, FP32 PCG in FP64 refinement to 1e-10", "refine"),
     "cfg4": ("d=3 n=6 diag A, a_i=4+sum_j 0.5cos(th_j+phi_ij), 16^6 modes, 3 correctors, FP32 PCG in FP64 "
              "refinement to 1e-10", "refine"),
 }
@@ -48,6 +50,9 @@ FP64_PEAK_TFLOPS = 1.25      # nominal GB300 FP64 rate (CUDA cores); the FMA-loo
 
 
 def instance(name, N=None):
+    """The workload's instance (for the batched cfg3: its largest instance, used for samples and the apply)."""
+    if name == "cfg3":
+        return W.cfg3()[-1]
     return getattr(W, name)() if N is None else getattr(W, name)(N=N)
 
 
@@ -130,19 +135,41 @@ def run_ours(args, rank, world, local_rank):
     desc, default_mode = WORKLOADS[name]
     mode_name = args.mode or default_mode
     mode = qp.QP_MODE_FP64 if mode_name == "fp64" else qp.QP_MODE_FP32_REFINE
-    inst = instance(name, args.N)
-    tol = inst.tol
-    plan = qp.plan_from_instance(inst, exec_mode=qp.QP_EXEC_DIRECT if args.exec == "direct" else qp.QP_EXEC_GRAPH)
-    pinfo = qp.qp_plan_query(plan)
+    exec_mode = qp.QP_EXEC_DIRECT if args.exec == "direct" else qp.QP_EXEC_GRAPH
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2 (129 MiB)
+    if name == "cfg3":
+        insts = W.cfg3()
+        tol = 1e-10
+        plans = [qp.plan_from_instance(i, exec_mode=exec_mode) for i in insts]
+        batch = qp.qp_batch_create(plans)
+        unit_D = [i.D for i in insts for _ in range(i.d)]
+        inst = insts[-1]
+        plan = plans[-1]
+        total_D = sum(unit_D)
 
-    def step():
-        return qp.qp_homogenized(plan, tol=tol, mode=mode, maxit=2000)
+        def step():
+            As, infs = qp.qp_batch_homogenized(batch, tol=tol, mode=mode, maxit=2000)
+            return As, infs
+
+        def dof_iters(infs):
+            return sum(D * (i["iterations"] + i["outer_iterations"]) for D, i in zip(unit_D, infs))
+    else:
+        inst = instance(name, args.N)
+        tol = inst.tol
+        plan = qp.plan_from_instance(inst, exec_mode=exec_mode)
+        total_D = inst.D * inst.d
+
+        def step():
+            return qp.qp_homogenized(plan, tol=tol, mode=mode, maxit=2000)
+
+        def dof_iters(infs):
+            return sum(inst.D * (i["iterations"] + i["outer_iterations"]) for i in infs)
+    pinfo = qp.qp_plan_query(plan)
 
     for _ in range(max(args.warmup, 3)):
         A, infos = step()
-    dof_iters_step = sum(inst.D * (i["iterations"] + i["outer_iterations"]) for i in infos)
+    dof_iters_step = dof_iters(infos)
 
     sampler = ClockSampler(None)
     sampler.start()
@@ -160,7 +187,7 @@ def run_ours(args, rank, world, local_rank):
         starts[k].record(stream)
         A, infos = step()
         ends[k].record(stream)
-        total_dof_iters += sum(inst.D * (i["iterations"] + i["outer_iterations"]) for i in infos)
+        total_dof_iters += dof_iters(infos)
         max_rel = max(max_rel, max(i["rel_residual"] for i in infos))
     torch.cuda.synchronize()
     wall1 = time.perf_counter()
@@ -200,20 +227,20 @@ def run_ours(args, rank, world, local_rank):
         achieved = flops / (apply_ms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": None,
-                "kernel": "taps_apply_kernel<double> (FP64 CUDA cores)", "apply_us": round(apply_ms * 1e3, 2),
+                "kernel": "k_apply_plain<double> (taps stencil, FP64 pipe), timed alone on the bench stream", "apply_us": round(apply_ms * 1e3, 2),
                 "flops_per_launch": flops, "peak_source": "nominal FP64 1.25 TFLOP/s (FMA probe: 1.196)"}
     else:
         bytes_ = 2 * nrhs * inst.D * (16 if prec == qp.QP_FP64 else 8)
         achieved = bytes_ / (apply_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": round(achieved / pk["hbm_gbs"], 4), "traffic": None,
-                "kernel": "taps_apply_kernel<float>" if c.taps_k is not None else "fft passes",
+                "kernel": ("k_apply_plain<float> (taps stencil), timed alone" if c.taps_k is not None else "FFT-backend apply (all passes), timed alone"),
                 "apply_us": round(apply_ms * 1e3, 2), "bytes_per_launch": bytes_,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" + (" (fallback)" if pk.get("_fallback") else "")}
 
     # ---- end to end through the public API with host inputs: plan from host taps -> a* on the host
     e2e = None
-    if c.taps_k is not None:
+    if c.taps_k is not None and name != "cfg3":
         kk = np.ascontiguousarray(c.taps_k, dtype=np.int32)
         vv = np.ascontiguousarray(np.asarray(c.taps_val, dtype=np.complex128))
         h2d = kk.nbytes + vv.nbytes + inst.P.nbytes + 4 * inst.n
@@ -234,7 +261,7 @@ def run_ours(args, rank, world, local_rank):
     # ---- the other precision mode on the same workload (time-to-a*), for the FP64-vs-refinement comparison
     variants = {}
     other = "refine" if mode_name == "fp64" else "fp64"
-    if not args.no_variants:
+    if not args.no_variants and name != "cfg3":
         om = qp.QP_MODE_FP32_REFINE if other == "refine" else qp.QP_MODE_FP64
         for _ in range(3):
             qp.qp_homogenized(plan, tol=tol, mode=om, maxit=2000)
@@ -270,13 +297,15 @@ def run_ours(args, rank, world, local_rank):
         "vs_baseline": None,
         "dtype": "f64" if mode_name == "fp64" else "f32+f64-refine",
         "data": "synthetic",
-        "config": {"workload": name + ": " + desc, "D": inst.D, "correctors": inst.d, "mode": mode_name,
+        "config": {"workload": name + ": " + desc, "D": total_D if name == "cfg3" else inst.D,
+                   "correctors": len(infos), "mode": mode_name,
                    "backend": pinfo["backend"], "tol": tol, "l2": "flushed before every step (256 MiB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "time_to_astar_ms": ms / args.steps,
         "iterations_per_step": [(i["iterations"], i["outer_iterations"]) for i in infos],
         "max_rel_residual": max_rel,
-        "astar": np.round(A.real, 14).tolist(),
+        "astar": (np.round(A.real, 14).tolist() if name != "cfg3" else
+                  [np.round(a, 12).tolist() for a in (A[:2] + A[-2:])]),
         "wall_s_timed_region": wall1 - wall0,
         "roofline": roof,
         "cpu_baseline": cpu,
@@ -285,7 +314,12 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": int(launches),
         "variants": variants,
     }
-    qp.qp_plan_destroy(plan)
+    if name == "cfg3":
+        qp.qp_batch_destroy(batch)
+        for p_ in plans:
+            qp.qp_plan_destroy(p_)
+    else:
+        qp.qp_plan_destroy(plan)
     return out
 
 

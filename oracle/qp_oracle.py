@@ -503,8 +503,8 @@ def timed_pcg_sample(inst, max_seconds: float = 15.0, precond: str = "jacobi"):
     op = Operator(inst)
     M = jacobi_inverse(op.P, op.N, op.Ahat) if precond == "jacobi" else frobenius_diag(op.P, op.N, op.Ahat)
     F = corrector_rhs(op.P, op.N, op.Ahat, 0)
+    op(F)                                   # warm-up (first-call costs), then one timed apply sizes the sample
     t0 = time.perf_counter()
-    # one apply to size the sample
     op(F)
     t1 = time.perf_counter()
     per_it = max(t1 - t0, 1e-6)
