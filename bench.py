@@ -135,7 +135,8 @@ def run_ours(args, rank, world, local_rank):
     desc, default_mode = WORKLOADS[name]
     mode_name = args.mode or default_mode
     mode = qp.QP_MODE_FP64 if mode_name == "fp64" else qp.QP_MODE_FP32_REFINE
-    exec_mode = qp.QP_EXEC_DIRECT if args.exec == "direct" else qp.QP_EXEC_GRAPH
+    exec_mode = {"auto": qp.QP_EXEC_AUTO, "graph": qp.QP_EXEC_GRAPH, "direct": qp.QP_EXEC_DIRECT,
+                 "persistent": qp.QP_EXEC_PERSISTENT}[args.exec]
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2 (129 MiB)
     if name == "cfg3":
@@ -298,7 +299,7 @@ def run_ours(args, rank, world, local_rank):
         "dtype": "f64" if mode_name == "fp64" else "f32+f64-refine",
         "data": "synthetic",
         "config": {"workload": name + ": " + desc, "D": total_D if name == "cfg3" else inst.D,
-                   "correctors": len(infos), "mode": mode_name,
+                   "correctors": len(infos), "mode": mode_name, "exec": args.exec,
                    "backend": pinfo["backend"], "tol": tol, "l2": "flushed before every step (256 MiB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "time_to_astar_ms": ms / args.steps,
@@ -397,8 +398,9 @@ def main():
                     help="profiling aid: build the plan and launch only the stiffness apply --steps times")
     ap.add_argument("--N", type=int, default=None, help="modes per axis (overrides the workload's N)")
     ap.add_argument("--precision", default=None, choices=["fp64", "fp32"], help="with --apply-only")
-    ap.add_argument("--exec", default="graph", choices=["graph", "direct"],
-                    help="graph: one CUDA-graph launch per solve (default); direct: kernel by kernel (profilers)")
+    ap.add_argument("--exec", default="auto", choices=["auto", "persistent", "graph", "direct"],
+                    help="auto (default): persistent where it applies, else graph; persistent: one cooperative "
+                         "launch per solve; graph: one CUDA-graph launch per solve; direct: kernel by kernel")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -52,7 +52,7 @@ enum { QP_BACKEND_AUTO = 0, QP_BACKEND_TAPS = 1, QP_BACKEND_FFT = 2 };
 enum { QP_FP64 = 0, QP_FP32 = 1 };
 enum { QP_PRECOND_JACOBI = 0, QP_PRECOND_FROBENIUS = 1 };
 enum { QP_MODE_FP64 = 0, QP_MODE_FP32_REFINE = 1 };
-enum { QP_EXEC_GRAPH = 0, QP_EXEC_DIRECT = 1 };
+enum { QP_EXEC_AUTO = 0, QP_EXEC_DIRECT = 1, QP_EXEC_GRAPH = 2, QP_EXEC_PERSISTENT = 3 };
 enum { QP_MAX_N_AXES = 6, QP_MAX_D = 3, QP_MAX_RHS = 4, QP_MAX_TAPS = 256 };
 
 typedef struct qp_plan qp_plan;     /* opaque; owns every internal device buffer */
@@ -79,9 +79,14 @@ typedef struct {
   int backend;      /* QP_BACKEND_*: AUTO picks TAPS for a tap coefficient, FFT for a grid one */
   int max_rhs;      /* right-hand sides solved together, 1..QP_MAX_RHS; 0 = d */
   int precisions;   /* workspace: bit 0 = FP64 solve, bit 1 = FP32 (refinement inner) solve; 0 = both */
-  int exec;         /* QP_EXEC_GRAPH (default): a solve is one CUDA-graph launch whose loops are conditional WHILE
-                       nodes; QP_EXEC_DIRECT: the same kernels launched one by one, the host polling convergence
-                       (for profilers and callers that cannot launch graphs) */
+  int exec;         /* how a solve is driven (the iterates are bitwise the same in every mode):
+                       QP_EXEC_GRAPH: one CUDA-graph launch whose loops are conditional WHILE nodes (three kernels
+                       per PCG iteration); QP_EXEC_PERSISTENT: one cooperative launch of a persistent kernel that
+                       meets at grid barriers (taps backend, single-plan solves; others use the graph);
+                       QP_EXEC_DIRECT: the graph's kernels launched one by one, the host polling convergence (for
+                       profilers and callers that cannot launch graphs); QP_EXEC_AUTO (0, default): PERSISTENT
+                       where it applies and every chunk of modes gets its own resident block, else GRAPH. A persistent solve whose barrier wait exceeds its limit
+                       returns QP_ERR_TIMEOUT. */
 } qp_options;
 
 typedef struct {
@@ -183,6 +188,12 @@ const char* qp_last_error(void);
 
 /* Number of CUDA kernels this library has launched in this process so far (all threads, all plans). */
 uint64_t qp_launch_count(void);
+
+/* Limit, in seconds, of each grid-barrier wait of a persistent solve (QP_EXEC_PERSISTENT / AUTO); default 2.
+ * A wait covers one phase (one stiffness apply or one vector update) of the slowest block, so the limit only
+ * has to exceed the longest phase. A solve that exceeds it returns QP_ERR_TIMEOUT with its outputs undefined;
+ * the device stays usable. Process-wide; 0 < seconds <= 3600, else QP_ERR_INVALID_ARG. */
+qp_status qp_set_barrier_timeout(double seconds);
 
 #ifdef __cplusplus
 }

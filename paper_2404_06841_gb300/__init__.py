@@ -27,14 +27,14 @@ QP_BACKEND_AUTO, QP_BACKEND_TAPS, QP_BACKEND_FFT = 0, 1, 2
 QP_FP64, QP_FP32 = 0, 1
 QP_PRECOND_JACOBI, QP_PRECOND_FROBENIUS = 0, 1
 QP_MODE_FP64, QP_MODE_FP32_REFINE = 0, 1
-QP_EXEC_GRAPH, QP_EXEC_DIRECT = 0, 1
+QP_EXEC_AUTO, QP_EXEC_DIRECT, QP_EXEC_GRAPH, QP_EXEC_PERSISTENT = 0, 1, 2, 3
 KIND_CODES = {"scalar": QP_COEF_SCALAR, "diag": QP_COEF_DIAG, "sym": QP_COEF_SYM}
 
 # Every symbol include/qp.h declares (checked by the test suite).
 EXPORTS = ("qp_plan_create", "qp_plan_destroy", "qp_plan_query", "qp_apply_stiffness", "qp_corrector_rhs",
            "qp_pcg_solve", "qp_homogenized_reduce", "qp_homogenized", "qp_fft", "qp_batch_create",
            "qp_batch_homogenized", "qp_batch_destroy", "qp_last_error", "qp_launch_count",
-           "qp_pcg_solve_taps_static")
+           "qp_pcg_solve_taps_static", "qp_set_barrier_timeout")
 
 
 class qp_coeff(C.Structure):
@@ -92,6 +92,7 @@ def load_library(path: str = LIB_PATH):
         "qp_batch_destroy": [vp],
         "qp_pcg_solve_taps_static": [i, i, dp, ip, C.POINTER(qp_coeff), i, vp, vp, C.POINTER(qp_solve_opts),
                                      C.POINTER(qp_solve_info), vp],
+        "qp_set_barrier_timeout": [C.c_double],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -171,7 +172,7 @@ def _coeff_struct(coeff, d, keep):
     return c
 
 
-def qp_plan_create(d, n, P, N, coeff, backend=QP_BACKEND_AUTO, max_rhs=0, precisions=0, exec_mode=QP_EXEC_GRAPH,
+def qp_plan_create(d, n, P, N, coeff, backend=QP_BACKEND_AUTO, max_rhs=0, precisions=0, exec_mode=QP_EXEC_AUTO,
                    stream=None) -> Plan:
     P = np.ascontiguousarray(P, dtype=np.float64).reshape(-1)
     Narr = np.ascontiguousarray(N, dtype=np.int32).reshape(-1)
@@ -333,6 +334,11 @@ def qp_last_error() -> str:
 
 def qp_launch_count() -> int:
     return int(_lib.qp_launch_count())
+
+
+def qp_set_barrier_timeout(seconds: float) -> None:
+    """Limit of each grid-barrier wait of a persistent solve (process-wide; default 2 s)."""
+    _check(_lib.qp_set_barrier_timeout(float(seconds)))
 
 
 def plan_from_instance(inst, **kw) -> Plan:

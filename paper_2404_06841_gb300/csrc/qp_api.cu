@@ -123,6 +123,8 @@ struct Entry {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int fixed_nodes = 0, body_nodes = 0, outer_nodes = 0;
+  int pgrid = 0;          // > 0: the solve is one persistent launch of this many blocks
+  size_t psmem = 0;
   ~Entry() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
@@ -141,6 +143,9 @@ struct Solver {
   unsigned* ucount = nullptr;
   unsigned* kcount = nullptr;
   int* ndone = nullptr;
+  unsigned* pbar = nullptr;              // persistent solve: grid barrier words
+  int* perr = nullptr;                   // persistent solve: barrier time-out flag
+  int* h_perr = nullptr;                 // pinned mirror
   cudaStream_t cap = nullptr;
   bool graphs_ok = true;
   std::vector<void*> allocs;
@@ -151,17 +156,21 @@ struct Solver {
     ucount = (unsigned*)alloc(nu * sizeof(unsigned));
     kcount = (unsigned*)alloc(64);
     ndone = (int*)alloc(64);
+    pbar = (unsigned*)alloc(64);
+    perr = (int*)alloc(64);
     CK(cudaMemset(st, 0, nu * MAXR * sizeof(RhsSt)));
     CK(cudaMemset(ucount, 0, nu * sizeof(unsigned)));
     CK(cudaMemset(kcount, 0, 64));
     CK(cudaMemset(ndone, 0, 64));
     CK(cudaMallocHost(&h_st, nu * MAXR * sizeof(RhsSt)));
+    CK(cudaMallocHost(&h_perr, sizeof(int)));
     CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
   }
   ~Solver() {
     cache.clear();
     if (cap) cudaStreamDestroy(cap);
     if (h_st) cudaFreeHost(h_st);
+    if (h_perr) cudaFreeHost(h_perr);
     for (void* p : allocs) cudaFree(p);
   }
   void* alloc(size_t b) {
@@ -435,6 +444,7 @@ struct Units {
   int max_coef = 1;
   int max_rhs = 1;
   bool direct = false;    // launch kernels directly (host-driven loops) instead of recording a graph
+  int exec = QP_EXEC_GRAPH;  // QP_EXEC_AUTO / PERSISTENT: a single taps unit may run as one persistent launch
 };
 
 // One stiffness apply over all units at a level: the FFT passes of FFT-backend units (they write w), then the
@@ -688,7 +698,7 @@ Entry& get_entry(Solver* sv, const Units& us, const Key& key) {
   bd.chunk_unit = (const int*)up(chunk_unit.data(), chunk_unit.size() * sizeof(int));
   {
     void* pp = nullptr;
-    CK(cudaMalloc(&pp, (size_t)NSLOT * nchunks * sizeof(double)));
+    CK(cudaMalloc(&pp, (size_t)NSLOT_PERSIST * nchunks * sizeof(double)));
     en->allocs.push_back(pp);
     bd.partials = (double*)pp;
   }
@@ -701,7 +711,25 @@ Entry& get_entry(Solver* sv, const Units& us, const Key& key) {
   bd.maxit = key.maxit;
   bd.max_outer = key.max_outer;
   en->nblk = nchunks;
-  if (sv->graphs_ok && !us.direct) {
+  if ((us.exec == QP_EXEC_AUTO || us.exec == QP_EXEC_PERSISTENT) && nu == 1 && !us.direct) {
+    // every block of a cooperative launch is resident: at most the occupancy limit, at most one per chunk.
+    // AUTO takes the persistent form only when every chunk has its own resident block (small and medium
+    // problems, where launch and synchronisation latency dominate); larger solves keep the graph, whose
+    // kernels run at higher occupancy.
+    const size_t smem = persistent_smem(us.max_coef);
+    int capn = 0;
+    try {
+      capn = persistent_capacity(us.all_real, us.max_rhs, smem);
+    } catch (const QpError&) {
+      cudaGetLastError();
+      capn = 0;
+    }
+    if (capn > 0 && (us.exec == QP_EXEC_PERSISTENT || nchunks <= capn)) {
+      en->pgrid = std::min(capn, nchunks);
+      en->psmem = smem;
+    }
+  }
+  if (en->pgrid == 0 && sv->graphs_ok && !us.direct) {
     try {
       build_graph(us, *en, key, sv->cap);
     } catch (const QpError&) {
@@ -719,6 +747,9 @@ Entry& get_entry(Solver* sv, const Units& us, const Key& key) {
   return ref;
 }
 
+// Limit of one grid-barrier wait in the persistent solve (a wait covers one phase of the slowest block).
+std::atomic<double> g_barrier_timeout{2.0};
+
 struct SolveResult {
   std::vector<int> iters, outer, status;
   std::vector<double> rel, f2;
@@ -729,11 +760,20 @@ void run_solve(Solver* sv, const Units& us, const Key& key, cudaStream_t s, Solv
   Entry& en = get_entry(sv, us, key);
   int nslots = 0;
   for (int r : us.nrhs) nslots += r;
-  if (en.exec) CK(cudaGraphLaunch(en.exec, s));
-  else run_direct(us, en, key, nslots, s);
+  if (en.pgrid > 0) {
+    launch_persistent(en.bd, us.all_real, us.max_rhs, key.mode, key.warm != 0, sv->pbar, sv->perr,
+                      g_barrier_timeout.load(), en.pgrid, en.psmem, s);
+    CK(cudaMemcpyAsync(sv->h_perr, sv->perr, sizeof(int), cudaMemcpyDeviceToHost, s));
+  } else if (en.exec) {
+    CK(cudaGraphLaunch(en.exec, s));
+  } else {
+    run_direct(us, en, key, nslots, s);
+  }
   const size_t nu = us.plans.size();
   CK(cudaMemcpyAsync(sv->h_st, sv->st, nu * MAXR * sizeof(RhsSt), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  if (en.pgrid > 0 && *sv->h_perr != 0)
+    raise(QP_ERR_TIMEOUT, "persistent solve: a grid-barrier wait exceeded its limit");
   res = SolveResult();
   int max_it = 0, max_outer = 0, sum_inner_max = 0;
   for (size_t u = 0; u < nu; ++u)
@@ -798,6 +838,7 @@ Units single_units(qp_plan* p, int nrhs) {
   us.max_coef = std::max(1, p->coef_count);
   us.max_rhs = nrhs;
   us.direct = p->exec == QP_EXEC_DIRECT;
+  us.exec = p->backend == QP_BACKEND_TAPS ? p->exec : QP_EXEC_GRAPH;
   return us;
 }
 
@@ -879,6 +920,13 @@ const char* qp_last_error(void) { return g_err.c_str(); }
 
 uint64_t qp_launch_count(void) { return qp::g_launches.load(std::memory_order_relaxed); }
 
+qp_status qp_set_barrier_timeout(double seconds) {
+  API_BEGIN
+  if (!(seconds > 0.0 && seconds <= 3600.0)) raise(QP_ERR_INVALID_ARG, "barrier timeout must be in (0, 3600] s");
+  g_barrier_timeout.store(seconds);
+  API_END
+}
+
 qp_status qp_plan_create(int d, int n, const double* P, const int* N, const qp_coeff* coeff, const qp_options* opt,
                          void* stream, qp_plan** out) {
   API_BEGIN
@@ -897,8 +945,8 @@ qp_status qp_plan_create(int d, int n, const double* P, const int* N, const qp_c
   p->max_rhs = (opt && opt->max_rhs > 0) ? opt->max_rhs : d;
   if (p->max_rhs > MAXR) raise(QP_ERR_INVALID_ARG, "max_rhs must be <= 4");
   p->precisions = (opt && opt->precisions) ? (opt->precisions & 3) : 3;
-  p->exec = opt ? opt->exec : QP_EXEC_GRAPH;
-  if (p->exec != QP_EXEC_GRAPH && p->exec != QP_EXEC_DIRECT) raise(QP_ERR_INVALID_ARG, "unknown exec mode");
+  p->exec = opt ? opt->exec : QP_EXEC_AUTO;
+  if (p->exec < QP_EXEC_AUTO || p->exec > QP_EXEC_PERSISTENT) raise(QP_ERR_INVALID_ARG, "unknown exec mode");
   if (coeff->repr == QP_REPR_TAPS) {
     p->backend = (backend_req == QP_BACKEND_FFT) ? QP_BACKEND_FFT : QP_BACKEND_TAPS;
   } else if (coeff->repr == QP_REPR_GRID) {

@@ -173,14 +173,15 @@ __device__ __forceinline__ bool chunk_arrive(const BatchDev& b, int c, int u, co
   return last;
 }
 
-// In the completing block: sums every slot over the unit's chunks in a fixed order; thread 0 gets the sums.
+// In the completing block: sums every slot (slot0 .. slot0 + NV - 1) over the unit's chunks in a fixed order;
+// thread 0 gets the sums.
 template <int NV>
-__device__ __forceinline__ void unit_sums(const BatchDev& b, const UnitDev& un, double (&v)[NV]) {
+__device__ __forceinline__ void unit_sums(const BatchDev& b, const UnitDev& un, double (&v)[NV], int slot0 = 0) {
 #pragma unroll
   for (int q = 0; q < NV; ++q) v[q] = 0.0;
   for (int i = threadIdx.x; i < un.nchunk; i += BLOCK) {
 #pragma unroll
-    for (int q = 0; q < NV; ++q) v[q] += __ldcg(b.partials + (size_t)q * b.nchunks + un.chunk0 + i);
+    for (int q = 0; q < NV; ++q) v[q] += __ldcg(b.partials + (size_t)(slot0 + q) * b.nchunks + un.chunk0 + i);
   }
   block_reduce<NV>(v);
 }

@@ -41,6 +41,9 @@ constexpr int MAXT = QP_MAX_TAPS;
 constexpr int BLOCK = 256;           // threads per block of every elementwise / stencil kernel
 constexpr int NQ = 4;                // reduction quantities per right-hand side
 constexpr int NSLOT = MAXR * NQ;     // partial slots per chunk
+// the persistent solve keeps consecutive reductions in disjoint slots: init [0,12), (h,w) [12,16),
+// update [16,24), true residual [24,32)
+constexpr int NSLOT_PERSIST = 2 * NSLOT;
 
 template <typename T> struct V2;
 template <> struct V2<double> { using type = double2; };
@@ -108,7 +111,7 @@ struct BatchDev {
   const UnitDev* units;
   RhsSt* st;                            // [nunits * MAXR]
   const int* chunk_unit;                // [nchunks]
-  double* partials;                     // [NSLOT][nchunks]
+  double* partials;                     // [NSLOT][nchunks] ([NSLOT_PERSIST][nchunks] for the persistent solve)
   unsigned* ucount;                     // [nunits] chunk arrivals per unit
   unsigned* kcount;                     // [1] units finalized by the current kernel
   int* ndone;                           // [2]: right-hand sides done at the PCG level, at the outer level
@@ -147,5 +150,18 @@ void launch_pcg_update(const BatchDev& b, int maxr, int level, unsigned long lon
 void launch_pcg_hupdate(const BatchDev& b, int maxr, int level, int nblk, cudaStream_t s);
 void launch_refine_prep(const BatchDev& b, int nblk, cudaStream_t s);
 void launch_refine_accum(const BatchDev& b, int nblk, cudaStream_t s);
+// persistent solve of one taps unit (qp_persistent.cu): the kernel's argument
+struct PersistArgs {
+  BatchDev b;          // b.single: one unit in b.pu, its state in b.st[0 .. MAXR)
+  unsigned* bar;       // [0] arrivals, [1] generation (zeroed before the launch)
+  int* err;            // set on a barrier timeout (zeroed before the launch)
+  int mode;            // QP_MODE_FP64 or QP_MODE_FP32_REFINE
+  int warm;            // start from the U held in the plan (else U = 0)
+  unsigned long long timeout_ns;
+};
+size_t persistent_smem(int coef_count);
+int persistent_capacity(bool realc, int nr, size_t smem);
+void launch_persistent(const BatchDev& b, bool realc, int nr, int mode, bool warm, unsigned* bar, int* err,
+                       double timeout_s, int grid, size_t smem, cudaStream_t s);
 
 }  // namespace qp

@@ -27,10 +27,13 @@ def test_library_loads_and_exports_every_declared_symbol():
 def test_header_enums_match_binding():
     import paper_2404_06841_gb300 as qp
     src = open(os.path.join(ROOT, "include", "qp.h")).read()
-    for name in ("QP_OK", "QP_ERR_INVALID_ARG", "QP_ERR_SINGULAR_P", "QP_ERR_NOT_ELLIPTIC", "QP_ERR_BREAKDOWN",
-                 "QP_ERR_NO_CONVERGENCE", "QP_ERR_TIMEOUT", "QP_ERR_UNSUPPORTED", "QP_ERR_OOM", "QP_ERR_CUDA"):
-        m = re.search(r"\b%s\s*=\s*(\d+)" % name, src)
-        assert m and int(m.group(1)) == getattr(qp, name), name
+    pairs = re.findall(r"\b(QP_[A-Z0-9_]+)\s*=\s*(\d+)", src)
+    names = {n for n, _ in pairs}
+    assert {"QP_OK", "QP_ERR_CUDA", "QP_EXEC_AUTO", "QP_EXEC_PERSISTENT", "QP_MODE_FP32_REFINE"} <= names
+    for name, val in pairs:
+        if name.startswith("QP_MAX_"):
+            continue
+        assert getattr(qp, name) == int(val), name
 
 
 @pytest.mark.parametrize("d,n,N,msg", [
