@@ -220,14 +220,6 @@ bool is_23(int N) {
   return N == 1;
 }
 
-FastDiv make_fastdiv(uint32_t d) {
-  uint32_t L = 0;
-  while ((1ull << L) < d) ++L;
-  const uint32_t p = 31 + L;
-  const uint64_t m = ((1ull << p) + d - 1) / d;
-  return FastDiv{d, (uint32_t)m, p};
-}
-
 // Cholesky test of the real symmetric d x d matrix M (positive definite?).
 bool spd(const double M[MAXD][MAXD], int d) {
   double L[MAXD][MAXD] = {};

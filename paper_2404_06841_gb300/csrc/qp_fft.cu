@@ -374,6 +374,29 @@ void fft_standalone(int n, const int* N, int count, void* data, int sign, int pr
 
 // ------------------------------------------------------------------------------------------------ FFT backend
 
+// A pass of the fused apply over one group of consecutive axes (kernels below).
+struct GroupPass {
+  int mode;                 // GP_*
+  int sign;                 // GP_PLAIN: +1 inverse, -1 forward
+  int ng, j0;               // axes j0 .. j0 + ng - 1
+  int Ng[MAXN], sg[MAXN];   // their sizes; stride of each in the group position (product of later group axes)
+  int nhi[MAXN];            // M / (Ng * sg): group positions above each axis
+  FastDiv fR, fM;           // tile element -> (l, pos, r)
+  FastDiv fsg[MAXN], fnhi[MAXN];
+  int M, I, L, R, TS, ntile;
+  long long O;
+  int tiles_o, tiles_i;
+  size_t smem;
+};
+
+enum { GP_GRAD_INV = 0, GP_PLAIN = 1, GP_INV_COEF_FWD = 2, GP_FWD_DIV = 3, GP_SINGLE = 4 };
+
+struct FusedSchedule {
+  bool ok = false;
+  int npass = 0;
+  GroupPass pass[5];
+};
+
 struct FftPlan {
   int d = 0, n = 0, D = 0, ncomp = 0, kind = 0, max_rhs = 0, precisions = 3;
   int N[MAXN] = {};
@@ -386,6 +409,7 @@ struct FftPlan {
   float2* f32 = nullptr;
   double* part = nullptr;       // reduction partials
   int nblk = 0;
+  FusedSchedule fused64, fused32;   // group-pass schedules of the apply (ok = false: per-axis passes)
   void* take(size_t b) {
     void* p = nullptr;
     cudaError_t e = cudaMalloc(&p, b);
@@ -401,6 +425,8 @@ struct FftPlan {
     for (void* p : allocs) cudaFree(p);
   }
 };
+
+static FusedSchedule plan_fused(const PlanDev& pd, int esize);
 
 FftPlan* fft_plan_create(const PlanDev& pd, int precisions, int max_rhs) {
   for (int j = 0; j < pd.n; ++j)
@@ -424,6 +450,8 @@ FftPlan* fft_plan_create(const PlanDev& pd, int precisions, int max_rhs) {
     else f->f64 = (double2*)f->take(D * sizeof(double2));   // set-up transforms only
     if (precisions & 2) f->f32 = (float2*)f->take(D * pd.d * max_rhs * sizeof(float2));
     f->nblk = (int)std::min<int64_t>((pd.D + BLOCK - 1) / BLOCK, 152 * 8);
+    f->fused64 = plan_fused(pd, (int)sizeof(double2));
+    f->fused32 = plan_fused(pd, (int)sizeof(float2));
     f->part = (double*)f->take((size_t)f->nblk * 2 * MAXD * MAXD * sizeof(double) + 1024);
   } catch (...) {
     delete f;
@@ -455,6 +483,37 @@ __device__ __forceinline__ T coef_at(int kind, int d, const T* c, int D, int e, 
   if (kind == QP_COEF_SCALAR) return a == b ? c[e] : T(0);
   if (kind == QP_COEF_DIAG) return a == b ? c[(size_t)a * D + e] : T(0);
   return c[(size_t)sym_idx(a, b, d) * D + e];
+}
+
+// entry (a, b) of A from the components c[0 .. ncomp) of one node (scalar / diagonal / upper triangle)
+constexpr int MAXC = MAXD * (MAXD + 1) / 2;
+// The d x d matrix from the components of one node, with compile-time indices only (registers, no stack).
+template <typename T>
+__device__ __forceinline__ void fill_matrix(int kind, int d, const T (&c)[MAXC], T (&A)[MAXD][MAXD]) {
+#pragma unroll
+  for (int a = 0; a < MAXD; ++a)
+#pragma unroll
+    for (int b = 0; b < MAXD; ++b) A[a][b] = T(0);
+  if (kind == QP_COEF_SCALAR) {
+    A[0][0] = A[1][1] = A[2][2] = c[0];
+  } else if (kind == QP_COEF_DIAG) {
+    A[0][0] = c[0];
+    A[1][1] = c[1];
+    A[2][2] = c[2];
+  } else if (d == 1) {
+    A[0][0] = c[0];
+  } else if (d == 2) {
+    A[0][0] = c[0];
+    A[0][1] = A[1][0] = c[1];
+    A[1][1] = c[2];
+  } else {
+    A[0][0] = c[0];
+    A[0][1] = A[1][0] = c[1];
+    A[0][2] = A[2][0] = c[2];
+    A[1][1] = c[3];
+    A[1][2] = A[2][1] = c[4];
+    A[2][2] = c[5];
+  }
 }
 
 // set-up: real grid samples -> complex buffer (component c), and the scaled FP64 / FP32 copies A / D
@@ -674,6 +733,448 @@ __global__ void __launch_bounds__(BLOCK) k_div(const PlanDev* pdp, int nrhs, con
   }
 }
 
+// ---- fused apply: groups of axes transformed in shared-memory tiles
+//
+// The axes are split into 1 to 3 groups of consecutive axes (each axis <= 32, a group up to all n axes). A pass
+// transforms one group of arrays seen as [O][M][I] (M = product of the group's sizes, O of the axes before it,
+// I of the axes after): a block stages tiles of L outer x M x R inner elements in shared memory (one padding
+// element per 32, so that lines of 8- and 16-byte elements spread over the banks) and runs the register DFT
+// along every axis of the group. Tiles divide the arrays exactly. Gradient, coefficient product and
+// divergence are applied while the d component tiles of one right-hand side are resident:
+//   one group:     [grad, inverse, A(y)/D, forward, divergence]                         one pass
+//   two groups:    [grad, inverse G0] [inverse G1, A(y)/D, forward G1] [forward G0, div]   three passes
+//   three groups:  as two, with a plain inverse and forward pass over the middle group     five passes
+// The DFT is separable, so transforming the groups in this order is the same n-dim transform. Global loads
+// and stores of a tile are unrolled so that each thread has all of its elements in flight at once.
+
+constexpr int GP_EPT = 32;   // most tile elements per thread (TS <= GP_EPT * BLOCK)
+template <typename T> __host__ __device__ constexpr int GP_BATCH() { return sizeof(T) == 8 ? 8 : 16; }   // loads in flight
+
+__device__ __forceinline__ int tphys(int i) { return i + (i >> 5); }
+__device__ __forceinline__ int fdivi(int x, const FastDiv& f) { return (int)fdiv((uint32_t)x, f); }
+
+// One group axis: its stride in the group position, the positions above it, and their fast divisions.
+struct AxisLines {
+  int sg, nhi;
+  FastDiv fsg, fnhi;
+};
+
+// DFT of size N along one group axis of ntile tiles (tstride elements apart): lines (l, other group digits, r)
+// spread over the block, neighbouring threads on neighbouring r and lower group digits.
+template <typename T, int N>
+__device__ __noinline__ void tile_axis(cplx<T>* tiles, int ntile, int tstride, const GroupPass& gp, AxisLines ax,
+                                       int sign) {
+  const int R = gp.R, M = gp.M;
+  const int per = gp.L * ax.nhi * ax.sg * R;
+  const int step = ax.sg * R;
+  for (int job = threadIdx.x; job < per * ntile; job += BLOCK) {
+    const int tl = ntile == 1 ? 0 : job / per;
+    const int line = job - tl * per;
+    int q = fdivi(line, gp.fR);
+    const int r = line - q * R;
+    int q2 = fdivi(q, ax.fsg);
+    const int lo = q - q2 * ax.sg;
+    const int l = fdivi(q2, ax.fnhi);
+    const int hi = q2 - l * ax.nhi;
+    const int base = (l * M + hi * N * ax.sg + lo) * R + r;
+    cplx<T>* tp = tiles + (size_t)tl * tstride;
+    cplx<T> x[N];
+    if ((step & 31) == 0) {
+      // the padding is then linear along the line: one add per element
+      cplx<T>* lp = tp + tphys(base);
+      const int stepP = step + (step >> 5);
+#pragma unroll
+      for (int k = 0; k < N; ++k) x[k] = lp[k * stepP];
+      RegDft<T, N>::run(x, sign);
+#pragma unroll
+      for (int k = 0; k < N; ++k) lp[k * stepP] = x[k];
+    } else {
+#pragma unroll
+      for (int k = 0; k < N; ++k) x[k] = tp[tphys(base + k * step)];
+      RegDft<T, N>::run(x, sign);
+#pragma unroll
+      for (int k = 0; k < N; ++k) tp[tphys(base + k * step)] = x[k];
+    }
+  }
+}
+
+// Every axis of the group, on ntile tiles; ends with a block barrier. (One call site per DFT size keeps the
+// kernel's code small.)
+template <typename T>
+__device__ void tile_transform(cplx<T>* tiles, int ntile, int tstride, const GroupPass& gp, int sign) {
+  for (int t = 0; t < gp.ng; ++t) {
+    int Nt = 0;
+    AxisLines ax;
+    switch (t) {
+#define QP_AX(i) \
+  case i: Nt = gp.Ng[i]; ax = AxisLines{gp.sg[i], gp.nhi[i], gp.fsg[i], gp.fnhi[i]}; break;
+      QP_AX(0) QP_AX(1) QP_AX(2) QP_AX(3) QP_AX(4) default: QP_AX(5)
+#undef QP_AX
+    }
+    switch (Nt) {
+      case 2: tile_axis<T, 2>(tiles, ntile, tstride, gp, ax, sign); break;
+      case 3: tile_axis<T, 3>(tiles, ntile, tstride, gp, ax, sign); break;
+      case 4: tile_axis<T, 4>(tiles, ntile, tstride, gp, ax, sign); break;
+      case 6: tile_axis<T, 6>(tiles, ntile, tstride, gp, ax, sign); break;
+      case 8: tile_axis<T, 8>(tiles, ntile, tstride, gp, ax, sign); break;
+      case 9: tile_axis<T, 9>(tiles, ntile, tstride, gp, ax, sign); break;
+      case 12: tile_axis<T, 12>(tiles, ntile, tstride, gp, ax, sign); break;
+      case 16: tile_axis<T, 16>(tiles, ntile, tstride, gp, ax, sign); break;
+      case 18: tile_axis<T, 18>(tiles, ntile, tstride, gp, ax, sign); break;
+      case 24: tile_axis<T, 24>(tiles, ntile, tstride, gp, ax, sign); break;
+      case 27: tile_axis<T, 27>(tiles, ntile, tstride, gp, ax, sign); break;
+      default: tile_axis<T, 32>(tiles, ntile, tstride, gp, ax, sign); break;
+    }
+    __syncthreads();
+  }
+}
+
+// lambda_a at the linear mode index e from per-axis tables tab[j][digit][a] = P_aj * k(digit).
+template <typename T>
+__device__ __forceinline__ void lam_tab(const PlanDev& p, const T* tab, int e, T (&lk)[MAXD]) {
+#pragma unroll
+  for (int a = 0; a < MAXD; ++a) lk[a] = T(0);
+  uint32_t x = (uint32_t)e;
+#pragma unroll
+  for (int j = MAXN - 1; j >= 0; --j) {
+    if (j < p.n) {
+      const uint32_t q = fdiv(x, p.div[j]);
+      const int dg = (int)(x - q * (uint32_t)p.N[j]);
+      x = q;
+#pragma unroll
+      for (int a = 0; a < MAXD; ++a) lk[a] += tab[(j * 32 + dg) * MAXD + a];
+    }
+  }
+}
+
+// One pass of the fused apply. blockIdx.x: tile (outer-major); blockIdx.y: right-hand side (GP_PLAIN: field).
+// Fields g are [d][nrhs][D]; h and w are [nrhs][D]; coef is A^{c}(y) / D, [ncomp][D].
+template <typename T, int MODE>
+__global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 1 : 2) k_fft_group(const PlanDev* pdp, GroupPass gp, int nrhs,
+                                                     const cplx<T>* h, cplx<T>* g, cplx<T>* w, const T* coef) {
+  __shared__ __align__(16) PlanDev sp;
+  __shared__ T tab[MAXN * 32 * MAXD];
+  extern __shared__ __align__(16) unsigned char smraw[];
+  {
+    const int4* src = reinterpret_cast<const int4*>(pdp);
+    int4* dst = reinterpret_cast<int4*>(&sp);
+    for (int i = threadIdx.x; i < (int)(sizeof(PlanDev) / sizeof(int4)); i += BLOCK) dst[i] = src[i];
+  }
+  __syncthreads();
+  constexpr bool LAM = (MODE == GP_GRAD_INV || MODE == GP_FWD_DIV || MODE == GP_SINGLE);
+  if (LAM) {
+    for (int i = threadIdx.x; i < MAXN * 32 * MAXD; i += BLOCK) {
+      const int a = i % MAXD, dg = (i / MAXD) % 32, j = i / (MAXD * 32);
+      T v = T(0);
+      if (j < sp.n && a < sp.d && dg < sp.N[j]) {
+        const int k = (2 * dg < sp.N[j]) ? dg : dg - sp.N[j];
+        v = (T)(pcoef<T>(sp, a, j) * (T)k);
+      }
+      tab[i] = v;
+    }
+    __syncthreads();
+  }
+  cplx<T>* tiles = reinterpret_cast<cplx<T>*>(smraw);
+  const int D = sp.D, d = sp.d, kind = sp.kind;
+  const int TS = gp.TS;
+  const int TSP = tphys(TS - 1) + 1;
+  const int to = blockIdx.x / gp.tiles_i, ti = blockIdx.x - to * gp.tiles_i;
+  const int base_o = to * gp.L, i0 = ti * gp.R;
+  const int y = blockIdx.y;
+  // linear index in the array of tile element idx
+  auto lin = [&](int idx) -> int {
+    const int q = fdivi(idx, gp.fR);
+    const int r = idx - q * gp.R;
+    const int l = fdivi(q, gp.fM);
+    const int pos = q - l * gp.M;
+    return ((base_o + l) * gp.M + pos) * gp.I + i0 + r;
+  };
+  const int ntile = (MODE == GP_PLAIN) ? 1 : d;
+
+  // ---- load the tiles: lambda_b h (gradient) or the stored fields, GP_BATCH loads in flight per thread
+  constexpr int NB = GP_BATCH<T>();
+  if (MODE == GP_GRAD_INV || MODE == GP_SINGLE) {
+    for (int u0 = 0; u0 * BLOCK < TS; u0 += NB) {
+      cplx<T> hv[NB];
+      int ev[NB];
+#pragma unroll
+      for (int u = 0; u < NB; ++u) {
+        const int idx = threadIdx.x + (u0 + u) * BLOCK;
+        ev[u] = idx < TS ? lin(idx) : 0;
+        if (idx < TS) hv[u] = h[(size_t)y * D + ev[u]];
+      }
+#pragma unroll
+      for (int u = 0; u < NB; ++u) {
+        const int idx = threadIdx.x + (u0 + u) * BLOCK;
+        if (idx < TS) {
+          T lk[MAXD];
+          lam_tab<T>(sp, tab, ev[u], lk);
+#pragma unroll
+          for (int b = 0; b < MAXD; ++b)
+            if (b < d) tiles[(size_t)b * TSP + tphys(idx)] = mk<T>(lk[b] * hv[u].x, lk[b] * hv[u].y);
+        }
+      }
+    }
+  } else {
+    // all tiles of an element from one index computation; NB / 2 elements of every tile in flight
+    constexpr int NE = NB / 2;
+    const cplx<T>* src0 = g + (size_t)y * D;   // field y (GP_PLAIN) or component 0 of right-hand side y
+    const size_t fstride = (size_t)nrhs * D;   // between the component fields of one right-hand side
+    for (int u0 = 0; u0 * BLOCK < TS; u0 += NE) {
+      cplx<T> v[NE][MAXD];
+#pragma unroll
+      for (int u = 0; u < NE; ++u) {
+        const int idx = threadIdx.x + (u0 + u) * BLOCK;
+        if (idx < TS) {
+          const int e = lin(idx);
+#pragma unroll
+          for (int b = 0; b < MAXD; ++b)
+            if (b < ntile) v[u][b] = src0[(size_t)b * fstride + e];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < NE; ++u) {
+        const int idx = threadIdx.x + (u0 + u) * BLOCK;
+        if (idx < TS) {
+#pragma unroll
+          for (int b = 0; b < MAXD; ++b)
+            if (b < ntile) tiles[(size_t)b * TSP + tphys(idx)] = v[u][b];
+        }
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---- transforms and the coefficient product
+  if (MODE == GP_INV_COEF_FWD || MODE == GP_SINGLE) {
+    tile_transform<T>(tiles, d, TSP, gp, +1);
+    // q_a = sum_b A^{ab}(y) / D g_b at every grid node of the tile (coefficient loads batched)
+    const int nc = sp.ncomp;
+    constexpr int CB = 4;
+    for (int u0 = 0; u0 * BLOCK < TS; u0 += CB) {
+      T cv[CB][MAXC];
+#pragma unroll
+      for (int u = 0; u < CB; ++u) {
+        const int idx = threadIdx.x + (u0 + u) * BLOCK;
+        const int e = idx < TS ? lin(idx) : 0;
+#pragma unroll
+        for (int c = 0; c < MAXC; ++c) cv[u][c] = (idx < TS && c < nc) ? coef[(size_t)c * D + e] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < CB; ++u) {
+        const int idx = threadIdx.x + (u0 + u) * BLOCK;
+        if (idx >= TS) break;
+        T A[MAXD][MAXD];
+        fill_matrix<T>(kind, d, cv[u], A);
+        cplx<T> gv[MAXD];
+#pragma unroll
+        for (int b = 0; b < MAXD; ++b) gv[b] = b < d ? tiles[(size_t)b * TSP + tphys(idx)] : mk<T>(0, 0);
+#pragma unroll
+        for (int a = 0; a < MAXD; ++a) {
+          if (a < d) {
+            cplx<T> q = mk<T>(0, 0);
+#pragma unroll
+            for (int b = 0; b < MAXD; ++b) {
+              q.x = fma(A[a][b], gv[b].x, q.x);
+              q.y = fma(A[a][b], gv[b].y, q.y);
+            }
+            tiles[(size_t)a * TSP + tphys(idx)] = q;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    tile_transform<T>(tiles, d, TSP, gp, -1);
+  } else {
+    tile_transform<T>(tiles, ntile, TSP, gp, MODE == GP_GRAD_INV ? +1 : (MODE == GP_FWD_DIV ? -1 : gp.sign));
+  }
+
+  // ---- store: divergence sum_a lambda_a q_a, or the fields
+  if (MODE == GP_FWD_DIV || MODE == GP_SINGLE) {
+#pragma unroll 4
+    for (int u = 0; u < GP_EPT; ++u) {
+      const int idx = threadIdx.x + u * BLOCK;
+      if (idx >= TS) break;
+      const int e = lin(idx);
+      T lk[MAXD];
+      lam_tab<T>(sp, tab, e, lk);
+      cplx<T> acc = mk<T>(0, 0);
+#pragma unroll
+      for (int a = 0; a < MAXD; ++a) {
+        if (a < d) {
+          const cplx<T> q = tiles[(size_t)a * TSP + tphys(idx)];
+          acc.x = fma(lk[a], q.x, acc.x);
+          acc.y = fma(lk[a], q.y, acc.y);
+        }
+      }
+      w[(size_t)y * D + e] = acc;
+    }
+  } else {
+    cplx<T>* dst0 = g + (size_t)y * D;
+    const size_t fstride = (size_t)nrhs * D;
+#pragma unroll 4
+    for (int u = 0; u < GP_EPT; ++u) {
+      const int idx = threadIdx.x + u * BLOCK;
+      if (idx >= TS) break;
+      const int e = lin(idx);
+#pragma unroll
+      for (int b = 0; b < MAXD; ++b)
+        if (b < ntile) dst0[(size_t)b * fstride + e] = tiles[(size_t)b * TSP + tphys(idx)];
+    }
+  }
+}
+
+// Largest divisor of x that is <= cap (>= 1).
+static long long largest_divisor_le(long long x, long long cap) {
+  for (long long v = std::min(x, std::max(1ll, cap)); v > 1; --v)
+    if (x % v == 0) return v;
+  return 1;
+}
+
+// Elements per tile that a pass may stage: ntile tiles (with padding) in about 100 KB, so that two blocks fit
+// on an SM, and at most GP_EPT elements per thread.
+static int tile_budget(int esize, int ntile) {
+  const int by_smem = (100 * 1024) / (esize * ntile) * 32 / 33 - 1;
+  return std::min(by_smem, GP_EPT * BLOCK);
+}
+
+static bool make_pass(const PlanDev& pd, int j0, int ng, int mode, int sign, int esize, GroupPass& gp) {
+  gp = GroupPass();
+  if (ng < 1 || ng > MAXN || j0 + ng > pd.n) return false;
+  gp.mode = mode;
+  gp.sign = sign;
+  gp.ng = ng;
+  gp.j0 = j0;
+  gp.ntile = (mode == GP_PLAIN) ? 1 : std::max(1, pd.d);
+  long long M = 1, O = 1, I = 1;
+  for (int t = 0; t < ng; ++t) {
+    gp.Ng[t] = pd.N[j0 + t];
+    if (gp.Ng[t] > 32) return false;
+    M *= gp.Ng[t];
+  }
+  for (int t = ng - 1, st = 1; t >= 0; --t) {
+    gp.sg[t] = st;
+    st *= gp.Ng[t];
+  }
+  for (int t = 0; t < ng; ++t) gp.nhi[t] = (int)(M / (gp.Ng[t] * gp.sg[t]));
+  for (int j = 0; j < j0; ++j) O *= pd.N[j];
+  for (int j = j0 + ng; j < pd.n; ++j) I *= pd.N[j];
+  const int budget = tile_budget(esize, gp.ntile);
+  if (M > budget) return false;
+  gp.M = (int)M;
+  gp.O = O;
+  gp.I = (int)I;
+  if (I > 1) {
+    gp.R = (int)largest_divisor_le(I, budget / M);
+    gp.L = gp.R == I ? (int)largest_divisor_le(O, budget / (M * I)) : 1;
+  } else {
+    gp.R = 1;
+    gp.L = (int)largest_divisor_le(O, budget / M);
+  }
+  gp.TS = gp.L * gp.M * gp.R;
+  gp.fR = make_fastdiv((uint32_t)gp.R);
+  gp.fM = make_fastdiv((uint32_t)gp.M);
+  for (int t = 0; t < ng; ++t) {
+    gp.fsg[t] = make_fastdiv((uint32_t)gp.sg[t]);
+    gp.fnhi[t] = make_fastdiv((uint32_t)gp.nhi[t]);
+  }
+  gp.tiles_i = (int)(I / gp.R);
+  gp.tiles_o = (int)(O / gp.L);
+  gp.smem = (size_t)((gp.TS - 1) + ((gp.TS - 1) >> 5) + 1) * esize * gp.ntile;
+  return (long long)gp.tiles_o * gp.tiles_i < (1ll << 31);
+}
+
+// Groups of consecutive axes and the passes over them (see above); ok = false leaves the per-axis path.
+static FusedSchedule plan_fused(const PlanDev& pd, int esize) {
+  FusedSchedule fs;
+  const int n = pd.n;
+  for (int j = 0; j < n; ++j)
+    if (pd.N[j] > 32) return fs;
+  GroupPass a, b, c, m1, m2;
+  if (make_pass(pd, 0, n, GP_SINGLE, 0, esize, a)) {
+    fs.pass[0] = a;
+    fs.npass = 1;
+    fs.ok = true;
+    return fs;
+  }
+  // two groups [0, s) and [s, n): the most balanced feasible split
+  int best = -1;
+  long long best_max = 0;
+  for (int s = 1; s < n; ++s) {
+    if (!make_pass(pd, 0, s, GP_GRAD_INV, 0, esize, a) || !make_pass(pd, s, n - s, GP_INV_COEF_FWD, 0, esize, b))
+      continue;
+    const long long mx = std::max(a.M, b.M);
+    if (best < 0 || mx < best_max) {
+      best = s;
+      best_max = mx;
+    }
+  }
+  if (best > 0) {
+    make_pass(pd, 0, best, GP_GRAD_INV, 0, esize, a);
+    make_pass(pd, best, n - best, GP_INV_COEF_FWD, 0, esize, b);
+    make_pass(pd, 0, best, GP_FWD_DIV, 0, esize, c);
+    fs.pass[0] = a;
+    fs.pass[1] = b;
+    fs.pass[2] = c;
+    fs.npass = 3;
+    fs.ok = true;
+    return fs;
+  }
+  // three groups [0, s1), [s1, s2), [s2, n)
+  int b1 = -1, b2 = -1;
+  for (int s1 = 1; s1 < n - 1; ++s1)
+    for (int s2 = s1 + 1; s2 < n; ++s2) {
+      if (!make_pass(pd, 0, s1, GP_GRAD_INV, 0, esize, a) || !make_pass(pd, s1, s2 - s1, GP_PLAIN, 1, esize, m1) ||
+          !make_pass(pd, s2, n - s2, GP_INV_COEF_FWD, 0, esize, b))
+        continue;
+      const long long mx = std::max<long long>(std::max(a.M, m1.M), b.M);
+      if (b1 < 0 || mx < best_max) {
+        b1 = s1;
+        b2 = s2;
+        best_max = mx;
+      }
+    }
+  if (b1 < 0) return fs;
+  make_pass(pd, 0, b1, GP_GRAD_INV, 0, esize, a);
+  make_pass(pd, b1, b2 - b1, GP_PLAIN, +1, esize, m1);
+  make_pass(pd, b2, n - b2, GP_INV_COEF_FWD, 0, esize, b);
+  make_pass(pd, b1, b2 - b1, GP_PLAIN, -1, esize, m2);
+  make_pass(pd, 0, b1, GP_FWD_DIV, 0, esize, c);
+  fs.pass[0] = a;
+  fs.pass[1] = m1;
+  fs.pass[2] = b;
+  fs.pass[3] = m2;
+  fs.pass[4] = c;
+  fs.npass = 5;
+  fs.ok = true;
+  return fs;
+}
+
+template <typename T, int MODE>
+static void launch_group(const GroupPass& gp, const PlanDev* pdp, int nrhs, int ny, const cplx<T>* h, cplx<T>* g,
+                         cplx<T>* w, const T* coef, cudaStream_t s) {
+  auto fn = k_fft_group<T, MODE>;
+  if (gp.smem > 48 * 1024) CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gp.smem));
+  dim3 grid((unsigned)((long long)gp.tiles_o * gp.tiles_i), (unsigned)ny);
+  fn<<<grid, BLOCK, gp.smem, s>>>(pdp, gp, nrhs, h, g, w, coef);
+  count_launch();
+}
+
+template <typename T>
+static void run_fused(const FusedSchedule& fs, const PlanDev& pd, const PlanDev* pdp, const cplx<T>* h, cplx<T>* g,
+                      cplx<T>* w, const T* coef, int nrhs, cudaStream_t s) {
+  for (int i = 0; i < fs.npass; ++i) {
+    const GroupPass& gp = fs.pass[i];
+    switch (gp.mode) {
+      case GP_SINGLE: launch_group<T, GP_SINGLE>(gp, pdp, nrhs, nrhs, h, g, w, coef, s); break;
+      case GP_GRAD_INV: launch_group<T, GP_GRAD_INV>(gp, pdp, nrhs, nrhs, h, g, w, coef, s); break;
+      case GP_INV_COEF_FWD: launch_group<T, GP_INV_COEF_FWD>(gp, pdp, nrhs, nrhs, h, g, w, coef, s); break;
+      case GP_FWD_DIV: launch_group<T, GP_FWD_DIV>(gp, pdp, nrhs, nrhs, h, g, w, coef, s); break;
+      default: launch_group<T, GP_PLAIN>(gp, pdp, nrhs, pd.d * nrhs, h, g, w, coef, s); break;
+    }
+  }
+}
+
 template <typename T> static cplx<T>* fields_of(FftPlan* f);
 template <> double2* fields_of<double>(FftPlan* f) { return f->f64; }
 template <> float2* fields_of<float>(FftPlan* f) { return f->f32; }
@@ -687,6 +1188,12 @@ void fft_apply(FftPlan* f, const PlanDev& pd, const PlanDev* pdp, const cplx<T>*
   cplx<T>* g = fields_of<T>(f);
   if (!g || nrhs > f->max_rhs)
     raise(QP_ERR_INVALID_ARG, "FFT plan has no workspace for this precision / number of right-hand sides");
+  const FusedSchedule& fs = (sizeof(T) == 8) ? f->fused64 : f->fused32;
+  if (fs.ok) {
+    run_fused<T>(fs, pd, pdp, h, g, w, coef_of<T>(f), nrhs, s);
+    CK_LAUNCH();
+    return;
+  }
   k_grad<T><<<f->nblk, BLOCK, 0, s>>>(pdp, nrhs, h, g);
   count_launch();
   fft_nd<T>(g, pd.n, pd.N, (long long)pd.d * nrhs, +1, s);

@@ -59,6 +59,14 @@ struct FastDiv {
   uint32_t p;
 };
 
+inline FastDiv make_fastdiv(uint32_t d) {
+  uint32_t L = 0;
+  while ((1ull << L) < d) ++L;
+  const uint32_t p = 31 + L;
+  const uint64_t m = ((1ull << p) + d - 1) / d;
+  return FastDiv{d, (uint32_t)m, p};
+}
+
 // Device description of one plan's geometry and (for the taps backend) its taps, sorted as
 // [mean tap][star taps of axis 0] .. [star taps of axis n-1][taps with several nonzero axes].
 struct alignas(16) PlanDev {

@@ -62,13 +62,6 @@ struct Carve {
   }
 };
 
-FastDiv fastdiv(uint32_t d) {
-  uint32_t L = 0;
-  while ((1ull << L) < d) ++L;
-  const uint32_t p = 31 + L;
-  const uint64_t m = ((1ull << p) + d - 1) / d;
-  return FastDiv{d, (uint32_t)m, p};
-}
 
 // Host description built without heap memory: geometry plus the merged, Hermitian-checked taps, sorted as
 // [mean][star taps per axis][multi-axis taps] (the device layout of PlanDev).
@@ -104,13 +97,13 @@ void build_host(int d, int n, const double* P, const int* N, const qp_coeff* c, 
   for (int j = n - 1; j >= 0; --j) {
     pd.N[j] = N[j];
     pd.stride[j] = st;
-    pd.div[j] = fastdiv((uint32_t)N[j]);
+    pd.div[j] = make_fastdiv((uint32_t)N[j]);
     st *= N[j];
   }
   for (int j = n; j < MAXN; ++j) {
     pd.N[j] = 1;
     pd.stride[j] = (int)D;
-    pd.div[j] = fastdiv(1);
+    pd.div[j] = make_fastdiv(1);
   }
   for (int a = 0; a < d; ++a)
     for (int j = 0; j < n; ++j) {
