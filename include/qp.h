@@ -82,11 +82,11 @@ typedef struct {
   int exec;         /* how a solve is driven (the iterates are bitwise the same in every mode):
                        QP_EXEC_GRAPH: one CUDA-graph launch whose loops are conditional WHILE nodes (three kernels
                        per PCG iteration); QP_EXEC_PERSISTENT: one cooperative launch of a persistent kernel that
-                       meets at grid barriers (taps backend, single-plan solves; others use the graph);
-                       QP_EXEC_DIRECT: the graph's kernels launched one by one, the host polling convergence (for
-                       profilers and callers that cannot launch graphs); QP_EXEC_AUTO (0, default): PERSISTENT
-                       where it applies and every chunk of modes gets its own resident block, else GRAPH. A persistent solve whose barrier wait exceeds its limit
-                       returns QP_ERR_TIMEOUT. */
+                       meets at grid barriers (taps backend, single-plan solves, even last-axis length; others use
+                       the graph); QP_EXEC_DIRECT: the graph's kernels launched one by one, the host polling
+                       convergence (for profilers and callers that cannot launch graphs); QP_EXEC_AUTO (0,
+                       default): PERSISTENT where it applies and every chunk of modes gets its own resident block,
+                       else GRAPH. A persistent solve whose barrier wait exceeds its limit returns QP_ERR_TIMEOUT. */
 } qp_options;
 
 typedef struct {

@@ -428,6 +428,10 @@ void alloc_workspace(qp_plan* p) {
 
 // ------------------------------------------------------------------------------------------------ recording
 
+// Modes per thread step of the stencil kernels for this plan: runs of 2 along the last axis when its length is
+// even (the run then never crosses a row), else 1.
+int last_axis_run(const qp_plan* p) { return (p->host_pd.N[p->host_pd.n - 1] % 2 == 0) ? 2 : 1; }
+
 // Everything a solve needs about its units on the host side.
 struct Units {
   std::vector<qp_plan*> plans;
@@ -437,6 +441,7 @@ struct Units {
   int max_rhs = 1;
   bool direct = false;    // launch kernels directly (host-driven loops) instead of recording a graph
   int exec = QP_EXEC_GRAPH;  // QP_EXEC_AUTO / PERSISTENT: a single taps unit may run as one persistent launch
+  int run = 2;               // stencil modes per thread step: 2 when every unit's last axis has even length
 };
 
 // One stiffness apply over all units at a level: the FFT passes of FFT-backend units (they write w), then the
@@ -451,7 +456,7 @@ void record_apply(const Units& us, const Entry& en, int level, int epi, bool ref
     else if (epi == EPI_DOT_HW) fft_apply<double>(p->fft, p->host_pd, p->pd, p->v64.h, p->v64.w, nr, s);
     else fft_apply<double>(p->fft, p->host_pd, p->pd, p->v64.X, p->v64.w, nr, s);
   }
-  launch_apply(en.bd, us.all_real, us.max_coef, us.max_rhs, level, epi, refine, cond, en.nblk, s);
+  launch_apply(en.bd, us.all_real, us.max_coef, us.max_rhs, level, epi, refine, cond, en.nblk, us.run, s);
   CK_LAUNCH();
 }
 
@@ -703,7 +708,7 @@ Entry& get_entry(Solver* sv, const Units& us, const Key& key) {
   bd.maxit = key.maxit;
   bd.max_outer = key.max_outer;
   en->nblk = nchunks;
-  if ((us.exec == QP_EXEC_AUTO || us.exec == QP_EXEC_PERSISTENT) && nu == 1 && !us.direct) {
+  if ((us.exec == QP_EXEC_AUTO || us.exec == QP_EXEC_PERSISTENT) && nu == 1 && !us.direct && us.run == 2) {
     // every block of a cooperative launch is resident: at most the occupancy limit, at most one per chunk.
     // AUTO takes the persistent form only when every chunk has its own resident block (small and medium
     // problems, where launch and synchronisation latency dominate); larger solves keep the graph, whose
@@ -831,6 +836,7 @@ Units single_units(qp_plan* p, int nrhs) {
   us.max_rhs = nrhs;
   us.direct = p->exec == QP_EXEC_DIRECT;
   us.exec = p->backend == QP_BACKEND_TAPS ? p->exec : QP_EXEC_GRAPH;
+  us.run = last_axis_run(p);
   return us;
 }
 
@@ -1011,9 +1017,11 @@ qp_status qp_apply_stiffness(qp_plan* p, int nrhs, const void* U, void* QU, int 
   cudaStream_t s = S(stream);
   if (p->backend == QP_BACKEND_TAPS) {
     if (precision == QP_FP64)
-      launch_apply_plain<double>(p->pd, p->real_coef, p->coef_count, p->D, nrhs, (const double2*)U, (double2*)QU, s);
+      launch_apply_plain<double>(p->pd, p->real_coef, p->coef_count, p->D, nrhs, (const double2*)U, (double2*)QU,
+                                 last_axis_run(p), s);
     else
-      launch_apply_plain<float>(p->pd, p->real_coef, p->coef_count, p->D, nrhs, (const float2*)U, (float2*)QU, s);
+      launch_apply_plain<float>(p->pd, p->real_coef, p->coef_count, p->D, nrhs, (const float2*)U, (float2*)QU,
+                                last_axis_run(p), s);
   } else {
     if (precision == QP_FP64) fft_apply<double>(p->fft, p->host_pd, p->pd, (const double2*)U, (double2*)QU, nrhs, s);
     else fft_apply<float>(p->fft, p->host_pd, p->pd, (const float2*)U, (float2*)QU, nrhs, s);
@@ -1128,6 +1136,7 @@ qp_status qp_batch_homogenized(qp_batch* b, const qp_solve_opts* opts, double* A
     us.nrhs.push_back(p->d);
     us.max_rhs = std::max(us.max_rhs, p->d);
     us.direct = us.direct || p->exec == QP_EXEC_DIRECT;
+    us.run = std::min(us.run, last_axis_run(p));
     if (p->backend == QP_BACKEND_TAPS) {
       us.all_real = us.all_real && p->real_coef;
       us.max_coef = std::max(us.max_coef, p->coef_count);

@@ -139,11 +139,11 @@ enum { LEVEL_FP64 = 0, LEVEL_FP32 = 1 };   // which vector set a PCG kernel work
 // realc: every taps plan in the batch has real tap values; mc: largest ntaps * ncomp over its taps plans.
 // maxr: the largest nrhs of the batch's units.
 void launch_apply(const BatchDev& b, bool realc, int mc, int maxr, int level, int epi, bool refine,
-                  unsigned long long cond, int nblk, cudaStream_t s);
+                  unsigned long long cond, int nblk, int run, cudaStream_t s);
 // Standalone apply of one plan: w = Q h for nrhs vectors (no reductions).
 template <typename T>
 void launch_apply_plain(const PlanDev* plan_dev, bool realc, int mc, int D, int nrhs, const cplx<T>* h, cplx<T>* w,
-                        cudaStream_t s);
+                        int run, cudaStream_t s);
 void launch_diag(const PlanDev* plan_dev, int mc, int D, double* jac, double* frob, float* jac32, float* frob32,
                  double* partials, unsigned* counter, double* out, int nblk, cudaStream_t s);
 void launch_rhs_taps(const PlanDev* plan_dev, int mc, int j0, int nrhs, int D, double2* F, cudaStream_t s);

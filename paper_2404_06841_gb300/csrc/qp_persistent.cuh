@@ -4,7 +4,7 @@
 // microseconds of memory traffic, this removes the per-kernel launch, fence and atomic latency of the graph
 // form (three kernels per iteration).
 //
-// The arithmetic is the graph form's: the same stencil (apply_point), the same per-element updates, the same
+// The arithmetic is the graph form's: the same stencil (apply_run), the same per-element updates, the same
 // per-chunk partial sums (block tree; FP32 warp level for FP32 vectors), and the same fixed-order sum over the
 // chunks, which every block now computes for itself after a barrier instead of one finalizing block. Iterates,
 // iteration counts and a* are therefore bitwise those of the graph form. Consecutive reductions write
@@ -20,6 +20,7 @@ namespace qp {
 namespace {
 
 constexpr int S_INIT = 0, S_HW = 12, S_UPD = 16, S_RES = 24;   // partial slots of the four reductions
+constexpr int PRUN = 2;   // stencil runs of two modes (the plan's last axis has even length)
 static_assert(S_HW >= 3 * MAXR && S_UPD >= S_HW + MAXR && S_RES >= S_UPD + 2 * MAXR &&
                   NSLOT_PERSIST >= S_RES + 2 * MAXR,
               "persistent partial slots overlap");
@@ -150,25 +151,29 @@ __device__ __forceinline__ void ph_apply(const BatchDev& b, const UnitDev& un, i
   for (int q = 0; q < NV; ++q) vt[q] = T(0);
   int base, end;
   chunk_range(un, c, base, end);
-  for (int e = base + threadIdx.x; e < end; e += BLOCK) {
-    cplx<T> acc[NR];
-    apply_point<T, REALC, NR, false>(sp, scoef, e, src, D, nrhs, acc);
+  for (int e0 = base + PRUN * threadIdx.x; e0 < end; e0 += PRUN * BLOCK) {
+    cplx<T> acc[PRUN][NR];
+    apply_run<T, REALC, NR, PRUN, false>(sp, scoef, e0, src, D, nrhs, acc);
 #pragma unroll
-    for (int r = 0; r < NR; ++r) {
-      if (r < nrhs) {
-        const size_t o = (size_t)r * D + e;
-        if (EPI == EPI_DOT_HW) {
-          dst[o] = acc[r];
-          const cplx<T> hv = src[o];
-          vt[r] = fma(hv.x, acc[r].x, fma(hv.y, acc[r].y, vt[r]));
-        } else if (EPI == EPI_RESIDUAL) {
-          const cplx<T> f = F[o];
-          const cplx<T> res = (e == 0) ? mk<T>(0, 0) : mk<T>(f.x - acc[r].x, f.y - acc[r].y);
-          dst[o] = res;
-          vt[2 * r] = fma(res.x, res.x, fma(res.y, res.y, vt[2 * r]));
-          if (e != 0) vt[2 * r + 1] = fma(f.x, f.x, fma(f.y, f.y, vt[2 * r + 1]));
-        } else {
-          dst[o] = acc[r];
+    for (int s = 0; s < PRUN; ++s) {
+      const int e = e0 + s;
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        if (r < nrhs) {
+          const size_t o = (size_t)r * D + e;
+          if (EPI == EPI_DOT_HW) {
+            dst[o] = acc[s][r];
+            const cplx<T> hv = src[o];
+            vt[r] = fma(hv.x, acc[s][r].x, fma(hv.y, acc[s][r].y, vt[r]));
+          } else if (EPI == EPI_RESIDUAL) {
+            const cplx<T> f = F[o];
+            const cplx<T> res = (e == 0) ? mk<T>(0, 0) : mk<T>(f.x - acc[s][r].x, f.y - acc[s][r].y);
+            dst[o] = res;
+            vt[2 * r] = fma(res.x, res.x, fma(res.y, res.y, vt[2 * r]));
+            if (e != 0) vt[2 * r + 1] = fma(f.x, f.x, fma(f.y, f.y, vt[2 * r + 1]));
+          } else {
+            dst[o] = acc[s][r];
+          }
         }
       }
     }

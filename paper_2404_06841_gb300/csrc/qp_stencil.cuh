@@ -1,9 +1,9 @@
-// The per-mode stencil of the taps backend, shared by the batch apply kernels (qp_taps.cu) and the persistent
-// solve (qp_persistent.cu): the compressed mat-vec of Sec. 4.2,
+// The stencil of the taps backend, shared by the batch apply kernels (qp_taps.cu) and the persistent solve
+// (qp_persistent.cu): the compressed mat-vec of Sec. 4.2,
 //   (Q h)(k) = sum_t lambda(k)^T C_t lambda(k -N m_t) h(k -N m_t),   lambda(k) = P k,
-// (eq. n-discrete_equation; App. D for a matrix coefficient). Star taps (one nonzero axis) are grouped per
-// axis so that each costs one wrap test, one index update and, for a scalar coefficient, one fused
-// multiply-add for the weight: lambda(k).lambda(k') = |lambda(k)|^2 + dk (lambda(k).P_j).
+// (eq. n-discrete_equation; App. D for a matrix coefficient), evaluated on runs of consecutive modes along the
+// last axis. Star taps (one nonzero axis) are grouped per axis; for a scalar coefficient a star tap's weight
+// costs one fused multiply-add per mode: lambda(k).lambda(k') = |lambda(k)|^2 + dk (lambda(k).P_j).
 #pragma once
 #include "qp_device.cuh"
 
@@ -45,107 +45,194 @@ __device__ __forceinline__ void mac(cplx<T>& acc, const cplx<T>& c, const cplx<T
   }
 }
 
-// acc[r] = (Q h_r)(e) for r < nrhs: the whole tap sum at one mode.
-template <typename T, bool REALC, int NR, bool RO = true>
-__device__ __forceinline__ void apply_point(const PlanDev& p, const cplx<T>* __restrict__ sc, int e,
-                                            const cplx<T>* h, int D, int nrhs, cplx<T> (&acc)[NR]) {
+// acc[s][r] = (Q h_r)(e0 + s), s < RUN: the whole tap sum at RUN consecutive modes of one row of the last
+// axis (e0 a multiple of RUN, RUN dividing N_{n-1}). Everything that depends only on the row is done once per
+// run: the digits of e0, lambda over the other axes, and for every tap along another axis its wrapped offset and
+// its mode step dk; that tap then reads RUN consecutive entries of h. The weights are formed per mode:
+//   scalar:  c_t (|lambda|^2 + dk lambda.P_j),   otherwise  lambda^T C_t (lambda + dk P_j)   (star tap on axis j).
+template <typename T, bool REALC, int NR, int RUN, bool RO = true>
+__device__ __forceinline__ void apply_run(const PlanDev& p, const cplx<T>* __restrict__ sc, int e0,
+                                          const cplx<T>* h, int D, int nrhs, cplx<T> (&acc)[RUN][NR]) {
   int ib[MAXN], k[MAXN];
-  mode_digits(p, e, ib, k);
-  const int d = p.d, kind = p.kind, nc = p.ncomp;
-  T lk[MAXD];
-#pragma unroll
-  for (int a = 0; a < MAXD; ++a) {
-    lk[a] = T(0);
-#pragma unroll
-    for (int j = 0; j < MAXN; ++j)
-      if (a < d && j < p.n) lk[a] = fma(pcoef<T>(p, a, j), (T)k[j], lk[a]);
-  }
+  mode_digits(p, e0, ib, k);
+  const int d = p.d, kind = p.kind, nc = p.ncomp, n = p.n;
+  const int jl = n - 1, Nl = p.N[jl];
+  const int ibl = e0 - (int)fdiv((uint32_t)e0, p.div[jl]) * Nl;   // digit of the last axis (kept in registers)
   const bool scalar = (kind == QP_COEF_SCALAR);
-  T lam2 = T(0), lp[MAXN];
+  // lambda per mode of the run
+  T lk[RUN][MAXD];
+  int kl[RUN];
+  {
+    T lr[MAXD];
 #pragma unroll
-  for (int a = 0; a < MAXD; ++a)
-    if (a < d) lam2 = fma(lk[a], lk[a], lam2);
+    for (int a = 0; a < MAXD; ++a) {
+      lr[a] = T(0);
 #pragma unroll
-  for (int j = 0; j < MAXN; ++j) {
-    lp[j] = T(0);
-    if (scalar && j < p.n) {
+      for (int j = 0; j < MAXN - 1; ++j)
+        if (a < d && j < jl) lr[a] = fma(pcoef<T>(p, a, j), (T)k[j], lr[a]);
+    }
 #pragma unroll
-      for (int a = 0; a < MAXD; ++a)
-        if (a < d) lp[j] = fma(lk[a], pcoef<T>(p, a, j), lp[j]);
+    for (int s = 0; s < RUN; ++s) {
+      const int ibs = ibl + s;
+      kl[s] = (2 * ibs < Nl) ? ibs : ibs - Nl;
+#pragma unroll
+      for (int a = 0; a < MAXD; ++a) lk[s][a] = (a < d) ? fma(pcoef<T>(p, a, jl), (T)kl[s], lr[a]) : T(0);
     }
   }
+  // scalar coefficient: |lambda|^2 per mode (lambda.P_j is formed per axis below)
+  T lam2[RUN];
 #pragma unroll
-  for (int r = 0; r < NR; ++r) acc[r] = mk<T>(0, 0);
+  for (int s = 0; s < RUN; ++s) {
+    lam2[s] = T(0);
+#pragma unroll
+    for (int a = 0; a < MAXD; ++a)
+      if (a < d) lam2[s] = fma(lk[s][a], lk[s][a], lam2[s]);
+  }
+#pragma unroll
+  for (int s = 0; s < RUN; ++s)
+#pragma unroll
+    for (int r = 0; r < NR; ++r) acc[s][r] = mk<T>(0, 0);
 
   // mean tap (sorted index 0): k' = k
   {
-    cplx<T> c;
-    if (scalar) {
-      c.x = sc[0].x * lam2;
-      c.y = REALC ? T(0) : sc[0].y * lam2;
-    } else {
-      c = weight_general<T>(kind, d, sc, lk, lk);
+#pragma unroll
+    for (int s = 0; s < RUN; ++s) {
+      cplx<T> c;
+      if (scalar) {
+        c.x = sc[0].x * lam2[s];
+        c.y = REALC ? T(0) : sc[0].y * lam2[s];
+      } else {
+        c = weight_general<T>(kind, d, sc, lk[s], lk[s]);
+      }
+#pragma unroll
+      for (int r = 0; r < NR; ++r)
+        if (r < nrhs) mac<T, REALC>(acc[s][r], c, ldh<RO>(h + (size_t)r * D + e0 + s));
     }
-#pragma unroll
-    for (int r = 0; r < NR; ++r)
-      if (r < nrhs) mac<T, REALC>(acc[r], c, ldh<RO>(h + (size_t)r * D + e));
   }
-  // star taps, grouped by axis
+  // star taps of the axes before the last: one offset per run, RUN consecutive reads per tap
 #pragma unroll
-  for (int j = 0; j < MAXN; ++j) {
-    if (j < p.n) {
+  for (int j = 0; j < MAXN - 1; ++j) {
+    if (j < jl) {
       const int Nj = p.N[j], sj = p.stride[j];
+      T pj[MAXD], lp[RUN];
+#pragma unroll
+      for (int a = 0; a < MAXD; ++a) pj[a] = pcoef<T>(p, a, j);
+#pragma unroll
+      for (int s = 0; s < RUN; ++s) {
+        lp[s] = T(0);
+#pragma unroll
+        for (int a = 0; a < MAXD; ++a)
+          if (scalar && a < d) lp[s] = fma(lk[s][a], pj[a], lp[s]);
+      }
       const int t1 = p.star_begin[j + 1];
       for (int t = p.star_begin[j]; t < t1; ++t) {
         int ib2 = ib[j] - (int)p.m[t][j];
         ib2 += (ib2 < 0) ? Nj : 0;
         ib2 -= (ib2 >= Nj) ? Nj : 0;
-        const int e2 = e + (ib2 - ib[j]) * sj;
+        const int e2 = e0 + (ib2 - ib[j]) * sj;
         const int k2 = (2 * ib2 < Nj) ? ib2 : ib2 - Nj;
         const T dk = (T)(k2 - k[j]);
-        cplx<T> c;
-        if (scalar) {
-          const T s = fma(dk, lp[j], lam2);
-          c.x = sc[t].x * s;
-          c.y = REALC ? T(0) : sc[t].y * s;
-        } else {
-          T l2[MAXD];
+        const cplx<T>* ct = sc + t * nc;
 #pragma unroll
-          for (int a = 0; a < MAXD; ++a) l2[a] = (a < d) ? fma(dk, pcoef<T>(p, a, j), lk[a]) : T(0);
-          c = weight_general<T>(kind, d, sc + t * nc, lk, l2);
+        for (int s = 0; s < RUN; ++s) {
+          cplx<T> c;
+          if (scalar) {
+            const T w = fma(dk, lp[s], lam2[s]);
+            c.x = ct[0].x * w;
+            c.y = REALC ? T(0) : ct[0].y * w;
+          } else {
+            T l2[MAXD];
+#pragma unroll
+            for (int a = 0; a < MAXD; ++a) l2[a] = (a < d) ? fma(dk, pj[a], lk[s][a]) : T(0);
+            c = weight_general<T>(kind, d, ct, lk[s], l2);
+          }
+#pragma unroll
+          for (int r = 0; r < NR; ++r)
+            if (r < nrhs) mac<T, REALC>(acc[s][r], c, ldh<RO>(h + (size_t)r * D + e2 + s));
         }
-#pragma unroll
-        for (int r = 0; r < NR; ++r)
-          if (r < nrhs) mac<T, REALC>(acc[r], c, ldh<RO>(h + (size_t)r * D + e2));
       }
     }
   }
-  // taps with several nonzero axes
-  for (int t = p.star_begin[p.n]; t < p.ntaps; ++t) {
-    int e2 = e;
-    T l2[MAXD];
+  // star taps of the last axis: per mode (the neighbour may wrap around the row)
+  {
+    const int row0 = e0 - ibl;
+    T pl[MAXD], lp[RUN];
 #pragma unroll
-    for (int a = 0; a < MAXD; ++a) l2[a] = lk[a];
+    for (int a = 0; a < MAXD; ++a) pl[a] = pcoef<T>(p, a, jl);
 #pragma unroll
-    for (int j = 0; j < MAXN; ++j) {
-      const int mj = (j < p.n) ? (int)p.m[t][j] : 0;
+    for (int s = 0; s < RUN; ++s) {
+      lp[s] = T(0);
+#pragma unroll
+      for (int a = 0; a < MAXD; ++a)
+        if (scalar && a < d) lp[s] = fma(lk[s][a], pl[a], lp[s]);
+    }
+    const int t1 = p.star_begin[jl + 1];
+    for (int t = p.star_begin[jl]; t < t1; ++t) {
+      const int mt = (int)p.m[t][jl];
+      const cplx<T>* ct = sc + t * nc;
+#pragma unroll
+      for (int s = 0; s < RUN; ++s) {
+        int ib2 = ibl + s - mt;
+        ib2 += (ib2 < 0) ? Nl : 0;
+        ib2 -= (ib2 >= Nl) ? Nl : 0;
+        const int k2 = (2 * ib2 < Nl) ? ib2 : ib2 - Nl;
+        const T dk = (T)(k2 - kl[s]);
+        cplx<T> c;
+        if (scalar) {
+          const T w = fma(dk, lp[s], lam2[s]);
+          c.x = ct[0].x * w;
+          c.y = REALC ? T(0) : ct[0].y * w;
+        } else {
+          T l2[MAXD];
+#pragma unroll
+          for (int a = 0; a < MAXD; ++a) l2[a] = (a < d) ? fma(dk, pl[a], lk[s][a]) : T(0);
+          c = weight_general<T>(kind, d, ct, lk[s], l2);
+        }
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+          if (r < nrhs) mac<T, REALC>(acc[s][r], c, ldh<RO>(h + (size_t)r * D + row0 + ib2));
+      }
+    }
+  }
+  // taps with several nonzero axes: the other axes once per run, the last axis per mode
+  for (int t = p.star_begin[n]; t < p.ntaps; ++t) {
+    int eo = e0 - ibl;
+    T lo[MAXD];
+#pragma unroll
+    for (int a = 0; a < MAXD; ++a) lo[a] = T(0);
+#pragma unroll
+    for (int j = 0; j < MAXN - 1; ++j) {
+      const int mj = (j < jl) ? (int)p.m[t][j] : 0;
       if (mj != 0) {
         const int Nj = p.N[j];
         int ib2 = ib[j] - mj;
         ib2 += (ib2 < 0) ? Nj : 0;
         ib2 -= (ib2 >= Nj) ? Nj : 0;
-        e2 += (ib2 - ib[j]) * p.stride[j];
+        eo += (ib2 - ib[j]) * p.stride[j];
         const int k2 = (2 * ib2 < Nj) ? ib2 : ib2 - Nj;
         const T dk = (T)(k2 - k[j]);
 #pragma unroll
         for (int a = 0; a < MAXD; ++a)
-          if (a < d) l2[a] = fma(dk, pcoef<T>(p, a, j), l2[a]);
+          if (a < d) lo[a] = fma(dk, pcoef<T>(p, a, j), lo[a]);
       }
     }
-    const cplx<T> c = weight_general<T>(kind, d, sc + t * nc, lk, l2);
+    const int mt = (int)p.m[t][jl];
+    const cplx<T>* ct = sc + t * nc;
 #pragma unroll
-    for (int r = 0; r < NR; ++r)
-      if (r < nrhs) mac<T, REALC>(acc[r], c, ldh<RO>(h + (size_t)r * D + e2));
+    for (int s = 0; s < RUN; ++s) {
+      int ib2 = ibl + s - mt;
+      ib2 += (ib2 < 0) ? Nl : 0;
+      ib2 -= (ib2 >= Nl) ? Nl : 0;
+      const int k2 = (2 * ib2 < Nl) ? ib2 : ib2 - Nl;
+      const T dk = (T)(k2 - kl[s]);
+      T l2[MAXD];
+#pragma unroll
+      for (int a = 0; a < MAXD; ++a) l2[a] = (a < d) ? fma(dk, pcoef<T>(p, a, jl), lk[s][a] + lo[a]) : T(0);
+      const cplx<T> c = weight_general<T>(kind, d, ct, lk[s], l2);
+#pragma unroll
+      for (int r = 0; r < NR; ++r)
+        if (r < nrhs) mac<T, REALC>(acc[s][r], c, ldh<RO>(h + (size_t)r * D + eo + ib2));
+    }
   }
 }
 

@@ -14,7 +14,7 @@ namespace qp {
 
 // ------------------------------------------------------------------------------------------------ batch apply
 
-template <typename T, int EPI, bool REALC, int NR>
+template <typename T, int EPI, bool REALC, int NR, int RUN>
 __global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 3) k_apply(BatchDev b, int level, int refine,
                                                                        unsigned long long cond) {
   __shared__ __align__(16) PlanDev sp;
@@ -57,30 +57,37 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 3) k_apply(BatchDe
     for (int q = 0; q < NV; ++q) vt[q] = T(0);
     const int base = (c - un.chunk0) * un.chunk;
     const int end = min(base + un.chunk, D);
-    for (int e = base + threadIdx.x; e < end; e += BLOCK) {
-      cplx<T> acc[NR];
+    // thread t takes runs of RUN consecutive modes: e0 = base + RUN t, base + RUN (t + BLOCK), ...
+    for (int e0 = base + RUN * threadIdx.x; e0 < end; e0 += RUN * BLOCK) {
+      cplx<T> acc[RUN][NR];
       if (fft_unit) {
 #pragma unroll
-        for (int r = 0; r < NR; ++r) acc[r] = (r < nrhs) ? dst[(size_t)r * D + e] : mk<T>(0, 0);
+        for (int s = 0; s < RUN; ++s)
+#pragma unroll
+          for (int r = 0; r < NR; ++r) acc[s][r] = (r < nrhs) ? dst[(size_t)r * D + e0 + s] : mk<T>(0, 0);
       } else {
-        apply_point<T, REALC, NR>(sp, scoef, e, src, D, nrhs, acc);
+        apply_run<T, REALC, NR, RUN>(sp, scoef, e0, src, D, nrhs, acc);
       }
 #pragma unroll
-      for (int r = 0; r < NR; ++r) {
-        if (r < nrhs) {
-          const size_t o = (size_t)r * D + e;
-          if (EPI == EPI_DOT_HW) {
-            if (!fft_unit) dst[o] = acc[r];
-            const cplx<T> hv = src[o];
-            vt[r] = fma(hv.x, acc[r].x, fma(hv.y, acc[r].y, vt[r]));
-          } else if (EPI == EPI_RESIDUAL) {
-            const cplx<T> f = F[o];
-            const cplx<T> res = (e == 0) ? mk<T>(0, 0) : mk<T>(f.x - acc[r].x, f.y - acc[r].y);
-            dst[o] = res;
-            vt[2 * r] = fma(res.x, res.x, fma(res.y, res.y, vt[2 * r]));
-            if (e != 0) vt[2 * r + 1] = fma(f.x, f.x, fma(f.y, f.y, vt[2 * r + 1]));
-          } else {
-            if (!fft_unit) dst[o] = acc[r];
+      for (int s = 0; s < RUN; ++s) {
+        const int e = e0 + s;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          if (r < nrhs) {
+            const size_t o = (size_t)r * D + e;
+            if (EPI == EPI_DOT_HW) {
+              if (!fft_unit) dst[o] = acc[s][r];
+              const cplx<T> hv = src[o];
+              vt[r] = fma(hv.x, acc[s][r].x, fma(hv.y, acc[s][r].y, vt[r]));
+            } else if (EPI == EPI_RESIDUAL) {
+              const cplx<T> f = F[o];
+              const cplx<T> res = (e == 0) ? mk<T>(0, 0) : mk<T>(f.x - acc[s][r].x, f.y - acc[s][r].y);
+              dst[o] = res;
+              vt[2 * r] = fma(res.x, res.x, fma(res.y, res.y, vt[2 * r]));
+              if (e != 0) vt[2 * r + 1] = fma(f.x, f.x, fma(f.y, f.y, vt[2 * r + 1]));
+            } else {
+              if (!fft_unit) dst[o] = acc[s][r];
+            }
           }
         }
       }
@@ -140,81 +147,99 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 3) k_apply(BatchDe
   }
 }
 
-template <typename T, int EPI, int NR>
+template <typename T, int EPI, int NR, int RUN>
 static void apply_launch_nr(bool realc, const BatchDev& b, int level, int refine, unsigned long long cond, int nblk,
                             size_t smem, cudaStream_t s) {
-  if (realc) k_apply<T, EPI, true, NR><<<nblk, BLOCK, smem, s>>>(b, level, refine, cond);
-  else k_apply<T, EPI, false, NR><<<nblk, BLOCK, smem, s>>>(b, level, refine, cond);
+  if (realc) k_apply<T, EPI, true, NR, RUN><<<nblk, BLOCK, smem, s>>>(b, level, refine, cond);
+  else k_apply<T, EPI, false, NR, RUN><<<nblk, BLOCK, smem, s>>>(b, level, refine, cond);
 }
 
-template <typename T, int EPI>
+template <typename T, int EPI, int RUN>
 static void apply_launch_real(bool realc, int maxr, const BatchDev& b, int level, int refine,
                               unsigned long long cond, int nblk, size_t smem, cudaStream_t s) {
   switch (maxr) {
-    case 1: apply_launch_nr<T, EPI, 1>(realc, b, level, refine, cond, nblk, smem, s); break;
-    case 2: apply_launch_nr<T, EPI, 2>(realc, b, level, refine, cond, nblk, smem, s); break;
-    case 3: apply_launch_nr<T, EPI, 3>(realc, b, level, refine, cond, nblk, smem, s); break;
-    default: apply_launch_nr<T, EPI, 4>(realc, b, level, refine, cond, nblk, smem, s); break;
+    case 1: apply_launch_nr<T, EPI, 1, RUN>(realc, b, level, refine, cond, nblk, smem, s); break;
+    case 2: apply_launch_nr<T, EPI, 2, RUN>(realc, b, level, refine, cond, nblk, smem, s); break;
+    case 3: apply_launch_nr<T, EPI, 3, RUN>(realc, b, level, refine, cond, nblk, smem, s); break;
+    default: apply_launch_nr<T, EPI, 4, RUN>(realc, b, level, refine, cond, nblk, smem, s); break;
+  }
+}
+
+template <int RUN>
+static void apply_launch_run(const BatchDev& b, bool realc, int mc, int maxr, int level, int epi, bool refine,
+                             unsigned long long cond, int nblk, cudaStream_t s) {
+  if (level == LEVEL_FP32) {
+    const size_t smem = (size_t)mc * sizeof(float2);
+    apply_launch_real<float, EPI_DOT_HW, RUN>(realc, maxr, b, level, refine, cond, nblk, smem, s);
+  } else {
+    const size_t smem = (size_t)mc * sizeof(double2);
+    if (epi == EPI_DOT_HW)
+      apply_launch_real<double, EPI_DOT_HW, RUN>(realc, maxr, b, level, refine, cond, nblk, smem, s);
+    else if (epi == EPI_RESIDUAL)
+      apply_launch_real<double, EPI_RESIDUAL, RUN>(realc, maxr, b, level, refine, cond, nblk, smem, s);
+    else apply_launch_real<double, EPI_NONE, RUN>(realc, maxr, b, level, refine, cond, nblk, smem, s);
   }
 }
 
 // realc: every taps plan of the batch has real tap values; mc: the largest ntaps * ncomp of its plans (sizes
-// the shared coefficient table); maxr: the largest nrhs of its units.
+// the shared coefficient table); maxr: the largest nrhs of its units; run: modes per thread step (2 when the
+// last axis of every unit has even length, else 1).
 void launch_apply(const BatchDev& b, bool realc, int mc, int maxr, int level, int epi, bool refine,
-                  unsigned long long cond, int nblk, cudaStream_t s) {
-  if (level == LEVEL_FP32) {
-    const size_t smem = (size_t)mc * sizeof(float2);
-    apply_launch_real<float, EPI_DOT_HW>(realc, maxr, b, level, refine, cond, nblk, smem, s);
-  } else {
-    const size_t smem = (size_t)mc * sizeof(double2);
-    if (epi == EPI_DOT_HW) apply_launch_real<double, EPI_DOT_HW>(realc, maxr, b, level, refine, cond, nblk, smem, s);
-    else if (epi == EPI_RESIDUAL)
-      apply_launch_real<double, EPI_RESIDUAL>(realc, maxr, b, level, refine, cond, nblk, smem, s);
-    else apply_launch_real<double, EPI_NONE>(realc, maxr, b, level, refine, cond, nblk, smem, s);
-  }
+                  unsigned long long cond, int nblk, int run, cudaStream_t s) {
+  if (run == 2) apply_launch_run<2>(b, realc, mc, maxr, level, epi, refine, cond, nblk, s);
+  else apply_launch_run<1>(b, realc, mc, maxr, level, epi, refine, cond, nblk, s);
   count_launch();
 }
 
 // ------------------------------------------------------------------------------------------------ plain apply
 
-template <typename T, bool REALC, int NR>
+template <typename T, bool REALC, int NR, int RUN>
 __global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 3) k_apply_plain(const PlanDev* plan, int D, int nrhs,
                                                                              const cplx<T>* h, cplx<T>* w) {
   __shared__ __align__(16) PlanDev sp;
   extern __shared__ __align__(16) unsigned char smraw[];
   cplx<T>* scoef = reinterpret_cast<cplx<T>*>(smraw);
   load_plan<T>(plan, sp, scoef);
-  const int e = blockIdx.x * BLOCK + threadIdx.x;   // one mode per thread: blocks sweep memory in order
-  if (e >= D) return;
-  cplx<T> acc[NR];
-  apply_point<T, REALC, NR>(sp, scoef, e, h, D, nrhs, acc);
+  const int e0 = (blockIdx.x * BLOCK + threadIdx.x) * RUN;   // one run per thread: blocks sweep memory in order
+  if (e0 >= D) return;
+  cplx<T> acc[RUN][NR];
+  apply_run<T, REALC, NR, RUN>(sp, scoef, e0, h, D, nrhs, acc);
 #pragma unroll
-  for (int r = 0; r < NR; ++r)
-    if (r < nrhs) w[(size_t)r * D + e] = acc[r];
+  for (int s = 0; s < RUN; ++s)
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+      if (r < nrhs) w[(size_t)r * D + e0 + s] = acc[s][r];
 }
 
-template <typename T, bool REALC>
-static void plain_nr(int nrhs, const PlanDev* plan_dev, int D, const cplx<T>* h, cplx<T>* w, int nblk, size_t smem,
+template <typename T, bool REALC, int RUN>
+static void plain_nr(int nrhs, const PlanDev* plan_dev, int D, const cplx<T>* h, cplx<T>* w, size_t smem,
                      cudaStream_t s) {
+  const int nblk = (D / RUN + BLOCK - 1) / BLOCK;
   switch (nrhs) {
-    case 1: k_apply_plain<T, REALC, 1><<<nblk, BLOCK, smem, s>>>(plan_dev, D, nrhs, h, w); break;
-    case 2: k_apply_plain<T, REALC, 2><<<nblk, BLOCK, smem, s>>>(plan_dev, D, nrhs, h, w); break;
-    case 3: k_apply_plain<T, REALC, 3><<<nblk, BLOCK, smem, s>>>(plan_dev, D, nrhs, h, w); break;
-    default: k_apply_plain<T, REALC, 4><<<nblk, BLOCK, smem, s>>>(plan_dev, D, nrhs, h, w); break;
+    case 1: k_apply_plain<T, REALC, 1, RUN><<<nblk, BLOCK, smem, s>>>(plan_dev, D, nrhs, h, w); break;
+    case 2: k_apply_plain<T, REALC, 2, RUN><<<nblk, BLOCK, smem, s>>>(plan_dev, D, nrhs, h, w); break;
+    case 3: k_apply_plain<T, REALC, 3, RUN><<<nblk, BLOCK, smem, s>>>(plan_dev, D, nrhs, h, w); break;
+    default: k_apply_plain<T, REALC, 4, RUN><<<nblk, BLOCK, smem, s>>>(plan_dev, D, nrhs, h, w); break;
   }
 }
 
+// run: modes per thread (2 when the last axis has even length, else 1).
 template <typename T>
 void launch_apply_plain(const PlanDev* plan_dev, bool realc, int mc, int D, int nrhs, const cplx<T>* h, cplx<T>* w,
-                        cudaStream_t s) {
+                        int run, cudaStream_t s) {
   const size_t smem = (size_t)mc * sizeof(cplx<T>);
-  const int nblk = (D + BLOCK - 1) / BLOCK;
-  if (realc) plain_nr<T, true>(nrhs, plan_dev, D, h, w, nblk, smem, s);
-  else plain_nr<T, false>(nrhs, plan_dev, D, h, w, nblk, smem, s);
+  if (run == 2) {
+    if (realc) plain_nr<T, true, 2>(nrhs, plan_dev, D, h, w, smem, s);
+    else plain_nr<T, false, 2>(nrhs, plan_dev, D, h, w, smem, s);
+  } else {
+    if (realc) plain_nr<T, true, 1>(nrhs, plan_dev, D, h, w, smem, s);
+    else plain_nr<T, false, 1>(nrhs, plan_dev, D, h, w, smem, s);
+  }
   count_launch();
 }
-template void launch_apply_plain<double>(const PlanDev*, bool, int, int, int, const double2*, double2*, cudaStream_t);
-template void launch_apply_plain<float>(const PlanDev*, bool, int, int, int, const float2*, float2*, cudaStream_t);
+template void launch_apply_plain<double>(const PlanDev*, bool, int, int, int, const double2*, double2*, int,
+                                         cudaStream_t);
+template void launch_apply_plain<float>(const PlanDev*, bool, int, int, int, const float2*, float2*, int, cudaStream_t);
 
 // ------------------------------------------------------------------------------------------------ set-up kernels
 
