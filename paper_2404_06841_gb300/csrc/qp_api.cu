@@ -446,9 +446,10 @@ struct Units {
 
 // One stiffness apply over all units at a level: the FFT passes of FFT-backend units (they write w), then the
 // batch stencil/epilogue kernel.
-void record_apply(const Units& us, const Entry& en, int level, int epi, bool refine, unsigned long long cond,
+void record_apply(const Units& us, const Entry& en, int level, int epi, int refine, unsigned long long cond,
                   cudaStream_t s) {
   for (size_t u = 0; u < us.plans.size(); ++u) {
+    if (refine == REFINE_ZERO_U) break;   // Q U = 0: no FFT passes either
     qp_plan* p = us.plans[u];
     if (p->backend != QP_BACKEND_FFT) continue;
     const int nr = us.nrhs[u];
@@ -461,7 +462,7 @@ void record_apply(const Units& us, const Entry& en, int level, int epi, bool ref
 }
 
 void body_pcg(const Units& us, const Entry& en, int level, unsigned long long cond, cudaStream_t s) {
-  record_apply(us, en, level, EPI_DOT_HW, false, cond, s);
+  record_apply(us, en, level, EPI_DOT_HW, REFINE_NONE, cond, s);
   launch_pcg_update(en.bd, us.max_rhs, level, cond, en.nblk, s);
   launch_pcg_hupdate(en.bd, us.max_rhs, level, en.nblk, s);
   CK_LAUNCH();
@@ -537,8 +538,9 @@ int count_kernel_nodes(cudaGraph_t g) {
 
 // Records the solve:
 //  FP64 mode:   [zero U] reset, [warm: w = Q U], init, WHILE{ apply+(h,w); update; hupdate }, true residual.
-//  refinement:  [zero U] outer reset, WHILE_outer{ r64 = F - Q U (FP64, decides convergence); F32 = r64/|r64|;
-//               reset; init32; WHILE_inner{ apply32; update32; hupdate32 }; U += |r64| c32 }.
+//  refinement:  [zero U] outer reset, r64 = F - Q U (FP64, decides convergence; = F without a warm start),
+//               WHILE_outer{ F32 = r64/|r64|; reset; init32; WHILE_inner{ apply32; update32; hupdate32 };
+//               U += |r64| c32; r64 = F - Q U }.
 void build_graph(const Units& us, Entry& en, const Key& key, cudaStream_t cap) {
   cudaGraph_t g;
   CK(cudaGraphCreate(&g, 0));
@@ -549,30 +551,32 @@ void build_graph(const Units& us, Entry& en, const Key& key, cudaStream_t cap) {
     auto pre = capture_into(g, {}, cap, [&](cudaStream_t s) {
       if (!key.warm) zero_solutions(us, s);
       launch_level_reset(en.bd, 0, s);
-      if (key.warm) record_apply(us, en, LEVEL_FP64, EPI_NONE, false, 0, s);
+      if (key.warm) record_apply(us, en, LEVEL_FP64, EPI_NONE, REFINE_NONE, 0, s);
       launch_pcg_init(en.bd, us.max_rhs, LEVEL_FP64, key.warm != 0, hc, en.nblk, s);
       CK_LAUNCH();
     });
     auto wl = add_while(g, pre, hc);
     capture_into(wl.second, {}, cap, [&](cudaStream_t s) { body_pcg(us, en, LEVEL_FP64, hc, s); });
     capture_into(g, {wl.first}, cap, [&](cudaStream_t s) {
-      record_apply(us, en, LEVEL_FP64, EPI_RESIDUAL, false, 0, s);
+      record_apply(us, en, LEVEL_FP64, EPI_RESIDUAL, REFINE_NONE, 0, s);
       zero_mean_mode(us, s);
     });
     en.body_nodes = count_kernel_nodes(wl.second);
   } else {
     cudaGraphConditionalHandle ho;
     CK(cudaGraphConditionalHandleCreate(&ho, g, 1, cudaGraphCondAssignDefault));
+    // the first true residual before the loop (U = 0 without a warm start: r64 = F, no apply), then per
+    // outer iteration: inner FP32 solve, accumulation, true residual
     auto pre = capture_into(g, {}, cap, [&](cudaStream_t s) {
       if (!key.warm) zero_solutions(us, s);
       launch_level_reset(en.bd, 1, s);
+      record_apply(us, en, LEVEL_FP64, EPI_RESIDUAL, key.warm ? REFINE_ON : REFINE_ZERO_U, ho, s);
     });
     auto wo = add_while(g, pre, ho);
     cudaGraph_t ob = wo.second;
     cudaGraphConditionalHandle hi;
     CK(cudaGraphConditionalHandleCreate(&hi, ob, 1, cudaGraphCondAssignDefault));
     auto b1 = capture_into(ob, {}, cap, [&](cudaStream_t s) {
-      record_apply(us, en, LEVEL_FP64, EPI_RESIDUAL, true, ho, s);
       launch_refine_prep(en.bd, en.nblk, s);
       launch_level_reset(en.bd, 0, s);
       launch_pcg_init(en.bd, us.max_rhs, LEVEL_FP32, false, hi, en.nblk, s);
@@ -582,6 +586,7 @@ void build_graph(const Units& us, Entry& en, const Key& key, cudaStream_t cap) {
     capture_into(wi.second, {}, cap, [&](cudaStream_t s) { body_pcg(us, en, LEVEL_FP32, hi, s); });
     capture_into(ob, {wi.first}, cap, [&](cudaStream_t s) {
       launch_refine_accum(en.bd, en.nblk, s);
+      record_apply(us, en, LEVEL_FP64, EPI_RESIDUAL, REFINE_ON, ho, s);
       CK_LAUNCH();
     });
     capture_into(g, {wo.first}, cap, [&](cudaStream_t s) { zero_mean_mode(us, s); });
@@ -612,21 +617,22 @@ void run_direct(const Units& us, Entry& en, const Key& key, int nslots, cudaStre
   if (key.mode == QP_MODE_FP64) {
     if (!key.warm) zero_solutions(us, s);
     launch_level_reset(en.bd, 0, s);
-    if (key.warm) record_apply(us, en, LEVEL_FP64, EPI_NONE, false, 0, s);
+    if (key.warm) record_apply(us, en, LEVEL_FP64, EPI_NONE, REFINE_NONE, 0, s);
     launch_pcg_init(en.bd, us.max_rhs, LEVEL_FP64, key.warm != 0, 0, en.nblk, s);
     pcg_loop(LEVEL_FP64);
-    record_apply(us, en, LEVEL_FP64, EPI_RESIDUAL, false, 0, s);
+    record_apply(us, en, LEVEL_FP64, EPI_RESIDUAL, REFINE_NONE, 0, s);
   } else {
     if (!key.warm) zero_solutions(us, s);
     launch_level_reset(en.bd, 1, s);
+    record_apply(us, en, LEVEL_FP64, EPI_RESIDUAL, key.warm ? REFINE_ON : REFINE_ZERO_U, 0, s);
     for (int outer = 0; outer < 64; ++outer) {
-      record_apply(us, en, LEVEL_FP64, EPI_RESIDUAL, true, 0, s);
       if (read_done(1) >= nslots) break;
       launch_refine_prep(en.bd, en.nblk, s);
       launch_level_reset(en.bd, 0, s);
       launch_pcg_init(en.bd, us.max_rhs, LEVEL_FP32, false, 0, en.nblk, s);
       pcg_loop(LEVEL_FP32);
       launch_refine_accum(en.bd, en.nblk, s);
+      record_apply(us, en, LEVEL_FP64, EPI_RESIDUAL, REFINE_ON, 0, s);
       CK_LAUNCH();
     }
   }
@@ -793,7 +799,8 @@ void run_solve(Solver* sv, const Units& us, const Key& key, cudaStream_t s, Solv
     }
   if (en.exec) {
     if (key.mode == QP_MODE_FP64) count_launch(en.fixed_nodes + en.body_nodes * std::max(1, max_it));
-    else count_launch(en.fixed_nodes + en.outer_nodes * max_outer + en.body_nodes * (sum_inner_max + max_outer));
+    else count_launch(en.fixed_nodes + en.outer_nodes * std::max(0, max_outer - 1) +
+                      en.body_nodes * (sum_inner_max + max_outer));
   }
 }
 

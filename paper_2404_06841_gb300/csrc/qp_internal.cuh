@@ -41,6 +41,8 @@ constexpr int MAXT = QP_MAX_TAPS;
 constexpr int BLOCK = 256;           // threads per block of every elementwise / stencil kernel
 constexpr int NQ = 4;                // reduction quantities per right-hand side
 constexpr int NSLOT = MAXR * NQ;     // partial slots per chunk
+// residual epilogue: plain, with the refinement bookkeeping, or with it and U = 0 (Q U not computed)
+enum { REFINE_NONE = 0, REFINE_ON = 1, REFINE_ZERO_U = 2 };
 // the persistent solve keeps consecutive reductions in disjoint slots: init [0,12), (h,w) [12,16),
 // update [16,24), true residual [24,32)
 constexpr int NSLOT_PERSIST = 2 * NSLOT;
@@ -138,7 +140,7 @@ enum { LEVEL_FP64 = 0, LEVEL_FP32 = 1 };   // which vector set a PCG kernel work
 // set to 0 by the call that completes the count of finished right-hand sides.
 // realc: every taps plan in the batch has real tap values; mc: largest ntaps * ncomp over its taps plans.
 // maxr: the largest nrhs of the batch's units.
-void launch_apply(const BatchDev& b, bool realc, int mc, int maxr, int level, int epi, bool refine,
+void launch_apply(const BatchDev& b, bool realc, int mc, int maxr, int level, int epi, int refine,
                   unsigned long long cond, int nblk, int run, cudaStream_t s);
 // Standalone apply of one plan: w = Q h for nrhs vectors (no reductions).
 template <typename T>

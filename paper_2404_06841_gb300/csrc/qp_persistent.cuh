@@ -142,7 +142,7 @@ __device__ __forceinline__ void ph_init(const BatchDev& b, const UnitDev& un, in
 template <typename T, bool REALC, int NR, int EPI>
 __device__ __forceinline__ void ph_apply(const BatchDev& b, const UnitDev& un, int c, const PlanDev& sp,
                                          const cplx<T>* scoef, const cplx<T>* src, cplx<T>* dst,
-                                         const cplx<T>* F) {
+                                         const cplx<T>* F, bool zero_src = false) {
   const int D = un.D, nrhs = un.nrhs;
   constexpr int NV = (EPI == EPI_RESIDUAL) ? 2 * NR : NR;
   T vt[NV];
@@ -153,7 +153,14 @@ __device__ __forceinline__ void ph_apply(const BatchDev& b, const UnitDev& un, i
   chunk_range(un, c, base, end);
   for (int e0 = base + PRUN * threadIdx.x; e0 < end; e0 += PRUN * BLOCK) {
     cplx<T> acc[PRUN][NR];
-    apply_run<T, REALC, NR, PRUN, false>(sp, scoef, e0, src, D, nrhs, acc);
+    if (zero_src) {   // src = 0: Q src = 0
+#pragma unroll
+      for (int s = 0; s < PRUN; ++s)
+#pragma unroll
+        for (int r = 0; r < NR; ++r) acc[s][r] = mk<T>(0, 0);
+    } else {
+      apply_run<T, REALC, NR, PRUN, false>(sp, scoef, e0, src, D, nrhs, acc);
+    }
 #pragma unroll
     for (int s = 0; s < PRUN; ++s) {
       const int e = e0 + s;
@@ -376,12 +383,13 @@ __device__ __forceinline__ bool pcg_solve_block(const PersistArgs& a, const Unit
 }
 
 // FP64 true residual w = F - Q U and its reduction; every thread gets (|r|^2, |F|^2) per right-hand side.
+// zero_u: U = 0, so w = F without an apply.
 template <bool REALC, int NR>
 __device__ __forceinline__ bool true_residual(const PersistArgs& a, const UnitDev& un, const PlanDev& sp, const double2* sc64,
-                              double (&v)[2 * NR]) {
+                              double (&v)[2 * NR], bool zero_u = false) {
   const BatchDev& b = a.b;
   for (int c = blockIdx.x; c < b.nchunks; c += gridDim.x)
-    ph_apply<double, REALC, NR, EPI_RESIDUAL>(b, un, c, sp, sc64, un.U, un.w, un.F);
+    ph_apply<double, REALC, NR, EPI_RESIDUAL>(b, un, c, sp, sc64, un.U, un.w, un.F, zero_u);
   if (!grid_sync(a)) return false;
   all_sums<2 * NR>(b, un, S_RES, v);
   return true;
@@ -439,7 +447,7 @@ __global__ void __launch_bounds__(BLOCK, 2) k_pcg_persistent(PersistArgs a) {
     for (int outer = 0; ok && outer <= b.max_outer + 1; ++outer) {
       // FP64 true residual: the outer convergence test and the scale of the next inner right-hand side
       double v[2 * NR];
-      if (!(ok = true_residual<REALC, NR>(a, un, sp, sc64, v))) break;
+      if (!(ok = true_residual<REALC, NR>(a, un, sp, sc64, v, outer == 0 && !a.warm))) break;
       if (threadIdx.x == 0) {
         for (int k = 0; k < nrhs && k < NR; ++k) {
           RhsSt& x = ls[k];

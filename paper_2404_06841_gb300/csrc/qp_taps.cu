@@ -60,7 +60,12 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 3) k_apply(BatchDe
     // thread t takes runs of RUN consecutive modes: e0 = base + RUN t, base + RUN (t + BLOCK), ...
     for (int e0 = base + RUN * threadIdx.x; e0 < end; e0 += RUN * BLOCK) {
       cplx<T> acc[RUN][NR];
-      if (fft_unit) {
+      if (EPI == EPI_RESIDUAL && refine == REFINE_ZERO_U) {
+#pragma unroll
+        for (int s = 0; s < RUN; ++s)
+#pragma unroll
+          for (int r = 0; r < NR; ++r) acc[s][r] = mk<T>(0, 0);
+      } else if (fft_unit) {
 #pragma unroll
         for (int s = 0; s < RUN; ++s)
 #pragma unroll
@@ -166,7 +171,7 @@ static void apply_launch_real(bool realc, int maxr, const BatchDev& b, int level
 }
 
 template <int RUN>
-static void apply_launch_run(const BatchDev& b, bool realc, int mc, int maxr, int level, int epi, bool refine,
+static void apply_launch_run(const BatchDev& b, bool realc, int mc, int maxr, int level, int epi, int refine,
                              unsigned long long cond, int nblk, cudaStream_t s) {
   if (level == LEVEL_FP32) {
     const size_t smem = (size_t)mc * sizeof(float2);
@@ -183,8 +188,9 @@ static void apply_launch_run(const BatchDev& b, bool realc, int mc, int maxr, in
 
 // realc: every taps plan of the batch has real tap values; mc: the largest ntaps * ncomp of its plans (sizes
 // the shared coefficient table); maxr: the largest nrhs of its units; run: modes per thread step (2 when the
-// last axis of every unit has even length, else 1).
-void launch_apply(const BatchDev& b, bool realc, int mc, int maxr, int level, int epi, bool refine,
+// last axis of every unit has even length, else 1); refine: REFINE_* (the refinement bookkeeping of the residual
+// epilogue; REFINE_ZERO_U: the solutions are zero, so Q U = 0 is not computed).
+void launch_apply(const BatchDev& b, bool realc, int mc, int maxr, int level, int epi, int refine,
                   unsigned long long cond, int nblk, int run, cudaStream_t s) {
   if (run == 2) apply_launch_run<2>(b, realc, mc, maxr, level, epi, refine, cond, nblk, s);
   else apply_launch_run<1>(b, realc, mc, maxr, level, epi, refine, cond, nblk, s);
