@@ -429,7 +429,8 @@ void alloc_workspace(qp_plan* p) {
 // ------------------------------------------------------------------------------------------------ recording
 
 // Modes per thread step of the stencil kernels for this plan: runs of 2 along the last axis when its length is
-// even (the run then never crosses a row), else 1.
+// even (the run then never crosses a row), else 1. (Longer runs cut index work further but need more registers
+// per thread; on GB300 the occupancy they cost outweighed it.)
 int last_axis_run(const qp_plan* p) { return (p->host_pd.N[p->host_pd.n - 1] % 2 == 0) ? 2 : 1; }
 
 // Everything a solve needs about its units on the host side.
@@ -441,7 +442,7 @@ struct Units {
   int max_rhs = 1;
   bool direct = false;    // launch kernels directly (host-driven loops) instead of recording a graph
   int exec = QP_EXEC_GRAPH;  // QP_EXEC_AUTO / PERSISTENT: a single taps unit may run as one persistent launch
-  int run = 2;               // stencil modes per thread step: 2 when every unit's last axis has even length
+  int run = 2;               // shortest stencil run of the units (the persistent form needs 2)
 };
 
 // One stiffness apply over all units at a level: the FFT passes of FFT-backend units (they write w), then the
@@ -457,7 +458,7 @@ void record_apply(const Units& us, const Entry& en, int level, int epi, int refi
     else if (epi == EPI_DOT_HW) fft_apply<double>(p->fft, p->host_pd, p->pd, p->v64.h, p->v64.w, nr, s);
     else fft_apply<double>(p->fft, p->host_pd, p->pd, p->v64.X, p->v64.w, nr, s);
   }
-  launch_apply(en.bd, us.all_real, us.max_coef, us.max_rhs, level, epi, refine, cond, en.nblk, us.run, s);
+  launch_apply(en.bd, us.all_real, us.max_coef, us.max_rhs, level, epi, refine, cond, en.nblk, s);
   CK_LAUNCH();
 }
 
@@ -666,6 +667,7 @@ Entry& get_entry(Solver* sv, const Units& us, const Key& key) {
     // chunks per SM, 256 to 8192 modes), so the reduction order of a unit does not depend on its batch
     const int64_t chunk = std::max<int64_t>(BLOCK, std::min<int64_t>(8192, (p->D / (152 * 8) + BLOCK - 1) / BLOCK * BLOCK));
     x.chunk = (int)chunk;
+    x.run = last_axis_run(p);
     x.chunk0 = (int)chunk_unit.size();
     x.nchunk = (int)((p->D + chunk - 1) / chunk);
     for (int c = 0; c < x.nchunk; ++c) chunk_unit.push_back(u);

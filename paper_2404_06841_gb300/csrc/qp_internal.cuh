@@ -90,7 +90,9 @@ static_assert(sizeof(PlanDev) % 16 == 0, "PlanDev is copied to shared memory in 
 struct UnitDev {
   const PlanDev* plan;
   int D, nrhs, chunk0, nchunk;
-  int chunk, pad_[3];  // modes per chunk: a function of D only, so a unit reduces in the same order alone or batched
+  int chunk;           // modes per chunk: a function of D only, so a unit reduces in the same order alone or batched
+  int run;             // stencil run along the last axis: 2 when its length is even, else 1
+  int pad_[2];
   const double2* F;   // right-hand side (FP64)
   double2* U;         // solution (FP64)
   double2* r;         // FP64 PCG residual
@@ -141,7 +143,7 @@ enum { LEVEL_FP64 = 0, LEVEL_FP32 = 1 };   // which vector set a PCG kernel work
 // realc: every taps plan in the batch has real tap values; mc: largest ntaps * ncomp over its taps plans.
 // maxr: the largest nrhs of the batch's units.
 void launch_apply(const BatchDev& b, bool realc, int mc, int maxr, int level, int epi, int refine,
-                  unsigned long long cond, int nblk, int run, cudaStream_t s);
+                  unsigned long long cond, int nblk, cudaStream_t s);
 // Standalone apply of one plan: w = Q h for nrhs vectors (no reductions).
 template <typename T>
 void launch_apply_plain(const PlanDev* plan_dev, bool realc, int mc, int D, int nrhs, const cplx<T>* h, cplx<T>* w,

@@ -217,7 +217,7 @@ extern "C" qp_status qp_pcg_solve_taps_static(int d, int n, const double* P, con
     const int nc = ht.pd.ncomp, G = ht.pd.ntaps;
     const int64_t chunk = std::max<int64_t>(BLOCK, std::min<int64_t>(8192, (D / (152 * 8) + BLOCK - 1) / BLOCK * BLOCK));
     const int nchunks = (int)((D + chunk - 1) / chunk);
-    const int run = (N[n - 1] % 2 == 0) ? 2 : 1;   // modes per thread step of the stencil
+    const int run = (N[n - 1] % 2 == 0) ? 2 : 1;   // stencil run along the last axis
     const int nblk_diag = (int)std::min<int64_t>((D + BLOCK - 1) / BLOCK, 152 * 8);
 
     // carve the static scratch (size checks before any device work)
@@ -267,6 +267,7 @@ extern "C" qp_status qp_pcg_solve_taps_static(int d, int n, const double* P, con
     un.D = D;
     un.nrhs = nrhs;
     un.chunk = (int)chunk;
+    un.run = run;
     un.chunk0 = 0;
     un.nchunk = nchunks;
     un.F = static_cast<const double2*>(F);
@@ -295,7 +296,7 @@ extern "C" qp_status qp_pcg_solve_taps_static(int d, int n, const double* P, con
     // warm start from U: w = Q U, r = F - w, then Algorithm 2 with the host polling the done count
     const bool realc = ht.real;
     launch_level_reset(bd, 0, s);
-    launch_apply(bd, realc, G * nc, nrhs, LEVEL_FP64, EPI_NONE, false, 0, nchunks, run, s);
+    launch_apply(bd, realc, G * nc, nrhs, LEVEL_FP64, EPI_NONE, false, 0, nchunks, s);
     launch_pcg_init(bd, nrhs, LEVEL_FP64, true, 0, nchunks, s);
     CK_LAUNCH();
     int done = 0, launched = 0, burst = 4;
@@ -305,7 +306,7 @@ extern "C" qp_status qp_pcg_solve_taps_static(int d, int n, const double* P, con
       if (done >= nrhs) break;
       if (launched > opts->maxit + 64) raise(QP_ERR_CUDA, "PCG loop exceeded its cap without the device count");
       for (int i = 0; i < burst; ++i) {
-        launch_apply(bd, realc, G * nc, nrhs, LEVEL_FP64, EPI_DOT_HW, false, 0, nchunks, run, s);
+        launch_apply(bd, realc, G * nc, nrhs, LEVEL_FP64, EPI_DOT_HW, false, 0, nchunks, s);
         launch_pcg_update(bd, nrhs, LEVEL_FP64, 0, nchunks, s);
         launch_pcg_hupdate(bd, nrhs, LEVEL_FP64, nchunks, s);
       }
@@ -314,7 +315,7 @@ extern "C" qp_status qp_pcg_solve_taps_static(int d, int n, const double* P, con
       burst = std::min(burst * 2, 32);
     }
     // FP64 true residual, then U(k = 0) = 0
-    launch_apply(bd, realc, G * nc, nrhs, LEVEL_FP64, EPI_RESIDUAL, false, 0, nchunks, run, s);
+    launch_apply(bd, realc, G * nc, nrhs, LEVEL_FP64, EPI_RESIDUAL, false, 0, nchunks, s);
     CK_LAUNCH();
     for (int k = 0; k < nrhs; ++k)
       CK(cudaMemsetAsync(static_cast<double2*>(U) + (size_t)k * D, 0, sizeof(double2), s));

@@ -20,7 +20,8 @@ namespace qp {
 namespace {
 
 constexpr int S_INIT = 0, S_HW = 12, S_UPD = 16, S_RES = 24;   // partial slots of the four reductions
-constexpr int PRUN = 2;   // stencil runs of two modes (the plan's last axis has even length)
+// stencil runs of two modes as in the graph form (the plan's last axis has even length)
+template <typename T> __host__ __device__ constexpr int prun() { return 2; }
 static_assert(S_HW >= 3 * MAXR && S_UPD >= S_HW + MAXR && S_RES >= S_UPD + 2 * MAXR &&
                   NSLOT_PERSIST >= S_RES + 2 * MAXR,
               "persistent partial slots overlap");
@@ -151,6 +152,7 @@ __device__ __forceinline__ void ph_apply(const BatchDev& b, const UnitDev& un, i
   for (int q = 0; q < NV; ++q) vt[q] = T(0);
   int base, end;
   chunk_range(un, c, base, end);
+  constexpr int PRUN = prun<T>();
   for (int e0 = base + PRUN * threadIdx.x; e0 < end; e0 += PRUN * BLOCK) {
     cplx<T> acc[PRUN][NR];
     if (zero_src) {   // src = 0: Q src = 0
@@ -396,7 +398,7 @@ __device__ __forceinline__ bool true_residual(const PersistArgs& a, const UnitDe
 }
 
 template <bool REALC, int NR>
-__global__ void __launch_bounds__(BLOCK, 2) k_pcg_persistent(PersistArgs a) {
+__global__ void __launch_bounds__(BLOCK, NR >= 3 ? 1 : 2) k_pcg_persistent(PersistArgs a) {
   __shared__ __align__(16) PlanDev sp;
   __shared__ RhsSt ls[MAXR];
   __shared__ int s_zero[MAXR];

@@ -14,9 +14,55 @@ namespace qp {
 
 // ------------------------------------------------------------------------------------------------ batch apply
 
-template <typename T, int EPI, bool REALC, int NR, int RUN>
-__global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 3) k_apply(BatchDev b, int level, int refine,
-                                                                       unsigned long long cond) {
+// One chunk [base, end) of a unit: dst = Q src with the epilogue, per-thread partials into vt. Thread t takes
+// runs of RUN consecutive modes: e0 = base + RUN t, base + RUN (t + BLOCK), ...
+template <typename T, int EPI, bool REALC, int NR, int RUN, int NV>
+__device__ __forceinline__ void apply_chunk(const PlanDev& sp, const cplx<T>* scoef, int base, int end, int D,
+                                            int nrhs, int refine, bool fft_unit, const cplx<T>* src, cplx<T>* dst,
+                                            const cplx<T>* F, T (&vt)[NV]) {
+  for (int e0 = base + RUN * threadIdx.x; e0 < end; e0 += RUN * BLOCK) {
+    cplx<T> acc[RUN][NR];
+    if (EPI == EPI_RESIDUAL && refine == REFINE_ZERO_U) {
+#pragma unroll
+      for (int s = 0; s < RUN; ++s)
+#pragma unroll
+        for (int r = 0; r < NR; ++r) acc[s][r] = mk<T>(0, 0);
+    } else if (fft_unit) {
+#pragma unroll
+      for (int s = 0; s < RUN; ++s)
+#pragma unroll
+        for (int r = 0; r < NR; ++r) acc[s][r] = (r < nrhs) ? dst[(size_t)r * D + e0 + s] : mk<T>(0, 0);
+    } else {
+      apply_run<T, REALC, NR, RUN>(sp, scoef, e0, src, D, nrhs, acc);
+    }
+#pragma unroll
+    for (int s = 0; s < RUN; ++s) {
+      const int e = e0 + s;
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        if (r < nrhs) {
+          const size_t o = (size_t)r * D + e;
+          if (EPI == EPI_DOT_HW) {
+            if (!fft_unit) dst[o] = acc[s][r];
+            const cplx<T> hv = src[o];
+            vt[r] = fma(hv.x, acc[s][r].x, fma(hv.y, acc[s][r].y, vt[r]));
+          } else if (EPI == EPI_RESIDUAL) {
+            const cplx<T> f = F[o];
+            const cplx<T> res = (e == 0) ? mk<T>(0, 0) : mk<T>(f.x - acc[s][r].x, f.y - acc[s][r].y);
+            dst[o] = res;
+            vt[2 * r] = fma(res.x, res.x, fma(res.y, res.y, vt[2 * r]));
+            if (e != 0) vt[2 * r + 1] = fma(f.x, f.x, fma(f.y, f.y, vt[2 * r + 1]));
+          } else {
+            if (!fft_unit) dst[o] = acc[s][r];
+          }
+        }
+      }
+    }
+  }
+}
+
+template <typename T, int EPI, bool REALC, int NR>
+__global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 3) k_apply(BatchDev b, int level, int refine, unsigned long long cond) {
   __shared__ __align__(16) PlanDev sp;
   extern __shared__ __align__(16) unsigned char smraw[];
   cplx<T>* scoef = reinterpret_cast<cplx<T>*>(smraw);
@@ -57,46 +103,11 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 3) k_apply(BatchDe
     for (int q = 0; q < NV; ++q) vt[q] = T(0);
     const int base = (c - un.chunk0) * un.chunk;
     const int end = min(base + un.chunk, D);
-    // thread t takes runs of RUN consecutive modes: e0 = base + RUN t, base + RUN (t + BLOCK), ...
-    for (int e0 = base + RUN * threadIdx.x; e0 < end; e0 += RUN * BLOCK) {
-      cplx<T> acc[RUN][NR];
-      if (EPI == EPI_RESIDUAL && refine == REFINE_ZERO_U) {
-#pragma unroll
-        for (int s = 0; s < RUN; ++s)
-#pragma unroll
-          for (int r = 0; r < NR; ++r) acc[s][r] = mk<T>(0, 0);
-      } else if (fft_unit) {
-#pragma unroll
-        for (int s = 0; s < RUN; ++s)
-#pragma unroll
-          for (int r = 0; r < NR; ++r) acc[s][r] = (r < nrhs) ? dst[(size_t)r * D + e0 + s] : mk<T>(0, 0);
-      } else {
-        apply_run<T, REALC, NR, RUN>(sp, scoef, e0, src, D, nrhs, acc);
-      }
-#pragma unroll
-      for (int s = 0; s < RUN; ++s) {
-        const int e = e0 + s;
-#pragma unroll
-        for (int r = 0; r < NR; ++r) {
-          if (r < nrhs) {
-            const size_t o = (size_t)r * D + e;
-            if (EPI == EPI_DOT_HW) {
-              if (!fft_unit) dst[o] = acc[s][r];
-              const cplx<T> hv = src[o];
-              vt[r] = fma(hv.x, acc[s][r].x, fma(hv.y, acc[s][r].y, vt[r]));
-            } else if (EPI == EPI_RESIDUAL) {
-              const cplx<T> f = F[o];
-              const cplx<T> res = (e == 0) ? mk<T>(0, 0) : mk<T>(f.x - acc[s][r].x, f.y - acc[s][r].y);
-              dst[o] = res;
-              vt[2 * r] = fma(res.x, res.x, fma(res.y, res.y, vt[2 * r]));
-              if (e != 0) vt[2 * r + 1] = fma(f.x, f.x, fma(f.y, f.y, vt[2 * r + 1]));
-            } else {
-              if (!fft_unit) dst[o] = acc[s][r];
-            }
-          }
-        }
-      }
-    }
+    // the unit's own run length (so that its reduction order does not depend on the batch)
+    if (un.run == 2)
+      apply_chunk<T, EPI, REALC, NR, 2, NV>(sp, scoef, base, end, D, nrhs, refine, fft_unit, src, dst, F, vt);
+    else
+      apply_chunk<T, EPI, REALC, NR, 1, NV>(sp, scoef, base, end, D, nrhs, refine, fft_unit, src, dst, F, vt);
     if (EPI == EPI_NONE) continue;
     block_reduce_mixed<T, NV>(vt, v);
     if (!chunk_arrive<NV>(b, c, u, v)) continue;
@@ -152,48 +163,40 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 3) k_apply(BatchDe
   }
 }
 
-template <typename T, int EPI, int NR, int RUN>
+template <typename T, int EPI, int NR>
 static void apply_launch_nr(bool realc, const BatchDev& b, int level, int refine, unsigned long long cond, int nblk,
                             size_t smem, cudaStream_t s) {
-  if (realc) k_apply<T, EPI, true, NR, RUN><<<nblk, BLOCK, smem, s>>>(b, level, refine, cond);
-  else k_apply<T, EPI, false, NR, RUN><<<nblk, BLOCK, smem, s>>>(b, level, refine, cond);
+  if (realc) k_apply<T, EPI, true, NR><<<nblk, BLOCK, smem, s>>>(b, level, refine, cond);
+  else k_apply<T, EPI, false, NR><<<nblk, BLOCK, smem, s>>>(b, level, refine, cond);
 }
 
-template <typename T, int EPI, int RUN>
+template <typename T, int EPI>
 static void apply_launch_real(bool realc, int maxr, const BatchDev& b, int level, int refine,
                               unsigned long long cond, int nblk, size_t smem, cudaStream_t s) {
   switch (maxr) {
-    case 1: apply_launch_nr<T, EPI, 1, RUN>(realc, b, level, refine, cond, nblk, smem, s); break;
-    case 2: apply_launch_nr<T, EPI, 2, RUN>(realc, b, level, refine, cond, nblk, smem, s); break;
-    case 3: apply_launch_nr<T, EPI, 3, RUN>(realc, b, level, refine, cond, nblk, smem, s); break;
-    default: apply_launch_nr<T, EPI, 4, RUN>(realc, b, level, refine, cond, nblk, smem, s); break;
-  }
-}
-
-template <int RUN>
-static void apply_launch_run(const BatchDev& b, bool realc, int mc, int maxr, int level, int epi, int refine,
-                             unsigned long long cond, int nblk, cudaStream_t s) {
-  if (level == LEVEL_FP32) {
-    const size_t smem = (size_t)mc * sizeof(float2);
-    apply_launch_real<float, EPI_DOT_HW, RUN>(realc, maxr, b, level, refine, cond, nblk, smem, s);
-  } else {
-    const size_t smem = (size_t)mc * sizeof(double2);
-    if (epi == EPI_DOT_HW)
-      apply_launch_real<double, EPI_DOT_HW, RUN>(realc, maxr, b, level, refine, cond, nblk, smem, s);
-    else if (epi == EPI_RESIDUAL)
-      apply_launch_real<double, EPI_RESIDUAL, RUN>(realc, maxr, b, level, refine, cond, nblk, smem, s);
-    else apply_launch_real<double, EPI_NONE, RUN>(realc, maxr, b, level, refine, cond, nblk, smem, s);
+    case 1: apply_launch_nr<T, EPI, 1>(realc, b, level, refine, cond, nblk, smem, s); break;
+    case 2: apply_launch_nr<T, EPI, 2>(realc, b, level, refine, cond, nblk, smem, s); break;
+    case 3: apply_launch_nr<T, EPI, 3>(realc, b, level, refine, cond, nblk, smem, s); break;
+    default: apply_launch_nr<T, EPI, 4>(realc, b, level, refine, cond, nblk, smem, s); break;
   }
 }
 
 // realc: every taps plan of the batch has real tap values; mc: the largest ntaps * ncomp of its plans (sizes
-// the shared coefficient table); maxr: the largest nrhs of its units; run: modes per thread step (2 when the
-// last axis of every unit has even length, else 1); refine: REFINE_* (the refinement bookkeeping of the residual
-// epilogue; REFINE_ZERO_U: the solutions are zero, so Q U = 0 is not computed).
+// the shared coefficient table); maxr: the largest nrhs of its units; refine: REFINE_* (the refinement
+// bookkeeping of the residual epilogue; REFINE_ZERO_U: the solutions are zero, so Q U = 0 is not computed).
+// Each unit's stencil runs (UnitDev.run) are its own.
 void launch_apply(const BatchDev& b, bool realc, int mc, int maxr, int level, int epi, int refine,
-                  unsigned long long cond, int nblk, int run, cudaStream_t s) {
-  if (run == 2) apply_launch_run<2>(b, realc, mc, maxr, level, epi, refine, cond, nblk, s);
-  else apply_launch_run<1>(b, realc, mc, maxr, level, epi, refine, cond, nblk, s);
+                  unsigned long long cond, int nblk, cudaStream_t s) {
+  if (level == LEVEL_FP32) {
+    const size_t smem = (size_t)mc * sizeof(float2);
+    apply_launch_real<float, EPI_DOT_HW>(realc, maxr, b, level, refine, cond, nblk, smem, s);
+  } else {
+    const size_t smem = (size_t)mc * sizeof(double2);
+    if (epi == EPI_DOT_HW) apply_launch_real<double, EPI_DOT_HW>(realc, maxr, b, level, refine, cond, nblk, smem, s);
+    else if (epi == EPI_RESIDUAL)
+      apply_launch_real<double, EPI_RESIDUAL>(realc, maxr, b, level, refine, cond, nblk, smem, s);
+    else apply_launch_real<double, EPI_NONE>(realc, maxr, b, level, refine, cond, nblk, smem, s);
+  }
   count_launch();
 }
 

@@ -22,6 +22,7 @@ def _mixed_instances():
     picks = [c3[0], c3[9], c3[33], c3[45]]          # d=1 N=64, d=1 N=128, d=2 N=8, d=2 N=16
     picks.append(W.random_instance(2, 3, (8, 6, 10), "sym", "taps", seed=41))
     picks.append(W.random_instance(3, 4, (6, 4, 6, 4), "diag", "taps", seed=42))
+    picks.append(W.random_instance(1, 3, (8, 6, 9), "scalar", "taps", seed=43))   # odd last axis: runs of 1
     return picks
 
 

@@ -27,13 +27,15 @@ def _rand_vecs(nrhs, N, seed):
 
 # (d, n, N, kind, nrhs, nmodes): scalar/diagonal/matrix coefficients, 1..4 right-hand sides, a single chunk
 # (D = 64) up to many chunks per block
+# (the persistent form needs a last axis of even length; (8, 9) checks that it then falls back to the graph)
 CASES = [
     (1, 2, (8, 8), "scalar", 1, None),
-    (2, 3, (10, 8, 6), "sym", 2, None),
-    (2, 4, (6, 6, 6, 6), "diag", 3, None),
+    (2, 3, (10, 6, 8), "sym", 2, None),
+    (2, 4, (6, 6, 6, 4), "diag", 3, None),
     (3, 3, (12, 10, 8), "sym", 4, None),
     (1, 3, (64, 48, 40), "scalar", 2, None),
-    (3, 6, (6, 6, 6, 6, 6, 6), "diag", 3, 24),
+    (3, 6, (6, 6, 6, 6, 6, 4), "diag", 3, 24),
+    (1, 2, (8, 9), "scalar", 2, None),
 ]
 
 
@@ -68,7 +70,7 @@ def test_persistent_equals_graph_and_direct_bitwise(qp, d, n, N, kind, nrhs, nmo
 
 @pytest.mark.parametrize("mode", ["fp64", "refine"])
 def test_persistent_warm_start_and_zero_rhs(qp, mode):
-    inst = W.random_instance(2, 3, (10, 8, 6), "diag", "taps", seed=7)
+    inst = W.random_instance(2, 3, (10, 6, 8), "diag", "taps", seed=7)
     m = qp.QP_MODE_FP64 if mode == "fp64" else qp.QP_MODE_FP32_REFINE
     F = _rand_vecs(3, inst.N, 11)
     F[1] = 0                                   # a zero right-hand side among others: U = 0, no iterations
