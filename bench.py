@@ -73,6 +73,120 @@ def apply_flops_per_dof(kind, d, ntaps, real, nrhs):
     return ntaps * (w + nrhs * (4 if real else 8))
 
 
+def update_flops_per_dof():
+    """Flops of one PCG vector update per mode and right-hand side (Algorithm 2): U += alpha h, r -= alpha Q h
+    (8), (r, M r) and |r|^2 (5), h = M r + beta h (6), rounded up to 20 with alpha/beta bookkeeping."""
+    return 20
+
+
+def fft_apply_bytes(d, ncomp, nrhs, D, es):
+    """Algorithmic bytes of the FFT-backend apply on the three-pass schedule: per right-hand side read h and
+    write w (2 es) and the d gradient fields written, read + written, read (4 d es) per mode; the coefficient
+    samples (ncomp reals of es / 2 bytes) once."""
+    return nrhs * D * es * (2 + 4 * d) + ncomp * D * (es // 2)
+
+
+# Per-launch DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the kernels below, from one ncu capture
+# of the current kernel each (summaries and commands under profiles/); None where no capture of the current kernel
+# exists.
+TRAFFIC = {
+    # cfg1: one solve (33 iterations, 2 correctors) in k_pcg_persistent; vectors stay in L2
+    ("k_pcg_persistent", "cfg1"): 4966400 + 452096,
+    # cfg4: captured at N = 14 (7.53 M modes; h and w exceed L2), scaled by 16^6 / 14^6 to the full launch
+    ("k_apply_plain", "cfg4"): int((207264512 + 150830592) * (16 ** 6 / 14 ** 6)),
+    # cfg2: the three fused passes of one FP32 apply (the gradient fields stay in L2 between passes)
+    ("k_fft_group", "cfg2"): 16874752 + 9472 + 46255616 + 0 + 33646848 + 0,
+}
+
+
+def measured_traffic(kernel_key, workload):
+    return TRAFFIC.get((kernel_key, workload))
+
+
+def persistent_roofline(qp, plan, inst, pinfo, real, tol, stream, dev):
+    """The persistent FP64 solve kernel (one launch per qp_pcg_solve when the automatic execution picks it):
+    algorithmic flops of its applies and vector updates per launch / its event-timed duration. Returns None
+    when this plan's solve is not a single persistent launch."""
+    import torch
+    nrhs = inst.d
+    F = torch.zeros((nrhs, inst.D), dtype=torch.complex128, device=dev)
+    qp.qp_corrector_rhs(plan, 0, nrhs, F)
+    U = torch.zeros_like(F)
+    torch.cuda.synchronize()
+    l0 = qp.qp_launch_count()
+    infos = qp.qp_pcg_solve(plan, F, U, tol=tol, maxit=2000)
+    if qp.qp_launch_count() - l0 != 1:
+        return None
+    reps = 20
+    ms = 0.0
+    for _ in range(reps):
+        U.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        infos = qp.qp_pcg_solve(plan, F, U, tol=tol, maxit=2000)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+    ms /= reps
+    its = [i["iterations"] for i in infos]
+    c = inst.coeff
+    # every iteration applies Q to all right-hand sides; plus the warm-start apply and the final true residual
+    applies = max(its) + 2
+    flops = (applies * apply_flops_per_dof(c.kind, inst.d, pinfo["ntaps"], real, nrhs) * inst.D
+             + sum(its) * update_flops_per_dof() * inst.D)
+    achieved = flops / (ms / 1e3) / 1e12
+    return {"bound": "alu", "achieved": round(achieved, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": None,
+            "kernel": "k_pcg_persistent (whole FP64 PCG solve in one cooperative launch), timed alone on the bench "
+                      "stream (the events also bracket two 4-byte memsets and the solver-state read-back)",
+            "kernel_key": "k_pcg_persistent", "launch_us": round(ms * 1e3, 2), "flops_per_launch": flops,
+            "iterations": its, "peak_source": "nominal FP64 1.25 TFLOP/s (FMA-loop probe on GB300: 1.196)"}
+
+
+def apply_roofline(qp, plan, inst, pinfo, real, mode_name, stream, dev):
+    """The stiffness apply in the precision of the workload's bulk iterations, timed alone."""
+    import torch
+    nrhs = inst.d
+    prec = qp.QP_FP64 if mode_name == "fp64" else qp.QP_FP32
+    dt = torch.complex128 if prec == qp.QP_FP64 else torch.complex64
+    es = 16 if prec == qp.QP_FP64 else 8
+    h = torch.randn((nrhs, inst.D), dtype=dt, device=dev)
+    w = torch.empty_like(h)
+    for _ in range(5):
+        qp.qp_apply_stiffness(plan, h, w, prec)
+    reps = 50
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        qp.qp_apply_stiffness(plan, h, w, prec)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    apply_ms = e0.elapsed_time(e1) / reps
+    c = inst.coeff
+    pk = peaks()
+    if prec == qp.QP_FP64 and c.taps_k is not None:
+        flops = apply_flops_per_dof(c.kind, inst.d, pinfo["ntaps"], real, nrhs) * inst.D
+        achieved = flops / (apply_ms / 1e3) / 1e12
+        return {"bound": "alu", "achieved": round(achieved, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": None,
+                "kernel": "k_apply_plain<double> (taps stencil, FP64 pipe), timed alone on the bench stream",
+                "kernel_key": "k_apply_plain<double>", "apply_us": round(apply_ms * 1e3, 2), "flops_per_launch": flops,
+                "peak_source": "nominal FP64 1.25 TFLOP/s (FMA-loop probe on GB300: 1.196)"}
+    if c.taps_k is not None:
+        bytes_ = 2 * nrhs * inst.D * es
+        kernel, key = "k_apply_plain (taps stencil; read h, write w), timed alone", "k_apply_plain"
+    else:
+        from qp_workloads import ncomp
+        bytes_ = fft_apply_bytes(inst.d, ncomp(c.kind, inst.d), nrhs, inst.D, es)
+        kernel, key = ("FFT-backend apply (fused group passes), timed alone; bytes of the three-pass schedule",
+                       "k_fft_group")
+    achieved = bytes_ / (apply_ms / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": round(achieved / pk["hbm_gbs"], 4), "traffic": None, "kernel": kernel, "kernel_key": key,
+            "apply_us": round(apply_ms * 1e3, 2), "bytes_per_launch": bytes_,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs" + (" (fallback)" if pk.get("_fallback") else "")}
+
+
 # ---------------------------------------------------------------------------------------------- clocks
 
 class ClockSampler:
@@ -204,40 +318,15 @@ def run_ours(args, rank, world, local_rank):
         t_sec = float(t.item())
     value = world * total_dof_iters / t_sec
 
-    # ---- roofline of the dominant kernel: the stiffness apply, timed alone with CUDA events on this stream
-    nrhs = inst.d
-    prec = qp.QP_FP64 if mode_name == "fp64" else qp.QP_FP32
-    dt = torch.complex128 if prec == qp.QP_FP64 else torch.complex64
-    h = torch.randn((nrhs, inst.D), dtype=dt, device=dev)
-    w = torch.empty_like(h)
-    for _ in range(5):
-        qp.qp_apply_stiffness(plan, h, w, prec)
-    reps = 50
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(reps):
-        qp.qp_apply_stiffness(plan, h, w, prec)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    apply_ms = e0.elapsed_time(e1) / reps
+    # ---- roofline of the dominant kernel, timed with CUDA events on this stream
     c = inst.coeff
     real = bool(np.all(np.asarray(c.taps_val).imag == 0)) if c.taps_k is not None else False
-    pk = peaks()
-    if prec == qp.QP_FP64 and c.taps_k is not None:
-        flops = apply_flops_per_dof(c.kind, inst.d, pinfo["ntaps"], real, nrhs) * inst.D
-        achieved = flops / (apply_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": None,
-                "kernel": "k_apply_plain<double> (taps stencil, FP64 pipe), timed alone on the bench stream", "apply_us": round(apply_ms * 1e3, 2),
-                "flops_per_launch": flops, "peak_source": "nominal FP64 1.25 TFLOP/s (FMA probe: 1.196)"}
-    else:
-        bytes_ = 2 * nrhs * inst.D * (16 if prec == qp.QP_FP64 else 8)
-        achieved = bytes_ / (apply_ms / 1e3) / 1e9
-        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": round(achieved / pk["hbm_gbs"], 4), "traffic": None,
-                "kernel": ("k_apply_plain<float> (taps stencil), timed alone" if c.taps_k is not None else "FFT-backend apply (all passes), timed alone"),
-                "apply_us": round(apply_ms * 1e3, 2), "bytes_per_launch": bytes_,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs" + (" (fallback)" if pk.get("_fallback") else "")}
+    roof = None
+    if mode_name == "fp64" and c.taps_k is not None and name != "cfg3":
+        roof = persistent_roofline(qp, plan, inst, pinfo, real, tol, stream, dev)
+    if roof is None:
+        roof = apply_roofline(qp, plan, inst, pinfo, real, mode_name, stream, dev)
+    roof["traffic"] = measured_traffic(roof["kernel_key"], name)
 
     # ---- end to end through the public API with host inputs: plan from host taps -> a* on the host
     e2e = None
@@ -383,6 +472,25 @@ def run_apply_only(args):
                       "launches": args.warmup + args.steps}))
 
 
+def run_solve_only(args):
+    """Launches qp_pcg_solve on the workload's corrector right-hand sides --warmup + --steps times (from U = 0);
+    used to capture the solve kernels (the persistent one where it applies) under a profiler."""
+    import torch
+    import paper_2404_06841_gb300 as qp
+    inst = instance(args.workload, args.N)
+    mode = qp.QP_MODE_FP64 if (args.mode or WORKLOADS[args.workload][1]) == "fp64" else qp.QP_MODE_FP32_REFINE
+    plan = qp.plan_from_instance(inst)
+    F = torch.zeros((inst.d, inst.D), dtype=torch.complex128, device="cuda")
+    qp.qp_corrector_rhs(plan, 0, inst.d, F)
+    U = torch.zeros_like(F)
+    for _ in range(args.warmup + args.steps):
+        U.zero_()
+        infos = qp.qp_pcg_solve(plan, F, U, tol=inst.tol, maxit=2000, mode=mode)
+    torch.cuda.synchronize()
+    print(json.dumps({"solve_only": args.workload, "D": inst.D, "launches": args.warmup + args.steps,
+                      "iterations": [i["iterations"] for i in infos]}))
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -396,6 +504,8 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--apply-only", action="store_true",
                     help="profiling aid: build the plan and launch only the stiffness apply --steps times")
+    ap.add_argument("--solve-only", action="store_true",
+                    help="profiling aid: launch only qp_pcg_solve on the corrector right-hand sides --steps times")
     ap.add_argument("--N", type=int, default=None, help="modes per axis (overrides the workload's N)")
     ap.add_argument("--precision", default=None, choices=["fp64", "fp32"], help="with --apply-only")
     ap.add_argument("--exec", default="auto", choices=["auto", "persistent", "graph", "direct"],
@@ -413,6 +523,9 @@ def main():
         return
     if args.apply_only:
         run_apply_only(args)
+        return
+    if args.solve_only:
+        run_solve_only(args)
         return
     if world > 1:
         import torch

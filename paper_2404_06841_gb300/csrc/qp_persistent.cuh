@@ -32,23 +32,34 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
+__device__ __forceinline__ unsigned atom_add_release(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 // Grid-wide barrier with a bounded wait; false (in every thread of the block) on timeout or error.
+// bar[0] counts arrivals over the whole launch: the k-th barrier is passed once it reaches (k + 1) * gridDim.x.
+// Each block's thread 0 arrives with one release-ordered atomic add (after the block barrier, so it publishes
+// the block's writes) and polls with acquire loads; no separate fences and no reset step. A single-block grid
+// needs only the block barrier.
 __device__ __noinline__ bool grid_barrier(unsigned* bar, int* err, unsigned long long timeout_ns) {
   __shared__ int s_ok;
   __syncthreads();
+  if (gridDim.x == 1) return true;
   if (threadIdx.x == 0) {
-    volatile unsigned* gen = bar + 1;
-    const unsigned g0 = *gen;
-    __threadfence();
-    const unsigned prev = atomicAdd(bar, 1u);
+    const unsigned ticket = atom_add_release(bar, 1u);
+    const unsigned target = (ticket / gridDim.x + 1u) * gridDim.x;
     int ok = 1;
-    if (prev == gridDim.x - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
+    if ((int)(ld_acquire(bar) - target) < 0) {
       const unsigned long long t0 = global_ns();
-      while (*gen == g0) {
+      for (;;) {
+        if ((int)(ld_acquire(bar) - target) >= 0) break;
         if (*((volatile int*)err)) {
           ok = 0;
           break;
@@ -58,10 +69,8 @@ __device__ __noinline__ bool grid_barrier(unsigned* bar, int* err, unsigned long
           ok = 0;
           break;
         }
-        __nanosleep(64);
       }
     }
-    __threadfence();
     s_ok = ok && !*((volatile int*)err);
   }
   __syncthreads();
