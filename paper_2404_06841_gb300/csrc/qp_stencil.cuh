@@ -15,6 +15,19 @@ template <bool RO, typename V> __device__ __forceinline__ V ldh(const V* p) {
   return *p;
 }
 
+// RUN consecutive complex values from p (p aligned to RUN elements): one 16-byte load for two FP32 values.
+template <bool RO, typename T, int RUN>
+__device__ __forceinline__ void ld_run(const cplx<T>* p, cplx<T> (&v)[RUN]) {
+  if (sizeof(T) == 4 && RUN == 2) {
+    const float4 q = RO ? __ldg(reinterpret_cast<const float4*>(p)) : *reinterpret_cast<const float4*>(p);
+    v[0] = mk<T>((T)q.x, (T)q.y);
+    v[RUN - 1] = mk<T>((T)q.z, (T)q.w);
+  } else {
+#pragma unroll
+    for (int s = 0; s < RUN; ++s) v[s] = ldh<RO>(p + s);
+  }
+}
+
 
 template <typename T>
 __device__ __forceinline__ void load_plan(const PlanDev* src, PlanDev& dst, cplx<T>* coef) {
@@ -59,6 +72,9 @@ __device__ __forceinline__ void apply_run(const PlanDev& p, const cplx<T>* __res
   const int jl = n - 1, Nl = p.N[jl];
   const int ibl = e0 - (int)fdiv((uint32_t)e0, p.div[jl]) * Nl;   // digit of the last axis (kept in registers)
   const bool scalar = (kind == QP_COEF_SCALAR);
+  const cplx<T>* hr[NR];   // each right-hand side's vector
+#pragma unroll
+  for (int r = 0; r < NR; ++r) hr[r] = h + (size_t)r * D;
   // lambda per mode of the run
   T lk[RUN][MAXD];
   int kl[RUN];
@@ -95,18 +111,24 @@ __device__ __forceinline__ void apply_run(const PlanDev& p, const cplx<T>* __res
 
   // mean tap (sorted index 0): k' = k
   {
+    cplx<T> c[RUN];
 #pragma unroll
     for (int s = 0; s < RUN; ++s) {
-      cplx<T> c;
       if (scalar) {
-        c.x = sc[0].x * lam2[s];
-        c.y = REALC ? T(0) : sc[0].y * lam2[s];
+        c[s].x = sc[0].x * lam2[s];
+        c[s].y = REALC ? T(0) : sc[0].y * lam2[s];
       } else {
-        c = weight_general<T>(kind, d, sc, lk[s], lk[s]);
+        c[s] = weight_general<T>(kind, d, sc, lk[s], lk[s]);
       }
+    }
 #pragma unroll
-      for (int r = 0; r < NR; ++r)
-        if (r < nrhs) mac<T, REALC>(acc[s][r], c, ldh<RO>(h + (size_t)r * D + e0 + s));
+    for (int r = 0; r < NR; ++r) {
+      if (r < nrhs) {
+        cplx<T> hv[RUN];
+        ld_run<RO, T, RUN>(hr[r] + e0, hv);
+#pragma unroll
+        for (int s = 0; s < RUN; ++s) mac<T, REALC>(acc[s][r], c[s], hv[s]);
+      }
     }
   }
   // star taps of the axes before the last: one offset per run, RUN consecutive reads per tap
@@ -133,22 +155,28 @@ __device__ __forceinline__ void apply_run(const PlanDev& p, const cplx<T>* __res
         const int k2 = (2 * ib2 < Nj) ? ib2 : ib2 - Nj;
         const T dk = (T)(k2 - k[j]);
         const cplx<T>* ct = sc + t * nc;
+        cplx<T> c[RUN];
 #pragma unroll
         for (int s = 0; s < RUN; ++s) {
-          cplx<T> c;
           if (scalar) {
             const T w = fma(dk, lp[s], lam2[s]);
-            c.x = ct[0].x * w;
-            c.y = REALC ? T(0) : ct[0].y * w;
+            c[s].x = ct[0].x * w;
+            c[s].y = REALC ? T(0) : ct[0].y * w;
           } else {
             T l2[MAXD];
 #pragma unroll
             for (int a = 0; a < MAXD; ++a) l2[a] = (a < d) ? fma(dk, pj[a], lk[s][a]) : T(0);
-            c = weight_general<T>(kind, d, ct, lk[s], l2);
+            c[s] = weight_general<T>(kind, d, ct, lk[s], l2);
           }
+        }
 #pragma unroll
-          for (int r = 0; r < NR; ++r)
-            if (r < nrhs) mac<T, REALC>(acc[s][r], c, ldh<RO>(h + (size_t)r * D + e2 + s));
+        for (int r = 0; r < NR; ++r) {
+          if (r < nrhs) {
+            cplx<T> hv[RUN];
+            ld_run<RO, T, RUN>(hr[r] + e2, hv);
+#pragma unroll
+            for (int s = 0; s < RUN; ++s) mac<T, REALC>(acc[s][r], c[s], hv[s]);
+          }
         }
       }
     }
@@ -190,7 +218,7 @@ __device__ __forceinline__ void apply_run(const PlanDev& p, const cplx<T>* __res
         }
 #pragma unroll
         for (int r = 0; r < NR; ++r)
-          if (r < nrhs) mac<T, REALC>(acc[s][r], c, ldh<RO>(h + (size_t)r * D + row0 + ib2));
+          if (r < nrhs) mac<T, REALC>(acc[s][r], c, ldh<RO>(hr[r] + row0 + ib2));
       }
     }
   }
@@ -231,7 +259,7 @@ __device__ __forceinline__ void apply_run(const PlanDev& p, const cplx<T>* __res
       const cplx<T> c = weight_general<T>(kind, d, ct, lk[s], l2);
 #pragma unroll
       for (int r = 0; r < NR; ++r)
-        if (r < nrhs) mac<T, REALC>(acc[s][r], c, ldh<RO>(h + (size_t)r * D + eo + ib2));
+        if (r < nrhs) mac<T, REALC>(acc[s][r], c, ldh<RO>(hr[r] + eo + ib2));
     }
   }
 }
