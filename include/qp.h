@@ -183,6 +183,14 @@ qp_status qp_pcg_solve_taps_static(int d, int n, const double* P, const int* N, 
                                    const void* F, void* U, const qp_solve_opts* opts, qp_solve_info* info,
                                    void* stream);
 
+/* Error of a computed solution in the L^2_QP norm (Sec. 5.1, e_N = ||u_N - u||): by the Parseval identity of that
+ * norm (Sec. 2.2, eq. parseval) it is the l^2 norm of the Fourier coefficients, out[r] = ||U_r - Uref_r||_2 over
+ * K_N^n. U, Uref: device complex128, nrhs x D (1 <= nrhs <= QP_MAX_RHS; Uref NULL gives ||U_r||). out: host
+ * double[nrhs]. When Uref holds the exact solution's coefficients on K_N^n, modes of the exact solution outside
+ * K_N^n (truncation) add the sum of their |coefficient|^2 to out[r]^2; the caller adds that part. Deterministic
+ * FP64 reduction; synchronises stream. */
+qp_status qp_l2qp_error(qp_plan* plan, int nrhs, const void* U, const void* Uref, double* out, void* stream);
+
 /* Description of the last error on this host thread ("" if none). The string stays valid until the next call. */
 const char* qp_last_error(void);
 

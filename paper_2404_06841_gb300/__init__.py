@@ -34,7 +34,7 @@ KIND_CODES = {"scalar": QP_COEF_SCALAR, "diag": QP_COEF_DIAG, "sym": QP_COEF_SYM
 EXPORTS = ("qp_plan_create", "qp_plan_destroy", "qp_plan_query", "qp_apply_stiffness", "qp_corrector_rhs",
            "qp_pcg_solve", "qp_homogenized_reduce", "qp_homogenized", "qp_fft", "qp_batch_create",
            "qp_batch_homogenized", "qp_batch_destroy", "qp_last_error", "qp_launch_count",
-           "qp_pcg_solve_taps_static", "qp_set_barrier_timeout")
+           "qp_pcg_solve_taps_static", "qp_set_barrier_timeout", "qp_l2qp_error")
 
 
 class qp_coeff(C.Structure):
@@ -93,6 +93,7 @@ def load_library(path: str = LIB_PATH):
         "qp_pcg_solve_taps_static": [i, i, dp, ip, C.POINTER(qp_coeff), i, vp, vp, C.POINTER(qp_solve_opts),
                                      C.POINTER(qp_solve_info), vp],
         "qp_set_barrier_timeout": [C.c_double],
+        "qp_l2qp_error": [vp, i, vp, vp, dp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -334,6 +335,18 @@ def qp_last_error() -> str:
 
 def qp_launch_count() -> int:
     return int(_lib.qp_launch_count())
+
+
+def qp_l2qp_error(plan: Plan, U, Uref=None, stream=None) -> np.ndarray:
+    """e_r = ||U_r - Uref_r|| in the L^2_QP norm (the l^2 norm of the Fourier coefficients, Parseval), per
+    right-hand side. U, Uref: contiguous device complex128 tensors holding nrhs x D entries."""
+    nrhs = U.numel() // plan.D
+    if nrhs * plan.D != U.numel() or (Uref is not None and Uref.numel() != U.numel()):
+        raise QPError(QP_ERR_INVALID_ARG, "U and Uref must hold nrhs x D entries each")
+    out = np.zeros(nrhs, dtype=np.float64)
+    _check(_lib.qp_l2qp_error(plan.handle, int(nrhs), _ptr(U), _ptr(Uref),
+                              out.ctypes.data_as(C.POINTER(C.c_double)), _stream(stream)))
+    return out
 
 
 def qp_set_barrier_timeout(seconds: float) -> None:

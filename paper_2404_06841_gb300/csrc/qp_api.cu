@@ -927,6 +927,19 @@ const char* qp_last_error(void) { return g_err.c_str(); }
 
 uint64_t qp_launch_count(void) { return qp::g_launches.load(std::memory_order_relaxed); }
 
+qp_status qp_l2qp_error(qp_plan* p, int nrhs, const void* U, const void* Uref, double* out, void* stream) {
+  API_BEGIN
+  if (!p || !U || !out) raise(QP_ERR_INVALID_ARG, "plan, U and out must be non-null");
+  if (nrhs < 1 || nrhs > MAXR) raise(QP_ERR_INVALID_ARG, "nrhs must be 1..QP_MAX_RHS");
+  cudaStream_t s = S(stream);
+  launch_l2_norms(p->D, nrhs, (const double2*)U, (const double2*)Uref, p->scratch, p->nblk, p->small, s);
+  CK_LAUNCH();
+  CK(cudaMemcpyAsync(p->h_small, p->small, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (int r = 0; r < nrhs; ++r) out[r] = p->h_small[r];
+  API_END
+}
+
 qp_status qp_set_barrier_timeout(double seconds) {
   API_BEGIN
   if (!(seconds > 0.0 && seconds <= 3600.0)) raise(QP_ERR_INVALID_ARG, "barrier timeout must be in (0, 3600] s");

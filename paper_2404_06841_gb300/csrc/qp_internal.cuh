@@ -162,6 +162,10 @@ void launch_pcg_update(const BatchDev& b, int maxr, int level, unsigned long lon
 void launch_pcg_hupdate(const BatchDev& b, int maxr, int level, int nblk, cudaStream_t s);
 void launch_refine_prep(const BatchDev& b, int nblk, cudaStream_t s);
 void launch_refine_accum(const BatchDev& b, int nblk, cudaStream_t s);
+// ||U_r - Uref_r||_2 over the Fourier coefficients (qp_norms.cu)
+void launch_l2_norms(int D, int nrhs, const double2* U, const double2* Uref, double* part, int nblk, double* out,
+                     cudaStream_t s);
+
 // persistent solve of one taps unit (qp_persistent.cu): the kernel's argument
 struct PersistArgs {
   BatchDev b;          // b.single: one unit in b.pu, its state in b.st[0 .. MAXR)

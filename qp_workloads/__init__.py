@@ -278,6 +278,26 @@ def cfg4(N: int = 16, seed: int = 4) -> Instance:
                     tol=1e-10, meta={"seed": seed, "phi": phi})
 
 
+def paper_elliptic_u1(N: int = 128) -> Instance:
+    """The first elliptic example of Sec. 5.1.1 (Table 2): alpha_1(x) = cos(2 pi x) + cos(2 pi sqrt2 x) + 6, lifted
+    with P = 2 pi (1, sqrt2) to 6 + cos th1 + cos th2, and the exact solution u_1(x) = sin(2 pi x) + sin(2 pi sqrt2 x),
+    lifted to sin th1 + sin th2, whose Fourier coefficients are -i/2 at (1, 0), (0, 1) and +i/2 at (-1, 0), (0, -1).
+    meta["u_modes"], meta["u_amps"]: those modes and coefficients."""
+    k, v = cos_sum_taps(2, 6.0, 1.0)
+    modes = np.array([(1, 0), (-1, 0), (0, 1), (0, -1)], dtype=np.int64)
+    amps = np.array([-0.5j, 0.5j, -0.5j, 0.5j])
+    return Instance("tab2_alpha1_u1_N%d" % N, 2.0 * math.pi * np.array([[1.0, SQRT2]]), (N, N),
+                    Coefficient("scalar", k, v), tol=1e-14, meta={"u_modes": modes, "u_amps": amps})
+
+
+def modes_on_grid(N, modes, amps) -> np.ndarray:
+    """Dense array on K_N^n (storage index k mod N_j) holding the given Fourier coefficients."""
+    out = np.zeros(tuple(N), dtype=np.complex128)
+    for m, a in zip(modes, amps):
+        out[tuple(int(x) % int(Nj) for x, Nj in zip(m, N))] += a
+    return out
+
+
 # --------------------------------------------------------------------------------------------- test inputs
 
 def random_P(d: int, n: int, seed: int) -> np.ndarray:
