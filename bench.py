@@ -434,6 +434,24 @@ def run_ours(args, rank, world, local_rank):
                            "iterations": [(i["iterations"], i["outer_iterations"]) for i in inf2],
                            "max_abs_astar_diff_vs_main": float(np.abs(A2 - A).max())}
 
+    # ---- the paper's Frobenius-optimal diagonal (Sec. 4.3) against Jacobi on the same solve (iterations, time)
+    if not args.no_variants and name not in ("cfg3", "tab2"):
+        P_F = qp.QP_PRECOND_FROBENIUS
+        qp.qp_homogenized(plan, tol=tol, mode=mode, maxit=4000, precond=P_F)        # builds the diagonal once
+        ts = []
+        for _ in range(max(3, min(args.steps, 10))):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            A3, inf3 = qp.qp_homogenized(plan, tol=tol, mode=mode, maxit=4000, precond=P_F)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        variants["frobenius"] = {"time_to_astar_ms": round(statistics.median(ts), 4),
+                                 "iterations": [(i["iterations"], i["outer_iterations"]) for i in inf3],
+                                 "jacobi_iterations": [(i["iterations"], i["outer_iterations"]) for i in infos],
+                                 "max_abs_astar_diff_vs_main": float(np.abs(A3 - A).max())}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(name, max_seconds=args.cpu_seconds)

@@ -92,7 +92,8 @@ typedef struct {
 typedef struct {
   double tol;         /* stop when ||F - Q U||_2 <= tol ||F||_2 (Fourier coefficients; Parseval) */
   int maxit;          /* PCG iteration cap (all inner iterations in refinement mode) */
-  int precond;        /* QP_PRECOND_JACOBI (diagonal of Q) or QP_PRECOND_FROBENIUS (eq. preconditioner) */
+  int precond;        /* QP_PRECOND_JACOBI (diagonal of Q) or QP_PRECOND_FROBENIUS (eq. preconditioner; on the FFT
+                         backend built on first use, see qp_plan_diagonal) */
   int mode;           /* QP_MODE_FP64: FP64 vectors and operator; QP_MODE_FP32_REFINE: FP32 inner PCG in an
                          FP64 iterative-refinement loop (FP64 true residual, FP64 dot products) */
   double inner_tol;   /* refinement: relative tolerance of each inner FP32 solve (0 = 1e-5) */
@@ -182,6 +183,14 @@ qp_status qp_batch_destroy(qp_batch* batch);
 qp_status qp_pcg_solve_taps_static(int d, int n, const double* P, const int* N, const qp_coeff* coeff, int nrhs,
                                    const void* F, void* U, const qp_solve_opts* opts, qp_solve_info* info,
                                    void* stream);
+
+/* The diagonal preconditioner of a solve, z = M r (Sec. 4.3): QP_PRECOND_JACOBI gives M(k) = 1/q(k), q the diagonal
+ * of Q; QP_PRECOND_FROBENIUS gives the Frobenius-optimal M(k) = q(k)/||Q e_k||^2 (eq. preconditioner): on the taps
+ * backend from the O(gD) column sums, on the FFT backend from FFT cross-correlations of lambda_a lambda_a' with
+ * A~^{ab} conj(A~^{a'b'}) (d^4 + d(d+1) FP64 n-dim DFTs plus ~(5 + d(d+1)/2) x 16 B x D of temporary device memory,
+ * done once, on this call or the first Frobenius solve). M(0) = 0 (the excluded mode). out: device double[D].
+ * Synchronises stream. */
+qp_status qp_plan_diagonal(qp_plan* plan, int precond, double* out, void* stream);
 
 /* Error of a computed solution in the L^2_QP norm (Sec. 5.1, e_N = ||u_N - u||): by the Parseval identity of that
  * norm (Sec. 2.2, eq. parseval) it is the l^2 norm of the Fourier coefficients, out[r] = ||U_r - Uref_r||_2 over

@@ -34,7 +34,7 @@ KIND_CODES = {"scalar": QP_COEF_SCALAR, "diag": QP_COEF_DIAG, "sym": QP_COEF_SYM
 EXPORTS = ("qp_plan_create", "qp_plan_destroy", "qp_plan_query", "qp_apply_stiffness", "qp_corrector_rhs",
            "qp_pcg_solve", "qp_homogenized_reduce", "qp_homogenized", "qp_fft", "qp_batch_create",
            "qp_batch_homogenized", "qp_batch_destroy", "qp_last_error", "qp_launch_count",
-           "qp_pcg_solve_taps_static", "qp_set_barrier_timeout", "qp_l2qp_error")
+           "qp_pcg_solve_taps_static", "qp_set_barrier_timeout", "qp_l2qp_error", "qp_plan_diagonal")
 
 
 class qp_coeff(C.Structure):
@@ -94,6 +94,7 @@ def load_library(path: str = LIB_PATH):
                                      C.POINTER(qp_solve_info), vp],
         "qp_set_barrier_timeout": [C.c_double],
         "qp_l2qp_error": [vp, i, vp, vp, dp, vp],
+        "qp_plan_diagonal": [vp, i, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -335,6 +336,14 @@ def qp_last_error() -> str:
 
 def qp_launch_count() -> int:
     return int(_lib.qp_launch_count())
+
+
+def qp_plan_diagonal(plan: Plan, precond=QP_PRECOND_JACOBI, stream=None):
+    """The preconditioner diagonal M (z = M r) as a device float64 tensor of the plan's grid shape."""
+    import torch
+    out = torch.empty(plan.N, dtype=torch.float64, device="cuda")
+    _check(_lib.qp_plan_diagonal(plan.handle, int(precond), _ptr(out), _stream(stream)))
+    return out
 
 
 def qp_l2qp_error(plan: Plan, U, Uref=None, stream=None) -> np.ndarray:

@@ -70,6 +70,7 @@ struct qp_plan {
 
   double* jac64 = nullptr;
   double* frob64 = nullptr;
+  bool frob_ready = false;          // the Frobenius diagonal is built (taps: at creation; FFT: on first use)
   float* jac32 = nullptr;
   float* frob32 = nullptr;
 
@@ -859,8 +860,14 @@ void check_opts(const qp_solve_opts* o, const qp_plan* p) {
     raise(QP_ERR_INVALID_ARG, "plan was created without the FP64 solve workspace");
   if (p && o->mode == QP_MODE_FP32_REFINE && !(p->precisions & 2))
     raise(QP_ERR_INVALID_ARG, "plan was created without the FP32 solve workspace");
-  if (p && p->backend == QP_BACKEND_FFT && o->precond == QP_PRECOND_FROBENIUS)
-    raise(QP_ERR_UNSUPPORTED, "the Frobenius diagonal is built on the taps backend only");
+}
+
+// Builds the diagonal a solve is about to use if the plan does not hold it yet (the FFT backend's Frobenius
+// diagonal, on first request).
+void prepare_precond(qp_plan* p, int precond, cudaStream_t s) {
+  if (precond != QP_PRECOND_FROBENIUS || p->frob_ready) return;
+  fft_frobenius(p->fft, p->host_pd, p->pd, p->frob64, p->frob32, s);
+  p->frob_ready = true;
 }
 
 void corrector_rhs(qp_plan* p, int j0, int nrhs, double2* F, cudaStream_t s) {
@@ -927,6 +934,18 @@ const char* qp_last_error(void) { return g_err.c_str(); }
 
 uint64_t qp_launch_count(void) { return qp::g_launches.load(std::memory_order_relaxed); }
 
+qp_status qp_plan_diagonal(qp_plan* p, int precond, double* out, void* stream) {
+  API_BEGIN
+  if (!p || !out) raise(QP_ERR_INVALID_ARG, "plan and out must be non-null");
+  if (precond != QP_PRECOND_JACOBI && precond != QP_PRECOND_FROBENIUS) raise(QP_ERR_INVALID_ARG, "unknown preconditioner");
+  cudaStream_t s = S(stream);
+  prepare_precond(p, precond, s);
+  const double* src = precond == QP_PRECOND_FROBENIUS ? p->frob64 : p->jac64;
+  CK(cudaMemcpyAsync(out, src, (size_t)p->D * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  API_END
+}
+
 qp_status qp_l2qp_error(qp_plan* p, int nrhs, const void* U, const void* Uref, double* out, void* stream) {
   API_BEGIN
   if (!p || !U || !out) raise(QP_ERR_INVALID_ARG, "plan, U and out must be non-null");
@@ -988,6 +1007,7 @@ qp_status qp_plan_create(int d, int n, const double* P, const int* N, const qp_c
     launch_diag(p->pd, p->coef_count, p->D, p->jac64, p->frob64, p->jac32, p->frob32, p->scratch, p->counter,
                 p->small, p->nblk, s);
     CK_LAUNCH();
+    p->frob_ready = true;
   } else {
     CK(cudaMemcpy(p->pd, &p->host_pd, sizeof(PlanDev), cudaMemcpyHostToDevice));
     p->fft = fft_plan_create(p->host_pd, p->precisions, p->max_rhs);
@@ -1067,6 +1087,7 @@ qp_status qp_pcg_solve(qp_plan* p, int nrhs, const void* F, void* U, const qp_so
   if (nrhs < 1 || nrhs > p->max_rhs) raise(QP_ERR_INVALID_ARG, "nrhs must be 1..max_rhs");
   check_opts(opts, p);
   cudaStream_t s = S(stream);
+  prepare_precond(p, opts->precond, s);
   const size_t bytes = (size_t)nrhs * p->D * sizeof(double2);
   CK(cudaMemcpyAsync(p->v64.F, F, bytes, cudaMemcpyDeviceToDevice, s));
   CK(cudaMemcpyAsync(p->v64.X, U, bytes, cudaMemcpyDeviceToDevice, s));
@@ -1096,6 +1117,7 @@ qp_status qp_homogenized(qp_plan* p, const qp_solve_opts* opts, double* Are, dou
   check_opts(opts, p);
   if (p->max_rhs < p->d) raise(QP_ERR_INVALID_ARG, "qp_homogenized needs a plan with max_rhs >= d");
   cudaStream_t s = S(stream);
+  prepare_precond(p, opts->precond, s);
   corrector_rhs(p, 0, p->d, p->v64.F, s);
   if (!p->solver) p->solver = new Solver({p});
   Units us = single_units(p, p->d);
@@ -1152,6 +1174,7 @@ qp_status qp_batch_homogenized(qp_batch* b, const qp_solve_opts* opts, double* A
   if (!b || !Astar_all) raise(QP_ERR_INVALID_ARG, "batch and Astar_all must be non-null");
   for (qp_plan* p : b->plans) check_opts(opts, p);
   cudaStream_t s = S(stream);
+  for (qp_plan* p : b->plans) prepare_precond(p, opts->precond, s);
   Units us;
   us.plans = b->plans;
   for (qp_plan* p : b->plans) {

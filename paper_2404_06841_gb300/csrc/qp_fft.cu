@@ -10,6 +10,7 @@
 // decimation in time for N <= 32) or as N = N1 x N2 four-step through shared memory (N up to 1024), and writes
 // the tile back. Twiddles for N <= 32 come from a constant-memory table filled once per device from host
 // cos/sin; larger sizes call sincospi in the kernel.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -584,8 +585,8 @@ void fft_set_taps(FftPlan* f, const PlanDev& pd, const PlanDev* pdp, cudaStream_
   CK_LAUNCH();
 }
 
-// Jacobi diagonal q(k) = lambda(k)^T A~_0 lambda(k); the Frobenius diagonal is not built on this backend
-// (frob = 0 marks it). Reduces min |lambda|^2 and min q/|lambda|^2 over k != 0 and the smallest Cholesky pivot of
+// Jacobi diagonal q(k) = lambda(k)^T A~_0 lambda(k); the Frobenius diagonal is built on first use
+// (fft_frobenius; frob = 0 until then). Reduces min |lambda|^2 and min q/|lambda|^2 over k != 0 and the smallest Cholesky pivot of
 // A over the grid nodes into partials; k_diag_fft_final writes out[0..2].
 __global__ void __launch_bounds__(BLOCK) k_diag_fft(const PlanDev* pdp, const double2* ahat, const double* c64,
                                                     double* jac, double* frob, float* jac32, float* frob32,
@@ -661,6 +662,166 @@ void fft_diag(FftPlan* f, const PlanDev*, const PlanDev* pdp, double* jac, doubl
   k_diag_fft_final<<<1, BLOCK, 0, s>>>(f->part, f->nblk, out);
   count_launch(2);
   CK_LAUNCH();
+}
+
+// ---- Frobenius-optimal diagonal (Sec. 4.3, eq. preconditioner) on the FFT backend
+//
+// M(k) = q(k) / ||Q e_k||^2 with q(k) = lambda(k)^T A~_0 lambda(k). Column k of Q holds, at row k + m (mod N),
+// e_m(k) = sum_ab lambda_a(k + m) A~^{ab}_m lambda_b(k), so
+//   ||Q e_k||^2 = sum_{b,b'} lambda_b(k) lambda_b'(k) sum_{a,a'} sum_m G^{aa'}(k + m) H^{ab,a'b'}(m),
+//   G^{aa'} = lambda_a lambda_a',  H^{ab,a'b'}(m) = A~^{ab}_m conj(A~^{a'b'}_m),
+// and each inner sum over all D modes m is a circular cross-correlation on the mode grid: with
+// Hr(z) = H(-z), sum_m G(k + m) H(m) = (G * Hr)(k) = DFT^-1(DFT(G) DFT(Hr))(k) / D. With a dense coefficient
+// this costs d^4 + d(d+1) FP64 n-dim DFTs instead of the O(D^2) direct sum.
+
+__device__ __forceinline__ int coef_comp(int kind, int d, int a, int b) {
+  if (kind == QP_COEF_SCALAR) return a == b ? 0 : -1;
+  if (kind == QP_COEF_DIAG) return a == b ? a : -1;
+  return sym_idx(a, b, d);
+}
+
+// G(e) = lambda_a(e) lambda_a'(e)
+__global__ void __launch_bounds__(BLOCK) k_fro_g(const PlanDev* pdp, int a, int a2, double2* G) {
+  const PlanDev& p = *pdp;
+  for (int e = blockIdx.x * BLOCK + threadIdx.x; e < p.D; e += gridDim.x * BLOCK) {
+    double lk[MAXD];
+    int ib[MAXN];
+    lambda_of<double>(p, e, lk, ib);
+    G[e] = make_double2(lk[a] * lk[a2], 0.0);
+  }
+}
+
+// Hr(e) = A~^{c1}(-e) conj(A~^{c2}(-e)), -e the mode with every storage digit negated mod N_j
+__global__ void __launch_bounds__(BLOCK) k_fro_h(const PlanDev* pdp, const double2* ahat, int c1, int c2,
+                                                 double2* H) {
+  const PlanDev& p = *pdp;
+  const int D = p.D;
+  for (int e = blockIdx.x * BLOCK + threadIdx.x; e < D; e += gridDim.x * BLOCK) {
+    int ib[MAXN], k[MAXN];
+    mode_digits(p, e, ib, k);
+    int en = 0;
+    for (int j = 0; j < p.n; ++j) en += (ib[j] == 0 ? 0 : p.N[j] - ib[j]) * p.stride[j];
+    const double2 x = ahat[(size_t)c1 * D + en], y = ahat[(size_t)c2 * D + en];
+    H[e] = make_double2(x.x * y.x + x.y * y.y, x.y * y.x - x.x * y.y);
+  }
+}
+
+// X += A B (complex, elementwise)
+__global__ void __launch_bounds__(BLOCK) k_fro_macc(int D, const double2* A, const double2* B, double2* X) {
+  for (int e = blockIdx.x * BLOCK + threadIdx.x; e < D; e += gridDim.x * BLOCK) {
+    const double2 a = A[e], b = B[e];
+    double2 x = X[e];
+    x.x = fma(a.x, b.x, fma(-a.y, b.y, x.x));
+    x.y = fma(a.x, b.y, fma(a.y, b.x, x.y));
+    X[e] = x;
+  }
+}
+
+// cn(e) += lambda_b(e) lambda_b'(e) Re(X(e)) / D
+__global__ void __launch_bounds__(BLOCK) k_fro_cn(const PlanDev* pdp, int b, int b2, const double2* X, double* cn) {
+  const PlanDev& p = *pdp;
+  const double invD = 1.0 / (double)p.D;
+  for (int e = blockIdx.x * BLOCK + threadIdx.x; e < p.D; e += gridDim.x * BLOCK) {
+    double lk[MAXD];
+    int ib[MAXN];
+    lambda_of<double>(p, e, lk, ib);
+    cn[e] = fma(lk[b] * lk[b2], X[e].x * invD, cn[e]);
+  }
+}
+
+// M(k) = q(k) / ||Q e_k||^2 (0 at k = 0 and where the column vanishes), FP64 and FP32 copies
+__global__ void __launch_bounds__(BLOCK) k_fro_final(const PlanDev* pdp, const double2* ahat, const double* cn,
+                                                     double* frob, float* frob32) {
+  const PlanDev& p = *pdp;
+  const int D = p.D, d = p.d;
+  for (int e = blockIdx.x * BLOCK + threadIdx.x; e < D; e += gridDim.x * BLOCK) {
+    double lk[MAXD];
+    int ib[MAXN];
+    lambda_of<double>(p, e, lk, ib);
+    double q = 0.0;
+    for (int a = 0; a < d; ++a)
+      for (int b = 0; b < d; ++b) {
+        const int c = coef_comp(p.kind, d, a, b);
+        if (c >= 0) q += lk[a] * ahat[(size_t)c * D].x * lk[b];
+      }
+    const double m = (e != 0 && cn[e] > 0.0) ? q / cn[e] : 0.0;
+    frob[e] = m;
+    frob32[e] = (float)m;
+  }
+}
+
+void fft_frobenius(FftPlan* f, const PlanDev& pd, const PlanDev* pdp, double* frob, float* frob32, cudaStream_t s) {
+  const int d = pd.d, kind = pd.kind;
+  const size_t D = (size_t)pd.D;
+  const int npair = d * (d + 1) / 2;
+  std::vector<void*> tmp;
+  auto take = [&](size_t bytes) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      for (void* t : tmp) cudaFree(t);
+      raise(e == cudaErrorMemoryAllocation ? QP_ERR_OOM : QP_ERR_CUDA, "cudaMalloc failed in the Frobenius set-up");
+    }
+    tmp.push_back(q);
+    return q;
+  };
+  try {
+    double2* G = (double2*)take(npair * D * sizeof(double2));
+    double2* H = (double2*)take(D * sizeof(double2));
+    double2* X = (double2*)take(D * sizeof(double2));
+    double* cn = (double*)take(D * sizeof(double));
+    CK(cudaMemsetAsync(cn, 0, D * sizeof(double), s));
+    auto pidx = [&](int a, int a2) {   // index of the unordered pair (min, max)
+      const int lo = std::min(a, a2), hi = std::max(a, a2);
+      return lo * d - lo * (lo - 1) / 2 + (hi - lo);
+    };
+    for (int a = 0; a < d; ++a)
+      for (int a2 = a; a2 < d; ++a2) {
+        double2* g = G + (size_t)pidx(a, a2) * D;
+        k_fro_g<<<f->nblk, BLOCK, 0, s>>>(pdp, a, a2, g);
+        count_launch();
+        fft_nd<double>(g, pd.n, pd.N, 1, -1, s);
+      }
+    auto comp = [&](int a, int b) -> int {
+      if (kind == QP_COEF_SCALAR) return a == b ? 0 : -1;
+      if (kind == QP_COEF_DIAG) return a == b ? a : -1;
+      const int lo = std::min(a, b), hi = std::max(a, b);
+      return lo * d - lo * (lo - 1) / 2 + (hi - lo);
+    };
+    for (int b = 0; b < d; ++b)
+      for (int b2 = b; b2 < d; ++b2) {
+        CK(cudaMemsetAsync(X, 0, D * sizeof(double2), s));
+        bool any = false;
+        for (int o = 0; o < (b == b2 ? 1 : 2); ++o) {
+          const int bb1 = o == 0 ? b : b2, bb2 = o == 0 ? b2 : b;   // (b, b') and, off the diagonal, (b', b)
+          for (int a = 0; a < d; ++a)
+            for (int a2 = 0; a2 < d; ++a2) {
+              const int c1 = comp(a, bb1), c2 = comp(a2, bb2);
+              if (c1 < 0 || c2 < 0) continue;
+              k_fro_h<<<f->nblk, BLOCK, 0, s>>>(pdp, f->ahat, c1, c2, H);
+              count_launch();
+              fft_nd<double>(H, pd.n, pd.N, 1, -1, s);
+              k_fro_macc<<<f->nblk, BLOCK, 0, s>>>(pd.D, G + (size_t)pidx(a, a2) * D, H, X);
+              count_launch();
+              any = true;
+            }
+        }
+        if (!any) continue;
+        fft_nd<double>(X, pd.n, pd.N, 1, +1, s);
+        k_fro_cn<<<f->nblk, BLOCK, 0, s>>>(pdp, b, b2, X, cn);
+        count_launch();
+      }
+    k_fro_final<<<f->nblk, BLOCK, 0, s>>>(pdp, f->ahat, cn, frob, frob32);
+    count_launch();
+    CK_LAUNCH();
+    CK(cudaStreamSynchronize(s));
+  } catch (...) {
+    cudaStreamSynchronize(s);
+    for (void* t : tmp) cudaFree(t);
+    throw;
+  }
+  for (void* t : tmp) cudaFree(t);
 }
 
 // ---- apply: gradient -> inverse DFT -> A(y) / D -> DFT -> divergence

@@ -19,6 +19,8 @@ void fft_set_taps(FftPlan* f, const PlanDev& pd, const PlanDev* pdp, cudaStream_
 // out[0..2]: min |lambda|^2, min q/|lambda|^2 over k != 0, smallest Cholesky pivot of A over the nodes.
 void fft_diag(FftPlan* f, const PlanDev* pd, const PlanDev* pdp, double* jac, double* frob, float* jac32,
               float* frob32, double* out, cudaStream_t s);
+// The Frobenius-optimal diagonal (Sec. 4.3) into frob / frob32 by FFT cross-correlations; synchronises s.
+void fft_frobenius(FftPlan* f, const PlanDev& pd, const PlanDev* pdp, double* frob, float* frob32, cudaStream_t s);
 // w = Q h for nrhs vectors of the plan.
 template <typename T>
 void fft_apply(FftPlan* f, const PlanDev& pd, const PlanDev* pdp, const cplx<T>* h, cplx<T>* w, int nrhs,
