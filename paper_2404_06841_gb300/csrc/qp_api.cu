@@ -664,9 +664,9 @@ Entry& get_entry(Solver* sv, const Units& us, const Key& key) {
     x.D = p->D;
     x.nrhs = us.nrhs[u];
     // one chunk per block, blocks dispatched in index order so that the resident blocks cover a contiguous
-    // window of modes (neighbour reads along outer axes then hit L2); the chunk depends on D only (about 8
-    // chunks per SM, 256 to 8192 modes), so the reduction order of a unit does not depend on its batch
-    const int64_t chunk = std::max<int64_t>(BLOCK, std::min<int64_t>(8192, (p->D / (152 * 8) + BLOCK - 1) / BLOCK * BLOCK));
+    // window of modes (neighbour reads along outer axes then hit L2); the chunk depends on D only
+    // (chunk_modes), so the reduction order of a unit does not depend on its batch
+    const int64_t chunk = chunk_modes(p->D);
     x.chunk = (int)chunk;
     x.run = last_axis_run(p);
     x.chunk0 = (int)chunk_unit.size();

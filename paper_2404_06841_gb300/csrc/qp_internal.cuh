@@ -1,5 +1,6 @@
 // Internal declarations shared by the CUDA translation units of libqp (not part of the C ABI).
 #pragma once
+#include <algorithm>
 
 #include <cuda_runtime.h>
 
@@ -60,6 +61,13 @@ struct FastDiv {
   uint32_t m;
   uint32_t p;
 };
+
+// Modes per chunk of a unit (a chunk is reduced by one block): 256..8192 modes, about 8 chunks per SM. It depends
+// on D only, so that a unit reduces in the same order alone or batched. (About two chunks per SM for small D,
+// which balances the FP64 apply across the SMs, measured no faster: per-iteration latency dominates there.)
+inline int64_t chunk_modes(int64_t D) {
+  return std::max<int64_t>(BLOCK, std::min<int64_t>(8192, (D / (152 * 8) + BLOCK - 1) / BLOCK * BLOCK));
+}
 
 inline FastDiv make_fastdiv(uint32_t d) {
   uint32_t L = 0;

@@ -215,7 +215,7 @@ extern "C" qp_status qp_pcg_solve_taps_static(int d, int n, const double* P, con
     build_host(d, n, P, N, coeff, ht);
     const int D = ht.pd.D;
     const int nc = ht.pd.ncomp, G = ht.pd.ntaps;
-    const int64_t chunk = std::max<int64_t>(BLOCK, std::min<int64_t>(8192, (D / (152 * 8) + BLOCK - 1) / BLOCK * BLOCK));
+    const int64_t chunk = chunk_modes(D);
     const int nchunks = (int)((D + chunk - 1) / chunk);
     const int run = (N[n - 1] % 2 == 0) ? 2 : 1;   // stencil run along the last axis
     const int nblk_diag = (int)std::min<int64_t>((D + BLOCK - 1) / BLOCK, 152 * 8);
