@@ -59,7 +59,8 @@ struct qp_plan {
   double min_abs_lambda = 0.0;
   int64_t bytes = 0;
   std::vector<void*> dev_allocs;
-  std::vector<void*> host_allocs;
+  std::vector<std::pair<void*, size_t>> host_allocs;
+  cudaStream_t create_stream = nullptr;   // plan buffers are allocated in this stream's order
 
   PlanDev host_pd{};           // host copy of the device plan description
   PlanDev* pd = nullptr;       // device copy
@@ -83,22 +84,14 @@ struct qp_plan {
   Solver* solver = nullptr;         // graph cache for single-plan solves
 
   void* dalloc(size_t bytes_) {
-    void* p = nullptr;
-    if (bytes_ == 0) bytes_ = 16;
-    cudaError_t e = cudaMalloc(&p, bytes_);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      raise(e == cudaErrorMemoryAllocation ? QP_ERR_OOM : QP_ERR_CUDA,
-            "cudaMalloc of " + std::to_string(bytes_) + " bytes failed: " + cudaGetErrorString(e));
-    }
+    void* p = dev_alloc(bytes_, create_stream);
     dev_allocs.push_back(p);
     bytes += (int64_t)bytes_;
     return p;
   }
   void* halloc(size_t bytes_) {
-    void* p = nullptr;
-    CK(cudaMallocHost(&p, bytes_));
-    host_allocs.push_back(p);
+    void* p = pinned_alloc(bytes_);
+    host_allocs.push_back({p, bytes_});
     return p;
   }
   ~qp_plan();
@@ -129,7 +122,7 @@ struct Entry {
   ~Entry() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
-    for (void* p : allocs) cudaFree(p);
+    for (void* p : allocs) dev_free(p);
   }
 };
 
@@ -151,7 +144,9 @@ struct Solver {
   bool graphs_ok = true;
   std::vector<void*> allocs;
 
-  explicit Solver(const std::vector<qp_plan*>& ps) : plans(ps) {
+  cudaStream_t s0 = nullptr;   // allocations are ordered on the stream of the call that created the solver
+
+  Solver(const std::vector<qp_plan*>& ps, cudaStream_t s) : plans(ps), s0(s) {
     const size_t nu = plans.size();
     st = (RhsSt*)alloc(nu * MAXR * sizeof(RhsSt));
     ucount = (unsigned*)alloc(nu * sizeof(unsigned));
@@ -159,38 +154,39 @@ struct Solver {
     ndone = (int*)alloc(64);
     pbar = (unsigned*)alloc(64);
     perr = (int*)alloc(64);
-    CK(cudaMemset(st, 0, nu * MAXR * sizeof(RhsSt)));
-    CK(cudaMemset(ucount, 0, nu * sizeof(unsigned)));
-    CK(cudaMemset(kcount, 0, 64));
-    CK(cudaMemset(ndone, 0, 64));
-    CK(cudaMallocHost(&h_st, nu * MAXR * sizeof(RhsSt)));
-    CK(cudaMallocHost(&h_perr, sizeof(int)));
-    CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    CK(cudaMemsetAsync(st, 0, nu * MAXR * sizeof(RhsSt), s));
+    CK(cudaMemsetAsync(ucount, 0, nu * sizeof(unsigned), s));
+    CK(cudaMemsetAsync(kcount, 0, 64, s));
+    CK(cudaMemsetAsync(ndone, 0, 64, s));
+    h_st = (RhsSt*)pinned_alloc(nu * MAXR * sizeof(RhsSt));
+    h_perr = (int*)pinned_alloc(sizeof(int));
   }
   ~Solver() {
     cache.clear();
     if (cap) cudaStreamDestroy(cap);
-    if (h_st) cudaFreeHost(h_st);
-    if (h_perr) cudaFreeHost(h_perr);
-    for (void* p : allocs) cudaFree(p);
+    pinned_free(h_st, plans.size() * MAXR * sizeof(RhsSt));
+    pinned_free(h_perr, sizeof(int));
+    for (void* p : allocs) dev_free(p);
   }
   void* alloc(size_t b) {
-    void* p = nullptr;
-    cudaError_t e = cudaMalloc(&p, b);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      raise(e == cudaErrorMemoryAllocation ? QP_ERR_OOM : QP_ERR_CUDA, "cudaMalloc failed in solver set-up");
-    }
+    void* p = dev_alloc(b, s0);
     allocs.push_back(p);
     return p;
+  }
+  // the capture stream of graph recording, created on first use (persistent solves never record a graph)
+  cudaStream_t capture_stream() {
+    if (!cap) CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    return cap;
   }
 };
 
 qp_plan::~qp_plan() {
+  cudaDeviceSynchronize();   // no work of any stream may still use the plan's buffers
   delete solver;
   if (fft) fft_plan_destroy(fft);
-  for (void* p : dev_allocs) cudaFree(p);
-  for (void* p : host_allocs) cudaFreeHost(p);
+  for (void* p : dev_allocs) dev_free(p);
+  for (auto& h : host_allocs) pinned_free(h.first, h.second);
+  dev_trim();
 }
 
 struct qp_batch {
@@ -198,10 +194,13 @@ struct qp_batch {
   Solver* solver = nullptr;
   double* small = nullptr;     // device a* outputs (2 d^2 per plan)
   double* h_small = nullptr;
+  size_t small_bytes = 0;
   ~qp_batch() {
+    cudaDeviceSynchronize();
     delete solver;
-    if (small) cudaFree(small);
-    if (h_small) cudaFreeHost(h_small);
+    dev_free(small);
+    pinned_free(h_small, small_bytes);
+    dev_trim();
   }
 };
 
@@ -390,7 +389,7 @@ void build_taps(qp_plan* p, const qp_coeff* c) {
   }
   auto up = [&](const void* src, size_t bytes_) {
     void* dst = p->dalloc(bytes_);
-    CK(cudaMemcpy(dst, src, bytes_, cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync(dst, src, bytes_, cudaMemcpyHostToDevice, p->create_stream));   // pageable: staged
     return dst;
   };
   pd.coef64 = (const double2*)up(coef64.data(), coef64.size() * sizeof(double2));
@@ -422,8 +421,8 @@ void alloc_workspace(qp_plan* p) {
   p->scratch = (double*)p->dalloc((size_t)4 * p->nblk * sizeof(double) + 64);
   p->counter = (unsigned*)p->dalloc(64);
   p->small = (double*)p->dalloc(256 * sizeof(double));
-  CK(cudaMemset(p->counter, 0, 64));
-  CK(cudaMemset(p->small, 0, 256 * sizeof(double)));
+  CK(cudaMemsetAsync(p->counter, 0, 64, p->create_stream));
+  CK(cudaMemsetAsync(p->small, 0, 256 * sizeof(double), p->create_stream));
   p->h_small = (double*)p->halloc(256 * sizeof(double));
 }
 
@@ -642,7 +641,7 @@ void run_direct(const Units& us, Entry& en, const Key& key, int nslots, cudaStre
 }
 
 // Builds (or finds) the entry for these units and key: device unit/chunk tables and the recorded graph.
-Entry& get_entry(Solver* sv, const Units& us, const Key& key) {
+Entry& get_entry(Solver* sv, const Units& us, const Key& key, cudaStream_t s) {
   auto it = sv->cache.find(key);
   if (it != sv->cache.end()) return *it->second;
   std::unique_ptr<Entry> en(new Entry());
@@ -687,10 +686,9 @@ Entry& get_entry(Solver* sv, const Units& us, const Key& key) {
   }
   const int nchunks = (int)chunk_unit.size();
   auto up = [&](const void* src, size_t bytes_) {
-    void* dst = nullptr;
-    CK(cudaMalloc(&dst, bytes_));
+    void* dst = dev_alloc(bytes_, s);
     en->allocs.push_back(dst);
-    CK(cudaMemcpy(dst, src, bytes_, cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync(dst, src, bytes_, cudaMemcpyHostToDevice, s));   // pageable source: staged before return
     return dst;
   };
   BatchDev& bd = en->bd;
@@ -703,8 +701,7 @@ Entry& get_entry(Solver* sv, const Units& us, const Key& key) {
   bd.st = sv->st;
   bd.chunk_unit = (const int*)up(chunk_unit.data(), chunk_unit.size() * sizeof(int));
   {
-    void* pp = nullptr;
-    CK(cudaMalloc(&pp, (size_t)NSLOT_PERSIST * nchunks * sizeof(double)));
+    void* pp = dev_alloc((size_t)NSLOT_PERSIST * nchunks * sizeof(double), s);
     en->allocs.push_back(pp);
     bd.partials = (double*)pp;
   }
@@ -737,7 +734,7 @@ Entry& get_entry(Solver* sv, const Units& us, const Key& key) {
   }
   if (en->pgrid == 0 && sv->graphs_ok && !us.direct) {
     try {
-      build_graph(us, *en, key, sv->cap);
+      build_graph(us, *en, key, sv->capture_stream());
     } catch (const QpError&) {
       // graphs with conditional nodes are unavailable: host-driven loops for this solver from now on
       cudaGetLastError();
@@ -763,7 +760,7 @@ struct SolveResult {
 
 // One solve of all units (their F in v64.F, solutions in v64.X); reads back the state.
 void run_solve(Solver* sv, const Units& us, const Key& key, cudaStream_t s, SolveResult& res) {
-  Entry& en = get_entry(sv, us, key);
+  Entry& en = get_entry(sv, us, key, s);
   int nslots = 0;
   for (int r : us.nrhs) nslots += r;
   if (en.pgrid > 0) {
@@ -974,6 +971,7 @@ qp_status qp_plan_create(int d, int n, const double* P, const int* N, const qp_c
   if (!coeff) raise(QP_ERR_INVALID_ARG, "coeff must be non-null");
   std::unique_ptr<qp_plan> p(new qp_plan());
   cudaStream_t s = S(stream);
+  p->create_stream = s;
   build_geometry(p.get(), d, n, P, N);
   if (coeff->kind < QP_COEF_SCALAR || coeff->kind > QP_COEF_SYM) raise(QP_ERR_INVALID_ARG, "unknown coefficient kind");
   p->kind = coeff->kind;
@@ -1003,14 +1001,14 @@ qp_status qp_plan_create(int d, int n, const double* P, const int* N, const qp_c
   alloc_workspace(p.get());
   p->pd = (PlanDev*)p->dalloc(sizeof(PlanDev));
   if (p->backend == QP_BACKEND_TAPS) {
-    CK(cudaMemcpy(p->pd, &p->host_pd, sizeof(PlanDev), cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync(p->pd, &p->host_pd, sizeof(PlanDev), cudaMemcpyHostToDevice, s));
     launch_diag(p->pd, p->coef_count, p->D, p->jac64, p->frob64, p->jac32, p->frob32, p->scratch, p->counter,
                 p->small, p->nblk, s);
     CK_LAUNCH();
     p->frob_ready = true;
   } else {
-    CK(cudaMemcpy(p->pd, &p->host_pd, sizeof(PlanDev), cudaMemcpyHostToDevice));
-    p->fft = fft_plan_create(p->host_pd, p->precisions, p->max_rhs);
+    CK(cudaMemcpyAsync(p->pd, &p->host_pd, sizeof(PlanDev), cudaMemcpyHostToDevice, s));
+    p->fft = fft_plan_create(p->host_pd, p->precisions, p->max_rhs, s);
     if (coeff->repr == QP_REPR_GRID) fft_set_grid(p->fft, p->host_pd, p->pd, coeff->grid, s);
     else fft_set_taps(p->fft, p->host_pd, p->pd, s);
     fft_diag(p->fft, &p->host_pd, p->pd, p->jac64, p->frob64, p->jac32, p->frob32, p->small, s);
@@ -1091,7 +1089,7 @@ qp_status qp_pcg_solve(qp_plan* p, int nrhs, const void* F, void* U, const qp_so
   const size_t bytes = (size_t)nrhs * p->D * sizeof(double2);
   CK(cudaMemcpyAsync(p->v64.F, F, bytes, cudaMemcpyDeviceToDevice, s));
   CK(cudaMemcpyAsync(p->v64.X, U, bytes, cudaMemcpyDeviceToDevice, s));
-  if (!p->solver) p->solver = new Solver({p});
+  if (!p->solver) p->solver = new Solver({p}, s);
   Units us = single_units(p, nrhs);
   SolveResult r;
   solve_units(p->solver, us, *opts, true, s, r);
@@ -1119,7 +1117,7 @@ qp_status qp_homogenized(qp_plan* p, const qp_solve_opts* opts, double* Are, dou
   cudaStream_t s = S(stream);
   prepare_precond(p, opts->precond, s);
   corrector_rhs(p, 0, p->d, p->v64.F, s);
-  if (!p->solver) p->solver = new Solver({p});
+  if (!p->solver) p->solver = new Solver({p}, s);
   Units us = single_units(p, p->d);
   SolveResult r;
   solve_units(p->solver, us, *opts, false, s, r);
@@ -1161,9 +1159,11 @@ qp_status qp_batch_create(int count, qp_plan* const* plans, qp_batch** out) {
     b->plans.push_back(plans[i]);
     tot += 2 * plans[i]->d * plans[i]->d;
   }
-  b->solver = new Solver(b->plans);
-  CK(cudaMalloc(&b->small, tot * sizeof(double)));
-  CK(cudaMallocHost(&b->h_small, tot * sizeof(double)));
+  b->solver = new Solver(b->plans, nullptr);
+  b->small = (double*)dev_alloc(tot * sizeof(double), nullptr);
+  b->small_bytes = tot * sizeof(double);
+  b->h_small = (double*)pinned_alloc(b->small_bytes);
+  CK(cudaStreamSynchronize(nullptr));
   *out = b.release();
   API_END
 }

@@ -411,29 +411,26 @@ struct FftPlan {
   double* part = nullptr;       // reduction partials
   int nblk = 0;
   FusedSchedule fused64, fused32;   // group-pass schedules of the apply (ok = false: per-axis passes)
+  cudaStream_t stream = nullptr;   // the creating stream (allocations are ordered on it)
   void* take(size_t b) {
-    void* p = nullptr;
-    cudaError_t e = cudaMalloc(&p, b);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      raise(e == cudaErrorMemoryAllocation ? QP_ERR_OOM : QP_ERR_CUDA, "cudaMalloc failed in the FFT plan");
-    }
+    void* p = dev_alloc(b, stream);
     allocs.push_back(p);
     bytes += (int64_t)b;
     return p;
   }
   ~FftPlan() {
-    for (void* p : allocs) cudaFree(p);
+    for (void* p : allocs) dev_free(p);
   }
 };
 
 static FusedSchedule plan_fused(const PlanDev& pd, int esize);
 
-FftPlan* fft_plan_create(const PlanDev& pd, int precisions, int max_rhs) {
+FftPlan* fft_plan_create(const PlanDev& pd, int precisions, int max_rhs, cudaStream_t s) {
   for (int j = 0; j < pd.n; ++j)
     if (!fft_supported(pd.N[j])) raise(QP_ERR_UNSUPPORTED, "FFT size " + std::to_string(pd.N[j]) + " is not built");
   ensure_twiddles();
   FftPlan* f = new FftPlan();
+  f->stream = s;
   try {
     f->d = pd.d;
     f->n = pd.n;
@@ -756,13 +753,7 @@ void fft_frobenius(FftPlan* f, const PlanDev& pd, const PlanDev* pdp, double* fr
   const int npair = d * (d + 1) / 2;
   std::vector<void*> tmp;
   auto take = [&](size_t bytes) {
-    void* q = nullptr;
-    cudaError_t e = cudaMalloc(&q, bytes);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      for (void* t : tmp) cudaFree(t);
-      raise(e == cudaErrorMemoryAllocation ? QP_ERR_OOM : QP_ERR_CUDA, "cudaMalloc failed in the Frobenius set-up");
-    }
+    void* q = dev_alloc(bytes, s);
     tmp.push_back(q);
     return q;
   };
@@ -818,10 +809,10 @@ void fft_frobenius(FftPlan* f, const PlanDev& pd, const PlanDev* pdp, double* fr
     CK(cudaStreamSynchronize(s));
   } catch (...) {
     cudaStreamSynchronize(s);
-    for (void* t : tmp) cudaFree(t);
+    for (void* t : tmp) dev_free(t);
     throw;
   }
-  for (void* t : tmp) cudaFree(t);
+  for (void* t : tmp) dev_free(t);
 }
 
 // ---- apply: gradient -> inverse DFT -> A(y) / D -> DFT -> divergence

@@ -8,7 +8,7 @@ namespace qp {
 struct FftPlan;
 
 // pd: host copy of the plan description; pdp: its device copy (must be uploaded before the set-up calls).
-FftPlan* fft_plan_create(const PlanDev& pd, int precisions, int max_rhs);
+FftPlan* fft_plan_create(const PlanDev& pd, int precisions, int max_rhs, cudaStream_t s);
 void fft_plan_destroy(FftPlan* f);
 int64_t fft_plan_bytes(const FftPlan* f);
 bool fft_supported(int N);

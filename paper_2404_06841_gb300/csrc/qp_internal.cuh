@@ -170,6 +170,14 @@ void launch_pcg_update(const BatchDev& b, int maxr, int level, unsigned long lon
 void launch_pcg_hupdate(const BatchDev& b, int maxr, int level, int nblk, cudaStream_t s);
 void launch_refine_prep(const BatchDev& b, int nblk, cudaStream_t s);
 void launch_refine_accum(const BatchDev& b, int nblk, cudaStream_t s);
+// Library memory (qp_mem.cu): device blocks from a stream-ordered pool that keeps freed blocks cached (dev_free
+// must come after the device work using the block has completed), page-locked host blocks from a size-class cache.
+void* dev_alloc(size_t bytes, cudaStream_t s);
+void dev_free(void* p);
+void dev_trim();
+void* pinned_alloc(size_t bytes);
+void pinned_free(void* p, size_t bytes);
+
 // ||U_r - Uref_r||_2 over the Fourier coefficients (qp_norms.cu)
 void launch_l2_norms(int D, int nrhs, const double2* U, const double2* Uref, double* part, int nblk, double* out,
                      cudaStream_t s);

@@ -1,0 +1,97 @@
+// Memory for plans, solvers and batches. Device buffers come from a library-owned stream-ordered pool per device
+// whose release threshold keeps freed blocks cached, so creating and destroying plans repeatedly (one plan per
+// request) reuses memory instead of calling cudaMalloc / cudaFree, each of which synchronises the device; a
+// destroy trims the pool back to 1 GiB, so a large plan's memory returns to the device. Small page-locked host
+// mirrors (solver state, a*) come from a process-wide cache by size class for the same reason.
+#include <cstdint>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "qp_internal.cuh"
+
+namespace qp {
+
+namespace {
+
+std::mutex g_pool_mutex;
+cudaMemPool_t g_pools[64] = {};
+
+cudaMemPool_t pool_of_current_device() {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) raise(QP_ERR_CUDA, "device index out of range");
+  std::lock_guard<std::mutex> lock(g_pool_mutex);
+  if (!g_pools[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    CK(cudaMemPoolCreate(&pool, &props));
+    uint64_t keep = UINT64_MAX;   // never trim: freed blocks stay with the pool for the next plan
+    CK(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+    g_pools[dev] = pool;
+  }
+  return g_pools[dev];
+}
+
+std::mutex g_pinned_mutex;
+std::map<size_t, std::vector<void*>> g_pinned_free;   // size class -> cached page-locked blocks
+
+size_t size_class(size_t b) {
+  size_t c = 256;
+  while (c < b) c <<= 1;
+  return c;
+}
+
+}  // namespace
+
+void* dev_alloc(size_t bytes, cudaStream_t s) {
+  if (bytes == 0) bytes = 16;
+  void* p = nullptr;
+  cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, pool_of_current_device(), s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    raise(e == cudaErrorMemoryAllocation ? QP_ERR_OOM : QP_ERR_CUDA,
+          "device allocation of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
+  }
+  return p;
+}
+
+void dev_free(void* p) {
+  if (p) cudaFreeAsync(p, 0);
+}
+
+// After a plan's buffers went back to the pool: keep up to 1 GiB cached for the next plans, return the rest.
+void dev_trim() {
+  cudaStreamSynchronize(0);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+  std::lock_guard<std::mutex> lock(g_pool_mutex);
+  if (g_pools[dev]) cudaMemPoolTrimTo(g_pools[dev], (size_t)1 << 30);
+}
+
+void* pinned_alloc(size_t bytes) {
+  const size_t c = size_class(bytes);
+  {
+    std::lock_guard<std::mutex> lock(g_pinned_mutex);
+    auto it = g_pinned_free.find(c);
+    if (it != g_pinned_free.end() && !it->second.empty()) {
+      void* p = it->second.back();
+      it->second.pop_back();
+      return p;
+    }
+  }
+  void* p = nullptr;
+  CK(cudaMallocHost(&p, c));
+  return p;
+}
+
+void pinned_free(void* p, size_t bytes) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lock(g_pinned_mutex);
+  g_pinned_free[size_class(bytes)].push_back(p);
+}
+
+}  // namespace qp
