@@ -1306,7 +1306,8 @@ template <typename T, int MODE>
 static void launch_group(const GroupPass& gp, const PlanDev* pdp, int nrhs, int ny, const cplx<T>* h, cplx<T>* g,
                          cplx<T>* w, const T* coef, cudaStream_t s) {
   auto fn = k_fft_group<T, MODE>;
-  if (gp.smem > 48 * 1024) CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gp.smem));
+  // the 48 KB default covers static + dynamic shared memory (about 7 KB static here): opt in above 40 KB
+  if (gp.smem > 40 * 1024) CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gp.smem));
   dim3 grid((unsigned)((long long)gp.tiles_o * gp.tiles_i), (unsigned)ny);
   fn<<<grid, BLOCK, gp.smem, s>>>(pdp, gp, nrhs, h, g, w, coef);
   count_launch();
