@@ -129,7 +129,8 @@ qp_status qp_plan_query(const qp_plan* plan, qp_plan_info* info);
 
 /* QU = Q U (eq. n-discrete_equation; compressed mat-vec of Sec. 4.2 on the taps backend, or gradient ->
  * inverse n-dim DFT -> pointwise A(y) -> forward DFT -> divergence on the FFT backend).
- * U, QU: device, nrhs x D complex (complex128 for QP_FP64, complex64 for QP_FP32); must not overlap. */
+ * U, QU: device, nrhs x D complex (complex128 for QP_FP64, complex64 for QP_FP32), each 16-byte aligned (the
+ * kernels move two complex64 values per access); must not overlap. A misaligned pointer gives QP_ERR_INVALID_ARG. */
 qp_status qp_apply_stiffness(qp_plan* plan, int nrhs, const void* U, void* QU, int precision, void* stream);
 
 /* F = the corrector right-hand sides F_j(k) = i sum_a lambda_a(k) A~^{aj}_k, F_j(0) = 0, for
@@ -196,7 +197,7 @@ qp_status qp_plan_diagonal(qp_plan* plan, int precond, double* out, void* stream
 
 /* Error of a computed solution in the L^2_QP norm (Sec. 5.1, e_N = ||u_N - u||): by the Parseval identity of that
  * norm (Sec. 2.2, eq. parseval) it is the l^2 norm of the Fourier coefficients, out[r] = ||U_r - Uref_r||_2 over
- * K_N^n. U, Uref: device complex128, nrhs x D (1 <= nrhs <= QP_MAX_RHS; Uref NULL gives ||U_r||). out: host
+ * K_N^n. U, Uref: device complex128, nrhs x D, 16-byte aligned (1 <= nrhs <= QP_MAX_RHS; Uref NULL gives ||U_r||). out: host
  * double[nrhs]. When Uref holds the exact solution's coefficients on K_N^n, modes of the exact solution outside
  * K_N^n (truncation) add the sum of their |coefficient|^2 to out[r]^2; the caller adds that part. Deterministic
  * FP64 reduction; synchronises stream. */

@@ -63,6 +63,7 @@ struct qp_plan {
   cudaStream_t create_stream = nullptr;   // plan buffers are allocated in this stream's order
 
   PlanDev host_pd{};           // host copy of the device plan description
+  StarParams star_host{};      // star-1 stencil data (host_pd.star1), passed by value to single-plan kernels
   PlanDev* pd = nullptr;       // device copy
   bool real_coef = false;
   int coef_count = 0;          // ntaps * ncomp
@@ -119,6 +120,7 @@ struct Entry {
   int fixed_nodes = 0, body_nodes = 0, outer_nodes = 0;
   int pgrid = 0;          // > 0: the solve is one persistent launch of this many blocks
   size_t psmem = 0;
+  int psk = 0;            // persistent kernel's stencil source (0 shared plan, 1/2 star-1 scalar/diagonal)
   ~Entry() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
@@ -398,6 +400,8 @@ void build_taps(qp_plan* p, const qp_coeff* c) {
   pd.real_coef = real_coef ? 1 : 0;
   p->real_coef = real_coef;
   p->coef_count = G * nc;
+  make_star(pd, coef64.data(), coef32.data(), p->star_host);
+  if (pd.star1) pd.star = (const StarParams*)up(&p->star_host, sizeof(StarParams));
 }
 
 void alloc_workspace(qp_plan* p) {
@@ -458,7 +462,11 @@ void record_apply(const Units& us, const Entry& en, int level, int epi, int refi
     else if (epi == EPI_DOT_HW) fft_apply<double>(p->fft, p->host_pd, p->pd, p->v64.h, p->v64.w, nr, s);
     else fft_apply<double>(p->fft, p->host_pd, p->pd, p->v64.X, p->v64.w, nr, s);
   }
-  launch_apply(en.bd, us.all_real, us.max_coef, us.max_rhs, level, epi, refine, cond, en.nblk, s);
+  // a single star-1 unit with an even last axis takes its stencil data as a kernel parameter
+  const qp_plan* p0 = us.plans.size() == 1 ? us.plans[0] : nullptr;
+  const bool st = p0 && p0->backend == QP_BACKEND_TAPS && p0->host_pd.star1 && last_axis_run(p0) == 2;
+  launch_apply(en.bd, us.all_real, us.max_coef, us.max_rhs, level, epi, refine, cond, en.nblk,
+               st ? &p0->star_host : nullptr, p0 ? p0->kind : 0, s);
   CK_LAUNCH();
 }
 
@@ -720,9 +728,11 @@ Entry& get_entry(Solver* sv, const Units& us, const Key& key, cudaStream_t s) {
     // problems, where launch and synchronisation latency dominate); larger solves keep the graph, whose
     // kernels run at higher occupancy.
     const size_t smem = persistent_smem(us.max_coef);
+    const qp_plan* p0 = us.plans[0];
+    const int sk = (p0->backend == QP_BACKEND_TAPS && p0->host_pd.star1) ? (p0->kind == QP_COEF_DIAG ? 2 : 1) : 0;
     int capn = 0;
     try {
-      capn = persistent_capacity(us.all_real, us.max_rhs, smem);
+      capn = persistent_capacity(us.all_real, us.max_rhs, sk, smem);
     } catch (const QpError&) {
       cudaGetLastError();
       capn = 0;
@@ -730,6 +740,7 @@ Entry& get_entry(Solver* sv, const Units& us, const Key& key, cudaStream_t s) {
     if (capn > 0 && (us.exec == QP_EXEC_PERSISTENT || nchunks <= capn)) {
       en->pgrid = std::min(capn, nchunks);
       en->psmem = smem;
+      en->psk = sk;
     }
   }
   if (en->pgrid == 0 && sv->graphs_ok && !us.direct) {
@@ -764,8 +775,8 @@ void run_solve(Solver* sv, const Units& us, const Key& key, cudaStream_t s, Solv
   int nslots = 0;
   for (int r : us.nrhs) nslots += r;
   if (en.pgrid > 0) {
-    launch_persistent(en.bd, us.all_real, us.max_rhs, key.mode, key.warm != 0, sv->pbar, sv->perr,
-                      g_barrier_timeout.load(), en.pgrid, en.psmem, s);
+    launch_persistent(en.bd, us.all_real, us.max_rhs, en.psk, en.psk ? &us.plans[0]->star_host : nullptr, key.mode,
+                      key.warm != 0, sv->pbar, sv->perr, g_barrier_timeout.load(), en.pgrid, en.psmem, s);
     CK(cudaMemcpyAsync(sv->h_perr, sv->perr, sizeof(int), cudaMemcpyDeviceToHost, s));
   } else if (en.exec) {
     CK(cudaGraphLaunch(en.exec, s));
@@ -947,6 +958,7 @@ qp_status qp_l2qp_error(qp_plan* p, int nrhs, const void* U, const void* Uref, d
   API_BEGIN
   if (!p || !U || !out) raise(QP_ERR_INVALID_ARG, "plan, U and out must be non-null");
   if (nrhs < 1 || nrhs > MAXR) raise(QP_ERR_INVALID_ARG, "nrhs must be 1..QP_MAX_RHS");
+  if (((uintptr_t)U | (uintptr_t)Uref) & 15u) raise(QP_ERR_INVALID_ARG, "U and Uref must be 16-byte aligned");
   cudaStream_t s = S(stream);
   launch_l2_norms(p->D, nrhs, (const double2*)U, (const double2*)Uref, p->scratch, p->nblk, p->small, s);
   CK_LAUNCH();
@@ -1053,15 +1065,17 @@ qp_status qp_apply_stiffness(qp_plan* p, int nrhs, const void* U, void* QU, int 
   if (!p) raise(QP_ERR_INVALID_ARG, "plan must be non-null");
   if (nrhs < 1 || nrhs > p->max_rhs) raise(QP_ERR_INVALID_ARG, "nrhs must be 1..max_rhs");
   if (!U || !QU || U == QU) raise(QP_ERR_INVALID_ARG, "U and QU must be distinct non-null device pointers");
+  if (((uintptr_t)U | (uintptr_t)QU) & 15u) raise(QP_ERR_INVALID_ARG, "U and QU must be 16-byte aligned");
   if (precision != QP_FP64 && precision != QP_FP32) raise(QP_ERR_INVALID_ARG, "precision must be QP_FP64 or QP_FP32");
   cudaStream_t s = S(stream);
   if (p->backend == QP_BACKEND_TAPS) {
+    const StarParams* st1 = p->host_pd.star1 ? &p->star_host : nullptr;
     if (precision == QP_FP64)
       launch_apply_plain<double>(p->pd, p->real_coef, p->coef_count, p->D, nrhs, (const double2*)U, (double2*)QU,
-                                 last_axis_run(p), s);
+                                 last_axis_run(p), st1, p->kind, s);
     else
       launch_apply_plain<float>(p->pd, p->real_coef, p->coef_count, p->D, nrhs, (const float2*)U, (float2*)QU,
-                                last_axis_run(p), s);
+                                last_axis_run(p), st1, p->kind, s);
   } else {
     if (precision == QP_FP64) fft_apply<double>(p->fft, p->host_pd, p->pd, (const double2*)U, (double2*)QU, nrhs, s);
     else fft_apply<float>(p->fft, p->host_pd, p->pd, (const float2*)U, (float2*)QU, nrhs, s);

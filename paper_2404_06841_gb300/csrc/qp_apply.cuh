@@ -1,0 +1,298 @@
+// The stiffness-apply kernels of the taps backend (batch apply with the PCG epilogues, plain apply), shared by
+// the translation units that instantiate them per vector precision and epilogue (qp_apply_*.cu), so that the
+// instantiations compile in parallel.
+#pragma once
+#include "qp_stencil.cuh"
+
+namespace qp {
+
+// ------------------------------------------------------------------------------------------------ batch apply
+
+// One chunk [base, end) of a unit: dst = Q src with the epilogue, per-thread partials into vt. Thread t takes
+// runs of RUN consecutive modes: e0 = base + RUN t, base + RUN (t + BLOCK), ...
+// SK: the stencil's data source: 0 the plan in shared memory (apply_run), 1 / 2 the star-1 stencil of a scalar /
+// diagonal coefficient from st (a kernel parameter).
+template <typename T, int EPI, bool REALC, int NR, int RUN, int NV, int SK = 0>
+__device__ __forceinline__ void apply_chunk(const PlanDev& sp, const cplx<T>* scoef, const StarParams& st, int base,
+                                            int end, int D, int nrhs, int refine, bool fft_unit, const cplx<T>* src,
+                                            cplx<T>* dst, const cplx<T>* F, T (&vt)[NV]) {
+  for (int e0 = base + RUN * threadIdx.x; e0 < end; e0 += RUN * BLOCK) {
+    cplx<T> acc[RUN][NR];
+    if (EPI == EPI_RESIDUAL && refine == REFINE_ZERO_U) {
+#pragma unroll
+      for (int s = 0; s < RUN; ++s)
+#pragma unroll
+        for (int r = 0; r < NR; ++r) acc[s][r] = mk<T>(0, 0);
+    } else if (fft_unit) {
+#pragma unroll
+      for (int s = 0; s < RUN; ++s)
+#pragma unroll
+        for (int r = 0; r < NR; ++r) acc[s][r] = (r < nrhs) ? dst[(size_t)r * D + e0 + s] : mk<T>(0, 0);
+    } else if constexpr (SK != 0 && RUN == 2) {
+      apply_run_star<T, REALC, NR, true, SK == 2>(st, e0, src, D, nrhs, acc);
+    } else {
+      apply_run<T, REALC, NR, RUN>(sp, scoef, e0, src, D, nrhs, acc);
+    }
+#pragma unroll
+    for (int s = 0; s < RUN; ++s) {
+      const int e = e0 + s;
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        if (r < nrhs) {
+          const size_t o = (size_t)r * D + e;
+          if (EPI == EPI_DOT_HW) {
+            if (!fft_unit) dst[o] = acc[s][r];
+            const cplx<T> hv = src[o];
+            vt[r] = fma(hv.x, acc[s][r].x, fma(hv.y, acc[s][r].y, vt[r]));
+          } else if (EPI == EPI_RESIDUAL) {
+            const cplx<T> f = F[o];
+            const cplx<T> res = (e == 0) ? mk<T>(0, 0) : mk<T>(f.x - acc[s][r].x, f.y - acc[s][r].y);
+            dst[o] = res;
+            vt[2 * r] = fma(res.x, res.x, fma(res.y, res.y, vt[2 * r]));
+            if (e != 0) vt[2 * r + 1] = fma(f.x, f.x, fma(f.y, f.y, vt[2 * r + 1]));
+          } else {
+            if (!fft_unit) dst[o] = acc[s][r];
+          }
+        }
+      }
+    }
+  }
+}
+
+template <typename T, int EPI, bool REALC, int NR, int SK>
+__device__ __forceinline__ void apply_units(const BatchDev& b, int level, int refine, unsigned long long cond,
+                                            const StarParams& stp) {
+  __shared__ __align__(16) PlanDev sp;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cplx<T>* scoef = reinterpret_cast<cplx<T>*>(smraw);
+  const PlanDev* cur = nullptr;
+  for (int c = blockIdx.x; c < b.nchunks; c += gridDim.x) {
+    const int u = unit_of_chunk(b, c);
+    const UnitDev& un = unit_at(b, u);
+    RhsSt* st = b.st + (size_t)u * MAXR;
+    const int nrhs = un.nrhs;
+    // skip units with nothing left to do at this level (same decision for every chunk of the unit)
+    bool active = false;
+    for (int r = 0; r < nrhs; ++r) {
+      if (EPI == EPI_DOT_HW) active |= !ld_int(&st[r].done);
+      else if (EPI == EPI_RESIDUAL && refine) active |= !ld_int(&st[r].odone);
+      else active = true;
+    }
+    if (!active) continue;
+    if (un.plan != cur) {
+      cur = un.plan;
+      load_plan<T, SK == 0>(cur, sp, scoef);
+    }
+    const int D = un.D;
+    const cplx<T>* src;
+    cplx<T>* dst;
+    if (level == LEVEL_FP32) {
+      src = reinterpret_cast<const cplx<T>*>(un.h32);
+      dst = reinterpret_cast<cplx<T>*>(un.w32);
+    } else {
+      src = reinterpret_cast<const cplx<T>*>(EPI == EPI_DOT_HW ? (const double2*)un.h : (const double2*)un.U);
+      dst = reinterpret_cast<cplx<T>*>(un.w);
+    }
+    const cplx<T>* F = reinterpret_cast<const cplx<T>*>(un.F);
+    const bool fft_unit = (sp.backend == QP_BACKEND_FFT);
+    constexpr int NV = (EPI == EPI_RESIDUAL) ? 2 * NR : NR;   // reduced quantities: (h,w) or (|F-w|^2, |F|^2)
+    T vt[NV];                                                   // per-thread partials in the vector precision
+    double v[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) vt[q] = T(0);
+    const int base = (c - un.chunk0) * un.chunk;
+    const int end = min(base + un.chunk, D);
+    // the unit's own run length (so that its reduction order does not depend on the batch)
+    if constexpr (SK != 0) {
+      apply_chunk<T, EPI, REALC, NR, 2, NV, SK>(sp, scoef, stp, base, end, D, nrhs, refine, fft_unit, src, dst, F, vt);
+    } else {
+      if (un.run == 2)
+        apply_chunk<T, EPI, REALC, NR, 2, NV>(sp, scoef, stp, base, end, D, nrhs, refine, fft_unit, src, dst, F, vt);
+      else
+        apply_chunk<T, EPI, REALC, NR, 1, NV>(sp, scoef, stp, base, end, D, nrhs, refine, fft_unit, src, dst, F, vt);
+    }
+    if (EPI == EPI_NONE) continue;
+    block_reduce_mixed<T, NV>(vt, v);
+    if (!chunk_arrive<NV>(b, c, u, v)) continue;
+    // this block completes unit u: finalize its right-hand sides
+    unit_sums<NV>(b, un, v);
+    for (int r = 0; r < nrhs && r < NR; ++r) {
+      const double s0 = (EPI == EPI_RESIDUAL) ? v[2 * r] : v[r];
+      const double s1 = (EPI == EPI_RESIDUAL) ? v[(2 * r + 1) % NV] : 0.0;
+      if (threadIdx.x == 0) {
+        RhsSt& x = st[r];
+        if (EPI == EPI_DOT_HW) {
+          if (!x.done) {
+            x.hw = s0;
+            if (!(s0 > 0.0) || !isfinite(s0)) {   // (h, Q h) <= 0 or NaN: breakdown
+              x.done = 1;
+              x.status = QP_ERR_BREAKDOWN;
+              count_done(b, 0, 1, cond);           // completing the count here ends the PCG loop
+            } else {
+              x.alpha = x.rz / s0;
+            }
+          }
+        } else if (!refine) {
+          x.orr = s0;
+          x.of2 = s1;
+        } else if (!x.odone) {
+          x.orr = s0;
+          x.of2 = s1;
+          x.outer += 1;
+          x.inner_total += x.iters;
+          const double rel = s1 > 0.0 ? sqrt(s0 / s1) : 0.0;
+          int od = 0, os = QP_ERR_NO_CONVERGENCE;
+          if (s1 == 0.0 || s0 <= b.otol2 * s1) {
+            od = 1;
+            os = QP_OK;
+          } else if (!isfinite(rel)) {
+            od = 1;
+            os = QP_ERR_BREAKDOWN;
+          } else if (rel > 0.9 * x.prev_rel || x.outer > b.max_outer || x.inner_total >= b.maxit) {
+            od = 1;   // stagnation or cap
+          }
+          x.prev_rel = rel;
+          x.inv_scale = sqrt(s0);
+          x.scale = s0 > 0.0 ? 1.0 / x.inv_scale : 0.0;
+          x.ostatus = os;
+          if (od) {
+            x.odone = 1;
+            count_done(b, 1, 1, cond);             // the right-hand side that completes the count ends the loop
+          }
+        }
+      }
+    }
+    if (threadIdx.x == 0) b.ucount[u] = 0;
+  }
+}
+
+// Batch apply over every chunk of the batch (plans from the unit table, in shared memory).
+template <typename T, int EPI, bool REALC, int NR>
+__global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 3) k_apply(BatchDev b, int level, int refine, unsigned long long cond) {
+  apply_units<T, EPI, REALC, NR, 0>(b, level, refine, cond, star_smem());
+}
+
+// Batch apply of a single star-1 unit (even last axis): the stencil data as a kernel parameter.
+template <typename T, int EPI, bool REALC, int NR, int SK>
+__global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 3)
+    k_apply_star(BatchDev b, int level, int refine, unsigned long long cond, const __grid_constant__ StarParams st) {
+  apply_units<T, EPI, REALC, NR, SK>(b, level, refine, cond, st);
+}
+
+template <typename T, int EPI, int NR, bool REALC>
+static void apply_launch_rc(const BatchDev& b, int level, int refine, unsigned long long cond, int nblk, size_t smem,
+                            const StarParams* st1, int kind, cudaStream_t s) {
+  if (!st1) k_apply<T, EPI, REALC, NR><<<nblk, BLOCK, smem, s>>>(b, level, refine, cond);
+  else if (kind == QP_COEF_DIAG) k_apply_star<T, EPI, REALC, NR, 2><<<nblk, BLOCK, smem, s>>>(b, level, refine, cond, *st1);
+  else k_apply_star<T, EPI, REALC, NR, 1><<<nblk, BLOCK, smem, s>>>(b, level, refine, cond, *st1);
+}
+
+// st1: the StarParams of the batch's single unit when it is a star-1 plan with an even last axis (kind its
+// coefficient kind), else null.
+template <typename T, int EPI>
+void apply_launch_real(bool realc, int maxr, const BatchDev& b, int level, int refine, unsigned long long cond,
+                       int nblk, size_t smem, const StarParams* st1, int kind, cudaStream_t s) {
+  switch (maxr * 2 + (realc ? 1 : 0)) {
+    case 2: apply_launch_rc<T, EPI, 1, false>(b, level, refine, cond, nblk, smem, st1, kind, s); break;
+    case 3: apply_launch_rc<T, EPI, 1, true>(b, level, refine, cond, nblk, smem, st1, kind, s); break;
+    case 4: apply_launch_rc<T, EPI, 2, false>(b, level, refine, cond, nblk, smem, st1, kind, s); break;
+    case 5: apply_launch_rc<T, EPI, 2, true>(b, level, refine, cond, nblk, smem, st1, kind, s); break;
+    case 6: apply_launch_rc<T, EPI, 3, false>(b, level, refine, cond, nblk, smem, st1, kind, s); break;
+    case 7: apply_launch_rc<T, EPI, 3, true>(b, level, refine, cond, nblk, smem, st1, kind, s); break;
+    case 8: apply_launch_rc<T, EPI, 4, false>(b, level, refine, cond, nblk, smem, st1, kind, s); break;
+    default: apply_launch_rc<T, EPI, 4, true>(b, level, refine, cond, nblk, smem, st1, kind, s); break;
+  }
+}
+
+
+template <typename T, bool REALC, int NR, int RUN>
+__global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 3) k_apply_plain(const PlanDev* plan, int D, int nrhs,
+                                                                             const cplx<T>* h, cplx<T>* w) {
+  __shared__ __align__(16) PlanDev sp;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cplx<T>* scoef = reinterpret_cast<cplx<T>*>(smraw);
+  load_plan<T, true>(plan, sp, scoef);
+  const int e0 = (blockIdx.x * BLOCK + threadIdx.x) * RUN;   // one run per thread: blocks sweep memory in order
+  if (e0 >= D) return;
+  cplx<T> acc[RUN][NR];
+  apply_run<T, REALC, NR, RUN>(sp, scoef, e0, h, D, nrhs, acc);
+#pragma unroll
+  for (int s = 0; s < RUN; ++s)
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+      if (r < nrhs) w[(size_t)r * D + e0 + s] = acc[s][r];
+}
+
+// Plain apply of a star-1 plan with an even last axis: the stencil data as a kernel parameter; one run of two
+// modes per thread.
+template <typename T, bool REALC, int NR, int SK>
+__global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 3)
+    k_apply_plain_star(const __grid_constant__ StarParams st, int D, int nrhs, const cplx<T>* h, cplx<T>* w) {
+  const int e0 = (blockIdx.x * BLOCK + threadIdx.x) * 2;
+  if (e0 >= D) return;
+  cplx<T> acc[2][NR];
+  apply_run_star<T, REALC, NR, true, SK == 2>(st, e0, h, D, nrhs, acc);
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    if (r < nrhs) {
+      cplx<T>* o = w + (size_t)r * D + e0;
+      if (sizeof(T) == 4) {
+        *reinterpret_cast<float4*>(o) = make_float4((float)acc[0][r].x, (float)acc[0][r].y, (float)acc[1][r].x,
+                                                    (float)acc[1][r].y);
+      } else {
+        o[0] = acc[0][r];
+        o[1] = acc[1][r];
+      }
+    }
+  }
+}
+
+template <typename T, bool REALC, int SK>
+static void plain_star_nr(int nrhs, const StarParams& st, int D, const cplx<T>* h, cplx<T>* w, cudaStream_t s) {
+  const int nblk = (D / 2 + BLOCK - 1) / BLOCK;
+  switch (nrhs) {
+    case 1: k_apply_plain_star<T, REALC, 1, SK><<<nblk, BLOCK, 0, s>>>(st, D, nrhs, h, w); break;
+    case 2: k_apply_plain_star<T, REALC, 2, SK><<<nblk, BLOCK, 0, s>>>(st, D, nrhs, h, w); break;
+    case 3: k_apply_plain_star<T, REALC, 3, SK><<<nblk, BLOCK, 0, s>>>(st, D, nrhs, h, w); break;
+    default: k_apply_plain_star<T, REALC, 4, SK><<<nblk, BLOCK, 0, s>>>(st, D, nrhs, h, w); break;
+  }
+}
+
+template <typename T, bool REALC, int RUN>
+static void plain_nr(int nrhs, const PlanDev* plan_dev, int D, const cplx<T>* h, cplx<T>* w, size_t smem,
+                     cudaStream_t s) {
+  const int nblk = (D / RUN + BLOCK - 1) / BLOCK;
+  switch (nrhs) {
+    case 1: k_apply_plain<T, REALC, 1, RUN><<<nblk, BLOCK, smem, s>>>(plan_dev, D, nrhs, h, w); break;
+    case 2: k_apply_plain<T, REALC, 2, RUN><<<nblk, BLOCK, smem, s>>>(plan_dev, D, nrhs, h, w); break;
+    case 3: k_apply_plain<T, REALC, 3, RUN><<<nblk, BLOCK, smem, s>>>(plan_dev, D, nrhs, h, w); break;
+    default: k_apply_plain<T, REALC, 4, RUN><<<nblk, BLOCK, smem, s>>>(plan_dev, D, nrhs, h, w); break;
+  }
+}
+
+// run: modes per thread (2 when the last axis has even length, else 1). st1: the plan's StarParams when it is
+// star-1 and run is 2 (kind its coefficient kind), else null.
+template <typename T>
+void launch_apply_plain(const PlanDev* plan_dev, bool realc, int mc, int D, int nrhs, const cplx<T>* h, cplx<T>* w,
+                        int run, const StarParams* st1, int kind, cudaStream_t s) {
+  const size_t smem = (size_t)mc * sizeof(cplx<T>);
+  if (st1 && run == 2) {
+    const bool dg = kind == QP_COEF_DIAG;
+    if (realc) {
+      if (dg) plain_star_nr<T, true, 2>(nrhs, *st1, D, h, w, s);
+      else plain_star_nr<T, true, 1>(nrhs, *st1, D, h, w, s);
+    } else {
+      if (dg) plain_star_nr<T, false, 2>(nrhs, *st1, D, h, w, s);
+      else plain_star_nr<T, false, 1>(nrhs, *st1, D, h, w, s);
+    }
+  } else if (run == 2) {
+    if (realc) plain_nr<T, true, 2>(nrhs, plan_dev, D, h, w, smem, s);
+    else plain_nr<T, false, 2>(nrhs, plan_dev, D, h, w, smem, s);
+  } else {
+    if (realc) plain_nr<T, true, 1>(nrhs, plan_dev, D, h, w, smem, s);
+    else plain_nr<T, false, 1>(nrhs, plan_dev, D, h, w, smem, s);
+  }
+  count_launch();
+}
+
+}  // namespace qp

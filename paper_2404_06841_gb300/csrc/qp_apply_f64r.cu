@@ -1,0 +1,9 @@
+// Instantiations of the taps-backend apply kernels (qp_apply.cuh): FP64 batch apply with the true-residual epilogue.
+#include "qp_apply.cuh"
+
+namespace qp {
+
+template void apply_launch_real<double, EPI_RESIDUAL>(bool, int, const BatchDev&, int, int, unsigned long long, int, size_t,
+                                              const StarParams*, int, cudaStream_t);
+
+}  // namespace qp

@@ -77,6 +77,26 @@ inline FastDiv make_fastdiv(uint32_t d) {
   return FastDiv{d, (uint32_t)m, p};
 }
 
+// Everything the star-1 stencil reads besides the vectors: the geometry, P, and the coefficients of the mean
+// tap and of the taps m = +e_j, m = -e_j of every axis, at fixed offsets. A kernel that serves one plan takes it
+// by value as a kernel parameter (read from the constant bank, so that the stencil's only L1 traffic is the
+// vectors); a kernel over several plans copies it to shared memory.
+struct alignas(16) StarParams {
+  double2 c64[MAXN][2][MAXD];   // [axis j][0: m = +e_j, 1: m = -e_j][component]
+  double2 c064[MAXD];           // the mean tap
+  double P64[MAXD][MAXN];
+  float2 c32[MAXN][2][MAXD];
+  float2 c032[MAXD];
+  float P32[MAXD][MAXN];
+  FastDiv div[MAXN];
+  int N[MAXN], stride[MAXN];
+  int woff[MAXN];               // (N_j - 1) stride_j
+  int half[MAXN];               // ceil(N_j / 2)
+  int has[MAXN];                // 1: the axis has the taps m = +-e_j
+  int n, d, pad_[2];
+};
+static_assert(sizeof(StarParams) % 16 == 0, "StarParams is copied to shared memory in 16-byte words");
+
 // Device description of one plan's geometry and (for the taps backend) its taps, sorted as
 // [mean tap][star taps of axis 0] .. [star taps of axis n-1][taps with several nonzero axes].
 struct alignas(16) PlanDev {
@@ -90,9 +110,58 @@ struct alignas(16) PlanDev {
   float P32[MAXD][MAXN];
   const double2* coef64;      // [ntaps][ncomp], sorted order
   const float2* coef32;
+  // star-1 form (star1 != 0): a scalar or diagonal coefficient with taps only at m = 0 and m = +-e_j, every
+  // axis with taps of length >= 2; its stencil data in "star" (device)
+  int star1, pad_star;
+  const StarParams* star;
   signed char m[MAXT][MAXN];  // sorted tap modes
 };
 static_assert(sizeof(PlanDev) % 16 == 0, "PlanDev is copied to shared memory in 16-byte words");
+
+// Sets PlanDev.star1 from the sorted taps (m, star_begin, N, stride, kind, backend must be set) and, for a
+// star-1 plan, fills sp from the geometry and the sorted tap values c64 / c32 ([ntaps][ncomp]).
+inline void make_star(PlanDev& pd, const double2* c64, const float2* c32, StarParams& sp) {
+  pd.star1 = 0;
+  sp = StarParams{};
+  if (pd.backend != QP_BACKEND_TAPS || pd.star_begin[pd.n] != pd.ntaps) return;   // multi-axis taps
+  if (pd.kind != QP_COEF_SCALAR && pd.kind != QP_COEF_DIAG) return;
+  const int nc = pd.ncomp;
+  for (int j = 0; j < pd.n; ++j) {
+    int tp = -1, tm = -1;
+    for (int t = pd.star_begin[j]; t < pd.star_begin[j + 1]; ++t) {
+      if (pd.m[t][j] == 1 && tp < 0) tp = t;
+      else if (pd.m[t][j] == -1 && tm < 0) tm = t;
+      else return;                                   // |m_j| > 1 or a repeated mode
+    }
+    if ((tp < 0) != (tm < 0)) return;
+    if (tp >= 0 && pd.N[j] < 2) return;
+    sp.has[j] = tp >= 0 ? 1 : 0;
+    for (int q = 0; q < nc && tp >= 0; ++q) {
+      sp.c64[j][0][q] = c64[tp * nc + q];
+      sp.c64[j][1][q] = c64[tm * nc + q];
+      sp.c32[j][0][q] = c32[tp * nc + q];
+      sp.c32[j][1][q] = c32[tm * nc + q];
+    }
+  }
+  for (int q = 0; q < nc; ++q) {
+    sp.c064[q] = c64[q];
+    sp.c032[q] = c32[q];
+  }
+  for (int j = 0; j < MAXN; ++j) {
+    sp.N[j] = pd.N[j];
+    sp.stride[j] = pd.stride[j];
+    sp.div[j] = pd.div[j];
+    sp.woff[j] = (pd.N[j] - 1) * pd.stride[j];
+    sp.half[j] = (pd.N[j] + 1) / 2;
+    for (int a = 0; a < MAXD; ++a) {
+      sp.P64[a][j] = pd.P[a][j];
+      sp.P32[a][j] = pd.P32[a][j];
+    }
+  }
+  sp.n = pd.n;
+  sp.d = pd.d;
+  pd.star1 = 1;
+}
 
 // One solve unit: a plan and its nrhs right-hand sides (contiguous nrhs x D vectors).
 struct UnitDev {
@@ -149,13 +218,14 @@ enum { LEVEL_FP64 = 0, LEVEL_FP32 = 1 };   // which vector set a PCG kernel work
 // (refinement) bookkeeping. cond (0 = none): the graph conditional of the loop this apply belongs to; it is
 // set to 0 by the call that completes the count of finished right-hand sides.
 // realc: every taps plan in the batch has real tap values; mc: largest ntaps * ncomp over its taps plans.
-// maxr: the largest nrhs of the batch's units.
+// maxr: the largest nrhs of the batch's units. st1: for a batch of one star-1 unit with an even last axis, its
+// StarParams (host memory, passed by value), else null; kind: that unit's coefficient kind.
 void launch_apply(const BatchDev& b, bool realc, int mc, int maxr, int level, int epi, int refine,
-                  unsigned long long cond, int nblk, cudaStream_t s);
-// Standalone apply of one plan: w = Q h for nrhs vectors (no reductions).
+                  unsigned long long cond, int nblk, const StarParams* st1, int kind, cudaStream_t s);
+// Standalone apply of one plan: w = Q h for nrhs vectors (no reductions); st1, kind as launch_apply.
 template <typename T>
 void launch_apply_plain(const PlanDev* plan_dev, bool realc, int mc, int D, int nrhs, const cplx<T>* h, cplx<T>* w,
-                        int run, cudaStream_t s);
+                        int run, const StarParams* st1, int kind, cudaStream_t s);
 void launch_diag(const PlanDev* plan_dev, int mc, int D, double* jac, double* frob, float* jac32, float* frob32,
                  double* partials, unsigned* counter, double* out, int nblk, cudaStream_t s);
 void launch_rhs_taps(const PlanDev* plan_dev, int mc, int j0, int nrhs, int D, double2* F, cudaStream_t s);
@@ -190,10 +260,13 @@ struct PersistArgs {
   int mode;            // QP_MODE_FP64 or QP_MODE_FP32_REFINE
   int warm;            // start from the U held in the plan (else U = 0)
   unsigned long long timeout_ns;
+  StarParams star;     // the unit's star-1 stencil data (kernels with sk != 0)
 };
 size_t persistent_smem(int coef_count);
-int persistent_capacity(bool realc, int nr, size_t smem);
-void launch_persistent(const BatchDev& b, bool realc, int nr, int mode, bool warm, unsigned* bar, int* err,
-                       double timeout_s, int grid, size_t smem, cudaStream_t s);
+// sk: 0 the plan's stencil from shared memory; 1 / 2 a star-1 plan with a scalar / diagonal coefficient (its
+// StarParams st passed by value).
+int persistent_capacity(bool realc, int nr, int sk, size_t smem);
+void launch_persistent(const BatchDev& b, bool realc, int nr, int sk, const StarParams* st, int mode, bool warm,
+                       unsigned* bar, int* err, double timeout_s, int grid, size_t smem, cudaStream_t s);
 
 }  // namespace qp

@@ -69,6 +69,7 @@ struct HostTaps {
   PlanDev pd;
   double2 c64[MAXT * 6];
   float2 c32[MAXT * 6];
+  StarParams star;
   bool real = true;
 };
 
@@ -192,6 +193,7 @@ void build_host(int d, int n, const double* P, const int* N, const qp_coeff* c, 
   }
   pd.ntaps = G;
   pd.real_coef = ht.real ? 1 : 0;
+  make_star(pd, ht.c64, ht.c32, ht.star);
 }
 
 }  // namespace
@@ -205,6 +207,7 @@ extern "C" qp_status qp_pcg_solve_taps_static(int d, int n, const double* P, con
                                               qp_solve_info* info, void* stream) {
   try {
     if (!F || !U || !opts) raise(QP_ERR_INVALID_ARG, "F, U and opts must be non-null");
+    if (((uintptr_t)F | (uintptr_t)U) & 15u) raise(QP_ERR_INVALID_ARG, "F and U must be 16-byte aligned");
     if (nrhs < 1 || nrhs > MAXR) raise(QP_ERR_INVALID_ARG, "nrhs must be 1..4");
     if (opts->mode != QP_MODE_FP64) raise(QP_ERR_INVALID_ARG, "qp_pcg_solve_taps_static runs the FP64 mode only");
     if (!(opts->tol >= 0.0) || opts->maxit < 1) raise(QP_ERR_INVALID_ARG, "tol must be >= 0 and maxit >= 1");
@@ -223,6 +226,7 @@ extern "C" qp_status qp_pcg_solve_taps_static(int d, int n, const double* P, con
     // carve the static scratch (size checks before any device work)
     Carve cv{static_scratch_address()};
     PlanDev* d_pd = cv.take<PlanDev>(1);
+    StarParams* d_star = cv.take<StarParams>(1);
     double2* d_c64 = cv.take<double2>((size_t)G * nc);
     float2* d_c32 = cv.take<float2>((size_t)G * nc);
     double* jac64 = cv.take<double>(D);
@@ -244,7 +248,9 @@ extern "C" qp_status qp_pcg_solve_taps_static(int d, int n, const double* P, con
     CK(cudaMemsetAsync(st, 0, MAXR * sizeof(RhsSt), s));
     ht.pd.coef64 = d_c64;
     ht.pd.coef32 = d_c32;
+    ht.pd.star = ht.pd.star1 ? d_star : nullptr;
     CK(cudaMemcpyAsync(d_pd, &ht.pd, sizeof(PlanDev), cudaMemcpyHostToDevice, s));
+    if (ht.pd.star1) CK(cudaMemcpyAsync(d_star, &ht.star, sizeof(StarParams), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(d_c64, ht.c64, (size_t)G * nc * sizeof(double2), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(d_c32, ht.c32, (size_t)G * nc * sizeof(float2), cudaMemcpyHostToDevice, s));
     launch_diag(d_pd, G * nc, D, jac64, frob64, jac32, frob32, partials, counters + 2, small, nblk_diag, s);
@@ -295,8 +301,9 @@ extern "C" qp_status qp_pcg_solve_taps_static(int d, int n, const double* P, con
 
     // warm start from U: w = Q U, r = F - w, then Algorithm 2 with the host polling the done count
     const bool realc = ht.real;
+    const StarParams* st1 = (ht.pd.star1 && run == 2) ? &ht.star : nullptr;   // passed by value to the kernels
     launch_level_reset(bd, 0, s);
-    launch_apply(bd, realc, G * nc, nrhs, LEVEL_FP64, EPI_NONE, false, 0, nchunks, s);
+    launch_apply(bd, realc, G * nc, nrhs, LEVEL_FP64, EPI_NONE, false, 0, nchunks, st1, ht.pd.kind, s);
     launch_pcg_init(bd, nrhs, LEVEL_FP64, true, 0, nchunks, s);
     CK_LAUNCH();
     int done = 0, launched = 0, burst = 4;
@@ -306,7 +313,7 @@ extern "C" qp_status qp_pcg_solve_taps_static(int d, int n, const double* P, con
       if (done >= nrhs) break;
       if (launched > opts->maxit + 64) raise(QP_ERR_CUDA, "PCG loop exceeded its cap without the device count");
       for (int i = 0; i < burst; ++i) {
-        launch_apply(bd, realc, G * nc, nrhs, LEVEL_FP64, EPI_DOT_HW, false, 0, nchunks, s);
+        launch_apply(bd, realc, G * nc, nrhs, LEVEL_FP64, EPI_DOT_HW, false, 0, nchunks, st1, ht.pd.kind, s);
         launch_pcg_update(bd, nrhs, LEVEL_FP64, 0, nchunks, s);
         launch_pcg_hupdate(bd, nrhs, LEVEL_FP64, nchunks, s);
       }
@@ -315,7 +322,7 @@ extern "C" qp_status qp_pcg_solve_taps_static(int d, int n, const double* P, con
       burst = std::min(burst * 2, 32);
     }
     // FP64 true residual, then U(k = 0) = 0
-    launch_apply(bd, realc, G * nc, nrhs, LEVEL_FP64, EPI_RESIDUAL, false, 0, nchunks, s);
+    launch_apply(bd, realc, G * nc, nrhs, LEVEL_FP64, EPI_RESIDUAL, false, 0, nchunks, st1, ht.pd.kind, s);
     CK_LAUNCH();
     for (int k = 0; k < nrhs; ++k)
       CK(cudaMemsetAsync(static_cast<double2*>(U) + (size_t)k * D, 0, sizeof(double2), s));

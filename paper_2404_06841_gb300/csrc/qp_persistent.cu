@@ -8,10 +8,22 @@ const void* persistent_kernel_nr1(bool realc);
 const void* persistent_kernel_nr2(bool realc);
 const void* persistent_kernel_nr3(bool realc);
 const void* persistent_kernel_nr4(bool realc);
+const void* persistent_star_kernel_nr1(bool realc, int sk);
+const void* persistent_star_kernel_nr2(bool realc, int sk);
+const void* persistent_star_kernel_nr3(bool realc, int sk);
+const void* persistent_star_kernel_nr4(bool realc, int sk);
 
 namespace {
 
-const void* pick(bool realc, int nr) {
+const void* pick(bool realc, int nr, int sk) {
+  if (sk != 0) {
+    switch (nr) {
+      case 1: return persistent_star_kernel_nr1(realc, sk);
+      case 2: return persistent_star_kernel_nr2(realc, sk);
+      case 3: return persistent_star_kernel_nr3(realc, sk);
+      default: return persistent_star_kernel_nr4(realc, sk);
+    }
+  }
   switch (nr) {
     case 1: return persistent_kernel_nr1(realc);
     case 2: return persistent_kernel_nr2(realc);
@@ -25,8 +37,8 @@ const void* pick(bool realc, int nr) {
 size_t persistent_smem(int coef_count) { return (size_t)coef_count * (sizeof(double2) + sizeof(float2)); }
 
 // Largest co-resident grid of the persistent solve for this instantiation (0: no cooperative launch).
-int persistent_capacity(bool realc, int nr, size_t smem) {
-  const void* fn = pick(realc, nr);
+int persistent_capacity(bool realc, int nr, int sk, size_t smem) {
+  const void* fn = pick(realc, nr, sk);
   int dev = 0, coop = 0, sms = 0, per = 0;
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
@@ -38,10 +50,11 @@ int persistent_capacity(bool realc, int nr, size_t smem) {
 }
 
 // Launches the persistent solve of one unit (b.single). bar (2 unsigned) and err (1 int) are device words
-// zeroed here on the stream; grid must not exceed persistent_capacity.
-void launch_persistent(const BatchDev& b, bool realc, int nr, int mode, bool warm, unsigned* bar, int* err,
-                       double timeout_s, int grid, size_t smem, cudaStream_t s) {
+// zeroed here on the stream; grid must not exceed persistent_capacity (of the same realc, nr, sk).
+void launch_persistent(const BatchDev& b, bool realc, int nr, int sk, const StarParams* st, int mode, bool warm,
+                       unsigned* bar, int* err, double timeout_s, int grid, size_t smem, cudaStream_t s) {
   PersistArgs a;
+  a.star = (sk != 0 && st) ? *st : StarParams{};
   a.b = b;
   a.bar = bar;
   a.err = err;
@@ -51,7 +64,7 @@ void launch_persistent(const BatchDev& b, bool realc, int nr, int mode, bool war
   CK(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
   CK(cudaMemsetAsync(err, 0, sizeof(int), s));
   void* args[] = {&a};
-  CK(cudaLaunchCooperativeKernel(pick(realc, nr), dim3(grid), dim3(BLOCK), args, smem, s));
+  CK(cudaLaunchCooperativeKernel(pick(realc, nr, sk), dim3(grid), dim3(BLOCK), args, smem, s));
   count_launch();
 }
 

@@ -5,8 +5,8 @@
 namespace qp {
 
 const void* persistent_kernel_nr1(bool realc) {
-  return realc ? reinterpret_cast<const void*>(&k_pcg_persistent<true, 1>)
-               : reinterpret_cast<const void*>(&k_pcg_persistent<false, 1>);
+  return realc ? reinterpret_cast<const void*>(&k_pcg_persistent<true, 1, 0>)
+               : reinterpret_cast<const void*>(&k_pcg_persistent<false, 1, 0>);
 }
 
 }  // namespace qp

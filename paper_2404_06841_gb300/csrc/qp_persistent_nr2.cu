@@ -5,8 +5,8 @@
 namespace qp {
 
 const void* persistent_kernel_nr2(bool realc) {
-  return realc ? reinterpret_cast<const void*>(&k_pcg_persistent<true, 2>)
-               : reinterpret_cast<const void*>(&k_pcg_persistent<false, 2>);
+  return realc ? reinterpret_cast<const void*>(&k_pcg_persistent<true, 2, 0>)
+               : reinterpret_cast<const void*>(&k_pcg_persistent<false, 2, 0>);
 }
 
 }  // namespace qp

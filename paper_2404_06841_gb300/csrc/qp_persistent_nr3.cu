@@ -5,8 +5,8 @@
 namespace qp {
 
 const void* persistent_kernel_nr3(bool realc) {
-  return realc ? reinterpret_cast<const void*>(&k_pcg_persistent<true, 3>)
-               : reinterpret_cast<const void*>(&k_pcg_persistent<false, 3>);
+  return realc ? reinterpret_cast<const void*>(&k_pcg_persistent<true, 3, 0>)
+               : reinterpret_cast<const void*>(&k_pcg_persistent<false, 3, 0>);
 }
 
 }  // namespace qp

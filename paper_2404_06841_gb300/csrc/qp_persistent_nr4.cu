@@ -5,8 +5,8 @@
 namespace qp {
 
 const void* persistent_kernel_nr4(bool realc) {
-  return realc ? reinterpret_cast<const void*>(&k_pcg_persistent<true, 4>)
-               : reinterpret_cast<const void*>(&k_pcg_persistent<false, 4>);
+  return realc ? reinterpret_cast<const void*>(&k_pcg_persistent<true, 4, 0>)
+               : reinterpret_cast<const void*>(&k_pcg_persistent<false, 4, 0>);
 }
 
 }  // namespace qp

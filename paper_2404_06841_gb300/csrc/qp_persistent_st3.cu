@@ -1,0 +1,15 @@
+// Instantiations of the persistent PCG solve of a star-1 plan (stencil data as a kernel parameter) for 3
+// right-hand sides: sk = 1 scalar, 2 diagonal coefficient.
+#include "qp_persistent.cuh"
+
+namespace qp {
+
+const void* persistent_star_kernel_nr3(bool realc, int sk) {
+  if (sk == 2)
+    return realc ? reinterpret_cast<const void*>(&k_pcg_persistent<true, 3, 2>)
+                 : reinterpret_cast<const void*>(&k_pcg_persistent<false, 3, 2>);
+  return realc ? reinterpret_cast<const void*>(&k_pcg_persistent<true, 3, 1>)
+               : reinterpret_cast<const void*>(&k_pcg_persistent<false, 3, 1>);
+}
+
+}  // namespace qp

@@ -29,13 +29,26 @@ __device__ __forceinline__ void ld_run(const cplx<T>* p, cplx<T> (&v)[RUN]) {
 }
 
 
-template <typename T>
+// The block's shared copy of the plan's StarParams (kernels that serve several plans).
+__device__ __forceinline__ StarParams& star_smem() {
+  __shared__ StarParams s_star;
+  return s_star;
+}
+
+// Copies the plan description and its coefficient table (precision T) to shared memory; STAR: also the
+// plan's StarParams (star-1 plans), which the stencil kernels read through star_smem().
+template <typename T, bool STAR = false>
 __device__ __forceinline__ void load_plan(const PlanDev* src, PlanDev& dst, cplx<T>* coef) {
   __syncthreads();
   const int4* s = reinterpret_cast<const int4*>(src);
   int4* d = reinterpret_cast<int4*>(&dst);
   for (int i = threadIdx.x; i < (int)(sizeof(PlanDev) / sizeof(int4)); i += BLOCK) d[i] = s[i];
   __syncthreads();
+  if (STAR && dst.star1) {
+    const int4* ss = reinterpret_cast<const int4*>(dst.star);
+    int4* sd = reinterpret_cast<int4*>(&star_smem());
+    for (int i = threadIdx.x; i < (int)(sizeof(StarParams) / sizeof(int4)); i += BLOCK) sd[i] = ss[i];
+  }
   const int nc = dst.ntaps * dst.ncomp;
   if (sizeof(T) == 8) {
     const double2* c = dst.coef64;
@@ -58,14 +71,242 @@ __device__ __forceinline__ void mac(cplx<T>& acc, const cplx<T>& c, const cplx<T
   }
 }
 
-// acc[s][r] = (Q h_r)(e0 + s), s < RUN: the whole tap sum at RUN consecutive modes of one row of the last
+// ---- star-1 stencils (PlanDev.star1: scalar or diagonal coefficient, taps at m = 0 and m = +-e_j only)
+//
+// The neighbour of the tap m = +-e_j is k -+ e_j, with lambda(k -+ e_j) = lambda(k) + dk P_j; the weight
+// lambda(k)^T C_t lambda(k -+ e_j) is then
+//   scalar:    c_t (q + dk r_j),                 q = |lambda|^2,   r_j = lambda . P_j
+//   diagonal:  sum_a c_t,a (q_a + dk r_a,j),     q_a = lambda_a^2, r_a,j = lambda_a P_a,j
+// with q formed once per mode and r once per axis. dk is -+1 except across the frequency wrap between
+// k_j = ceil(N_j/2) - 1 and ceil(N_j/2) - N_j, and the neighbour's storage index steps by -+stride_j except
+// across the storage wrap at index 0 / N_j - 1: each exception is one compare and one select. Runs of two
+// modes along the last axis (even length): its own taps read the run's two values and one neighbour each side.
+// Everything but the vectors comes from a StarParams (kernel parameter or shared memory) at fixed offsets.
+
+template <typename T> __device__ __forceinline__ T sp_P(const StarParams& s, int a, int j);
+template <> __device__ __forceinline__ double sp_P<double>(const StarParams& s, int a, int j) { return s.P64[a][j]; }
+template <> __device__ __forceinline__ float sp_P<float>(const StarParams& s, int a, int j) { return s.P32[a][j]; }
+// component a of the tap m = +e_j (sg = 0) or m = -e_j (sg = 1); sp_c0: of the mean tap
+template <typename T> __device__ __forceinline__ cplx<T> sp_c(const StarParams& s, int j, int sg, int a);
+template <> __device__ __forceinline__ double2 sp_c<double>(const StarParams& s, int j, int sg, int a) {
+  return s.c64[j][sg][a];
+}
+template <> __device__ __forceinline__ float2 sp_c<float>(const StarParams& s, int j, int sg, int a) {
+  return s.c32[j][sg][a];
+}
+template <typename T> __device__ __forceinline__ cplx<T> sp_c0(const StarParams& s, int a);
+template <> __device__ __forceinline__ double2 sp_c0<double>(const StarParams& s, int a) { return s.c064[a]; }
+template <> __device__ __forceinline__ float2 sp_c0<float>(const StarParams& s, int a) { return s.c032[a]; }
+
+template <typename T, bool REALC, int NR, bool RO, bool DIAGK>
+__device__ __forceinline__ void apply_run_star(const StarParams& sp, int e0, const cplx<T>* h, int D, int nrhs,
+                                               cplx<T> (&acc)[2][NR]) {
+  constexpr int NQ = DIAGK ? MAXD : 1;   // weight terms per mode: q_a (diagonal) or q (scalar)
+  const int d = sp.d, n = sp.n, jl = n - 1, Nl = sp.N[jl];
+  // storage digits and signed modes of the run's first mode
+  int ib[MAXN], k[MAXN];
+  {
+    uint32_t x = (uint32_t)e0;
+#pragma unroll
+    for (int j = MAXN - 1; j >= 0; --j) {
+      if (j < n) {
+        const uint32_t qd = fdiv(x, sp.div[j]);
+        ib[j] = (int)(x - qd * (uint32_t)sp.N[j]);
+        k[j] = (2 * ib[j] < sp.N[j]) ? ib[j] : ib[j] - sp.N[j];
+        x = qd;
+      } else {
+        ib[j] = 0;
+        k[j] = 0;
+      }
+    }
+  }
+  int ibl = 0, kl0 = 0;
+#pragma unroll
+  for (int j = 0; j < MAXN; ++j)
+    if (j == jl) {
+      ibl = ib[j];
+      kl0 = k[j];
+    }
+  const cplx<T>* hr[NR];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) hr[r] = h + (size_t)r * D;
+  T lk[2][MAXD];
+  {
+    T lr[MAXD];
+#pragma unroll
+    for (int a = 0; a < MAXD; ++a) {
+      lr[a] = T(0);
+#pragma unroll
+      for (int j = 0; j < MAXN - 1; ++j)
+        if (a < d && j < jl) lr[a] = fma(sp_P<T>(sp, a, j), (T)k[j], lr[a]);
+    }
+    const int kl1 = (2 * (ibl + 1) < Nl) ? ibl + 1 : ibl + 1 - Nl;
+#pragma unroll
+    for (int a = 0; a < MAXD; ++a) {
+      const T pl = sp_P<T>(sp, a, jl);
+      lk[0][a] = (a < d) ? fma(pl, (T)kl0, lr[a]) : T(0);
+      lk[1][a] = (a < d) ? fma(pl, (T)kl1, lr[a]) : T(0);
+    }
+  }
+  T q[2][NQ];
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    if (DIAGK) {
+#pragma unroll
+      for (int a = 0; a < NQ; ++a) q[s][a] = lk[s][a] * lk[s][a];
+    } else {
+      q[s][0] = T(0);
+#pragma unroll
+      for (int a = 0; a < MAXD; ++a)
+        if (a < d) q[s][0] = fma(lk[s][a], lk[s][a], q[s][0]);
+    }
+  }
+  auto rterms = [&](int j, T (&rt)[2][NQ]) {
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      if (DIAGK) {
+#pragma unroll
+        for (int a = 0; a < NQ; ++a) rt[s][a] = lk[s][a] * sp_P<T>(sp, a, j);
+      } else {
+        rt[s][0] = T(0);
+#pragma unroll
+        for (int a = 0; a < MAXD; ++a)
+          if (a < d) rt[s][0] = fma(lk[s][a], sp_P<T>(sp, a, j), rt[s][0]);
+      }
+    }
+  };
+  // weight of the tap m = +e_j (sg = 0) or -e_j (sg = 1) at one mode
+  auto wgt = [&](int j, int sg, T dk, const T (&qs)[NQ], const T (&rs)[NQ]) {
+    cplx<T> c;
+    if (DIAGK) {
+      c = mk<T>(0, 0);
+#pragma unroll
+      for (int a = 0; a < MAXD; ++a) {
+        if (a < d) {
+          const cplx<T> ca = sp_c<T>(sp, j, sg, a);
+          const T x = fma(dk, rs[a], qs[a]);
+          c.x = fma(ca.x, x, c.x);
+          if (!REALC) c.y = fma(ca.y, x, c.y);
+        }
+      }
+    } else {
+      const cplx<T> c0 = sp_c<T>(sp, j, sg, 0);
+      const T w = fma(dk, rs[0], qs[0]);
+      c.x = c0.x * w;
+      c.y = REALC ? T(0) : c0.y * w;
+    }
+    return c;
+  };
+  // mean tap and the last axis' taps, from the run's own values and one neighbour on each side
+  {
+    cplx<T> c0[2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      if (DIAGK) {
+        c0[s] = mk<T>(0, 0);
+#pragma unroll
+        for (int a = 0; a < MAXD; ++a) {
+          if (a < d) {
+            const cplx<T> ca = sp_c0<T>(sp, a);
+            c0[s].x = fma(ca.x, q[s][a], c0[s].x);
+            if (!REALC) c0[s].y = fma(ca.y, q[s][a], c0[s].y);
+          }
+        }
+      } else {
+        const cplx<T> ca = sp_c0<T>(sp, 0);
+        c0[s].x = ca.x * q[s][0];
+        c0[s].y = REALC ? T(0) : ca.y * q[s][0];
+      }
+    }
+    const bool has = sp.has[jl] != 0;
+    cplx<T> wp[2], wm[2];
+    int il = e0, ir = e0;
+    if (has) {
+      T rt[2][NQ];
+      rterms(jl, rt);
+      const int hl = sp.half[jl];
+      const T dp0 = (ibl == hl) ? T(Nl - 1) : T(-1);
+      const T dp1 = (ibl + 1 == hl) ? T(Nl - 1) : T(-1);
+      const T dm0 = (ibl == hl - 1) ? T(1 - Nl) : T(1);
+      const T dm1 = (ibl + 1 == hl - 1) ? T(1 - Nl) : T(1);
+      wp[0] = wgt(jl, 0, dp0, q[0], rt[0]);
+      wp[1] = wgt(jl, 0, dp1, q[1], rt[1]);
+      wm[0] = wgt(jl, 1, dm0, q[0], rt[0]);
+      wm[1] = wgt(jl, 1, dm1, q[1], rt[1]);
+      il = e0 + ((ibl == 0) ? Nl - 1 : -1);       // k - e_l of the run's first mode
+      ir = e0 + ((ibl + 2 == Nl) ? 2 - Nl : 2);   // k + e_l of its second mode
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      if (r < nrhs) {
+        cplx<T> hv[2];
+        ld_run<RO, T, 2>(hr[r] + e0, hv);
+        cplx<T> a0 = mk<T>(0, 0), a1 = mk<T>(0, 0);
+        mac<T, REALC>(a0, c0[0], hv[0]);
+        mac<T, REALC>(a1, c0[1], hv[1]);
+        if (has) {
+          mac<T, REALC>(a0, wm[0], hv[1]);
+          mac<T, REALC>(a1, wp[1], hv[0]);
+          mac<T, REALC>(a0, wp[0], ldh<RO>(hr[r] + il));
+          mac<T, REALC>(a1, wm[1], ldh<RO>(hr[r] + ir));
+        }
+        acc[0][r] = a0;
+        acc[1][r] = a1;
+      } else {
+        acc[0][r] = mk<T>(0, 0);
+        acc[1][r] = mk<T>(0, 0);
+      }
+    }
+  }
+  // the other axes: one neighbour offset and one dk per tap for the whole run
+#pragma unroll
+  for (int j = 0; j < MAXN - 1; ++j) {
+    if (j < jl && sp.has[j]) {
+      const int Nj = sp.N[j], ibj = ib[j], hj = sp.half[j];
+      T rt[2][NQ];
+      rterms(j, rt);
+      const int ep = e0 + ((ibj == 0) ? sp.woff[j] : -sp.stride[j]);        // k - e_j (tap m = +e_j)
+      const int em = e0 + ((ibj == Nj - 1) ? -sp.woff[j] : sp.stride[j]);   // k + e_j (tap m = -e_j)
+      const T dp = (ibj == hj) ? T(Nj - 1) : T(-1);
+      const T dm = (ibj == hj - 1) ? T(1 - Nj) : T(1);
+      cplx<T> wp[2], wm[2];
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        wp[s] = wgt(j, 0, dp, q[s], rt[s]);
+        wm[s] = wgt(j, 1, dm, q[s], rt[s]);
+      }
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        if (r < nrhs) {
+          cplx<T> hv[2];
+          ld_run<RO, T, 2>(hr[r] + ep, hv);
+          mac<T, REALC>(acc[0][r], wp[0], hv[0]);
+          mac<T, REALC>(acc[1][r], wp[1], hv[1]);
+          ld_run<RO, T, 2>(hr[r] + em, hv);
+          mac<T, REALC>(acc[0][r], wm[0], hv[0]);
+          mac<T, REALC>(acc[1][r], wm[1], hv[1]);
+        }
+      }
+    }
+  }
+}
+
+// acc[s][r] = (Q h_r)(e0 + s), s < RUN: the whole tap sum at RUN consecutive modes (STAR: a star-1 plan takes the
+// star-1 stencil from the block's shared StarParams; kernels that never see one leave it out) of one row of the last
 // axis (e0 a multiple of RUN, RUN dividing N_{n-1}). Everything that depends only on the row is done once per
 // run: the digits of e0, lambda over the other axes, and for every tap along another axis its wrapped offset and
 // its mode step dk; that tap then reads RUN consecutive entries of h. The weights are formed per mode:
 //   scalar:  c_t (|lambda|^2 + dk lambda.P_j),   otherwise  lambda^T C_t (lambda + dk P_j)   (star tap on axis j).
-template <typename T, bool REALC, int NR, int RUN, bool RO = true>
+template <typename T, bool REALC, int NR, int RUN, bool RO = true, bool STAR = true>
 __device__ __forceinline__ void apply_run(const PlanDev& p, const cplx<T>* __restrict__ sc, int e0,
                                           const cplx<T>* h, int D, int nrhs, cplx<T> (&acc)[RUN][NR]) {
+  if constexpr (RUN == 2 && STAR) {
+    if (p.star1) {   // the block's shared StarParams (load_plan<T, true>)
+      if (p.kind == QP_COEF_DIAG) apply_run_star<T, REALC, NR, RO, true>(star_smem(), e0, h, D, nrhs, acc);
+      else apply_run_star<T, REALC, NR, RO, false>(star_smem(), e0, h, D, nrhs, acc);
+      return;
+    }
+  }
   int ib[MAXN], k[MAXN];
   mode_digits(p, e0, ib, k);
   const int d = p.d, kind = p.kind, nc = p.ncomp, n = p.n;

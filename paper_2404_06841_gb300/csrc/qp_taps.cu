@@ -12,243 +12,33 @@
 
 namespace qp {
 
-// ------------------------------------------------------------------------------------------------ batch apply
+// ------------------------------------------------------------------------------------------------ apply launches
 
-// One chunk [base, end) of a unit: dst = Q src with the epilogue, per-thread partials into vt. Thread t takes
-// runs of RUN consecutive modes: e0 = base + RUN t, base + RUN (t + BLOCK), ...
-template <typename T, int EPI, bool REALC, int NR, int RUN, int NV>
-__device__ __forceinline__ void apply_chunk(const PlanDev& sp, const cplx<T>* scoef, int base, int end, int D,
-                                            int nrhs, int refine, bool fft_unit, const cplx<T>* src, cplx<T>* dst,
-                                            const cplx<T>* F, T (&vt)[NV]) {
-  for (int e0 = base + RUN * threadIdx.x; e0 < end; e0 += RUN * BLOCK) {
-    cplx<T> acc[RUN][NR];
-    if (EPI == EPI_RESIDUAL && refine == REFINE_ZERO_U) {
-#pragma unroll
-      for (int s = 0; s < RUN; ++s)
-#pragma unroll
-        for (int r = 0; r < NR; ++r) acc[s][r] = mk<T>(0, 0);
-    } else if (fft_unit) {
-#pragma unroll
-      for (int s = 0; s < RUN; ++s)
-#pragma unroll
-        for (int r = 0; r < NR; ++r) acc[s][r] = (r < nrhs) ? dst[(size_t)r * D + e0 + s] : mk<T>(0, 0);
-    } else {
-      apply_run<T, REALC, NR, RUN>(sp, scoef, e0, src, D, nrhs, acc);
-    }
-#pragma unroll
-    for (int s = 0; s < RUN; ++s) {
-      const int e = e0 + s;
-#pragma unroll
-      for (int r = 0; r < NR; ++r) {
-        if (r < nrhs) {
-          const size_t o = (size_t)r * D + e;
-          if (EPI == EPI_DOT_HW) {
-            if (!fft_unit) dst[o] = acc[s][r];
-            const cplx<T> hv = src[o];
-            vt[r] = fma(hv.x, acc[s][r].x, fma(hv.y, acc[s][r].y, vt[r]));
-          } else if (EPI == EPI_RESIDUAL) {
-            const cplx<T> f = F[o];
-            const cplx<T> res = (e == 0) ? mk<T>(0, 0) : mk<T>(f.x - acc[s][r].x, f.y - acc[s][r].y);
-            dst[o] = res;
-            vt[2 * r] = fma(res.x, res.x, fma(res.y, res.y, vt[2 * r]));
-            if (e != 0) vt[2 * r + 1] = fma(f.x, f.x, fma(f.y, f.y, vt[2 * r + 1]));
-          } else {
-            if (!fft_unit) dst[o] = acc[s][r];
-          }
-        }
-      }
-    }
-  }
-}
-
-template <typename T, int EPI, bool REALC, int NR>
-__global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 3) k_apply(BatchDev b, int level, int refine, unsigned long long cond) {
-  __shared__ __align__(16) PlanDev sp;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  cplx<T>* scoef = reinterpret_cast<cplx<T>*>(smraw);
-  const PlanDev* cur = nullptr;
-  for (int c = blockIdx.x; c < b.nchunks; c += gridDim.x) {
-    const int u = unit_of_chunk(b, c);
-    const UnitDev& un = unit_at(b, u);
-    RhsSt* st = b.st + (size_t)u * MAXR;
-    const int nrhs = un.nrhs;
-    // skip units with nothing left to do at this level (same decision for every chunk of the unit)
-    bool active = false;
-    for (int r = 0; r < nrhs; ++r) {
-      if (EPI == EPI_DOT_HW) active |= !ld_int(&st[r].done);
-      else if (EPI == EPI_RESIDUAL && refine) active |= !ld_int(&st[r].odone);
-      else active = true;
-    }
-    if (!active) continue;
-    if (un.plan != cur) {
-      cur = un.plan;
-      load_plan<T>(cur, sp, scoef);
-    }
-    const int D = un.D;
-    const cplx<T>* src;
-    cplx<T>* dst;
-    if (level == LEVEL_FP32) {
-      src = reinterpret_cast<const cplx<T>*>(un.h32);
-      dst = reinterpret_cast<cplx<T>*>(un.w32);
-    } else {
-      src = reinterpret_cast<const cplx<T>*>(EPI == EPI_DOT_HW ? (const double2*)un.h : (const double2*)un.U);
-      dst = reinterpret_cast<cplx<T>*>(un.w);
-    }
-    const cplx<T>* F = reinterpret_cast<const cplx<T>*>(un.F);
-    const bool fft_unit = (sp.backend == QP_BACKEND_FFT);
-    constexpr int NV = (EPI == EPI_RESIDUAL) ? 2 * NR : NR;   // reduced quantities: (h,w) or (|F-w|^2, |F|^2)
-    T vt[NV];                                                   // per-thread partials in the vector precision
-    double v[NV];
-#pragma unroll
-    for (int q = 0; q < NV; ++q) vt[q] = T(0);
-    const int base = (c - un.chunk0) * un.chunk;
-    const int end = min(base + un.chunk, D);
-    // the unit's own run length (so that its reduction order does not depend on the batch)
-    if (un.run == 2)
-      apply_chunk<T, EPI, REALC, NR, 2, NV>(sp, scoef, base, end, D, nrhs, refine, fft_unit, src, dst, F, vt);
-    else
-      apply_chunk<T, EPI, REALC, NR, 1, NV>(sp, scoef, base, end, D, nrhs, refine, fft_unit, src, dst, F, vt);
-    if (EPI == EPI_NONE) continue;
-    block_reduce_mixed<T, NV>(vt, v);
-    if (!chunk_arrive<NV>(b, c, u, v)) continue;
-    // this block completes unit u: finalize its right-hand sides
-    unit_sums<NV>(b, un, v);
-    for (int r = 0; r < nrhs && r < NR; ++r) {
-      const double s0 = (EPI == EPI_RESIDUAL) ? v[2 * r] : v[r];
-      const double s1 = (EPI == EPI_RESIDUAL) ? v[(2 * r + 1) % NV] : 0.0;
-      if (threadIdx.x == 0) {
-        RhsSt& x = st[r];
-        if (EPI == EPI_DOT_HW) {
-          if (!x.done) {
-            x.hw = s0;
-            if (!(s0 > 0.0) || !isfinite(s0)) {   // (h, Q h) <= 0 or NaN: breakdown
-              x.done = 1;
-              x.status = QP_ERR_BREAKDOWN;
-              count_done(b, 0, 1, cond);           // completing the count here ends the PCG loop
-            } else {
-              x.alpha = x.rz / s0;
-            }
-          }
-        } else if (!refine) {
-          x.orr = s0;
-          x.of2 = s1;
-        } else if (!x.odone) {
-          x.orr = s0;
-          x.of2 = s1;
-          x.outer += 1;
-          x.inner_total += x.iters;
-          const double rel = s1 > 0.0 ? sqrt(s0 / s1) : 0.0;
-          int od = 0, os = QP_ERR_NO_CONVERGENCE;
-          if (s1 == 0.0 || s0 <= b.otol2 * s1) {
-            od = 1;
-            os = QP_OK;
-          } else if (!isfinite(rel)) {
-            od = 1;
-            os = QP_ERR_BREAKDOWN;
-          } else if (rel > 0.9 * x.prev_rel || x.outer > b.max_outer || x.inner_total >= b.maxit) {
-            od = 1;   // stagnation or cap
-          }
-          x.prev_rel = rel;
-          x.inv_scale = sqrt(s0);
-          x.scale = s0 > 0.0 ? 1.0 / x.inv_scale : 0.0;
-          x.ostatus = os;
-          if (od) {
-            x.odone = 1;
-            count_done(b, 1, 1, cond);             // the right-hand side that completes the count ends the loop
-          }
-        }
-      }
-    }
-    if (threadIdx.x == 0) b.ucount[u] = 0;
-  }
-}
-
-template <typename T, int EPI, int NR>
-static void apply_launch_nr(bool realc, const BatchDev& b, int level, int refine, unsigned long long cond, int nblk,
-                            size_t smem, cudaStream_t s) {
-  if (realc) k_apply<T, EPI, true, NR><<<nblk, BLOCK, smem, s>>>(b, level, refine, cond);
-  else k_apply<T, EPI, false, NR><<<nblk, BLOCK, smem, s>>>(b, level, refine, cond);
-}
-
+// The apply kernels (qp_apply.cuh) are instantiated per vector precision and epilogue in qp_apply_*.cu.
 template <typename T, int EPI>
-static void apply_launch_real(bool realc, int maxr, const BatchDev& b, int level, int refine,
-                              unsigned long long cond, int nblk, size_t smem, cudaStream_t s) {
-  switch (maxr) {
-    case 1: apply_launch_nr<T, EPI, 1>(realc, b, level, refine, cond, nblk, smem, s); break;
-    case 2: apply_launch_nr<T, EPI, 2>(realc, b, level, refine, cond, nblk, smem, s); break;
-    case 3: apply_launch_nr<T, EPI, 3>(realc, b, level, refine, cond, nblk, smem, s); break;
-    default: apply_launch_nr<T, EPI, 4>(realc, b, level, refine, cond, nblk, smem, s); break;
-  }
-}
+void apply_launch_real(bool realc, int maxr, const BatchDev& b, int level, int refine, unsigned long long cond,
+                       int nblk, size_t smem, const StarParams* st1, int kind, cudaStream_t s);
 
 // realc: every taps plan of the batch has real tap values; mc: the largest ntaps * ncomp of its plans (sizes
 // the shared coefficient table); maxr: the largest nrhs of its units; refine: REFINE_* (the refinement
 // bookkeeping of the residual epilogue; REFINE_ZERO_U: the solutions are zero, so Q U = 0 is not computed).
-// Each unit's stencil runs (UnitDev.run) are its own.
+// Each unit's stencil runs (UnitDev.run) are its own. st1 (a single star-1 unit with an even last axis, else
+// null): its StarParams, passed to the kernel by value; kind: that unit's coefficient kind.
 void launch_apply(const BatchDev& b, bool realc, int mc, int maxr, int level, int epi, int refine,
-                  unsigned long long cond, int nblk, cudaStream_t s) {
+                  unsigned long long cond, int nblk, const StarParams* st1, int kind, cudaStream_t s) {
   if (level == LEVEL_FP32) {
     const size_t smem = (size_t)mc * sizeof(float2);
-    apply_launch_real<float, EPI_DOT_HW>(realc, maxr, b, level, refine, cond, nblk, smem, s);
+    apply_launch_real<float, EPI_DOT_HW>(realc, maxr, b, level, refine, cond, nblk, smem, st1, kind, s);
   } else {
     const size_t smem = (size_t)mc * sizeof(double2);
-    if (epi == EPI_DOT_HW) apply_launch_real<double, EPI_DOT_HW>(realc, maxr, b, level, refine, cond, nblk, smem, s);
+    if (epi == EPI_DOT_HW)
+      apply_launch_real<double, EPI_DOT_HW>(realc, maxr, b, level, refine, cond, nblk, smem, st1, kind, s);
     else if (epi == EPI_RESIDUAL)
-      apply_launch_real<double, EPI_RESIDUAL>(realc, maxr, b, level, refine, cond, nblk, smem, s);
-    else apply_launch_real<double, EPI_NONE>(realc, maxr, b, level, refine, cond, nblk, smem, s);
+      apply_launch_real<double, EPI_RESIDUAL>(realc, maxr, b, level, refine, cond, nblk, smem, st1, kind, s);
+    else apply_launch_real<double, EPI_NONE>(realc, maxr, b, level, refine, cond, nblk, smem, st1, kind, s);
   }
   count_launch();
 }
-
-// ------------------------------------------------------------------------------------------------ plain apply
-
-template <typename T, bool REALC, int NR, int RUN>
-__global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 3) k_apply_plain(const PlanDev* plan, int D, int nrhs,
-                                                                             const cplx<T>* h, cplx<T>* w) {
-  __shared__ __align__(16) PlanDev sp;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  cplx<T>* scoef = reinterpret_cast<cplx<T>*>(smraw);
-  load_plan<T>(plan, sp, scoef);
-  const int e0 = (blockIdx.x * BLOCK + threadIdx.x) * RUN;   // one run per thread: blocks sweep memory in order
-  if (e0 >= D) return;
-  cplx<T> acc[RUN][NR];
-  apply_run<T, REALC, NR, RUN>(sp, scoef, e0, h, D, nrhs, acc);
-#pragma unroll
-  for (int s = 0; s < RUN; ++s)
-#pragma unroll
-    for (int r = 0; r < NR; ++r)
-      if (r < nrhs) w[(size_t)r * D + e0 + s] = acc[s][r];
-}
-
-template <typename T, bool REALC, int RUN>
-static void plain_nr(int nrhs, const PlanDev* plan_dev, int D, const cplx<T>* h, cplx<T>* w, size_t smem,
-                     cudaStream_t s) {
-  const int nblk = (D / RUN + BLOCK - 1) / BLOCK;
-  switch (nrhs) {
-    case 1: k_apply_plain<T, REALC, 1, RUN><<<nblk, BLOCK, smem, s>>>(plan_dev, D, nrhs, h, w); break;
-    case 2: k_apply_plain<T, REALC, 2, RUN><<<nblk, BLOCK, smem, s>>>(plan_dev, D, nrhs, h, w); break;
-    case 3: k_apply_plain<T, REALC, 3, RUN><<<nblk, BLOCK, smem, s>>>(plan_dev, D, nrhs, h, w); break;
-    default: k_apply_plain<T, REALC, 4, RUN><<<nblk, BLOCK, smem, s>>>(plan_dev, D, nrhs, h, w); break;
-  }
-}
-
-// run: modes per thread (2 when the last axis has even length, else 1).
-template <typename T>
-void launch_apply_plain(const PlanDev* plan_dev, bool realc, int mc, int D, int nrhs, const cplx<T>* h, cplx<T>* w,
-                        int run, cudaStream_t s) {
-  const size_t smem = (size_t)mc * sizeof(cplx<T>);
-  if (run == 2) {
-    if (realc) plain_nr<T, true, 2>(nrhs, plan_dev, D, h, w, smem, s);
-    else plain_nr<T, false, 2>(nrhs, plan_dev, D, h, w, smem, s);
-  } else {
-    if (realc) plain_nr<T, true, 1>(nrhs, plan_dev, D, h, w, smem, s);
-    else plain_nr<T, false, 1>(nrhs, plan_dev, D, h, w, smem, s);
-  }
-  count_launch();
-}
-template void launch_apply_plain<double>(const PlanDev*, bool, int, int, int, const double2*, double2*, int,
-                                         cudaStream_t);
-template void launch_apply_plain<float>(const PlanDev*, bool, int, int, int, const float2*, float2*, int, cudaStream_t);
 
 // ------------------------------------------------------------------------------------------------ set-up kernels
 

@@ -337,6 +337,31 @@ def random_taps(d: int, n: int, kind: str, seed: int, radius: int = 1, nmodes: i
     return taps_from_dict(modes, n, nc)
 
 
+def random_star_instance(d: int, n: int, N, kind: str = "scalar", seed: int = 0, axes=None, real: bool = False,
+                         margin: float = 0.5, sigma: float = 0.3) -> Instance:
+    """Random instance whose taps sit only at m = 0 and m = +-e_j for j in ``axes`` (default: every axis);
+    ``real`` makes every tap value real (an even coefficient). Elliptic by the same Gershgorin mean as
+    random_taps."""
+    rng = np.random.default_rng(seed)
+    N = tuple(int(x) for x in ((N,) * n if np.isscalar(N) else N))
+    nc = ncomp(kind, d)
+    axes = list(range(n)) if axes is None else list(axes)
+    modes = {}
+    bound = 0.0
+    for j in axes:
+        s = sigma * rng.standard_normal(nc) + (0.0 if real else 1j * sigma * rng.standard_normal(nc))
+        e = [0] * n
+        e[j] = 1
+        _add_mode(modes, e, s, nc)
+        e[j] = -1
+        _add_mode(modes, e, np.conj(s), nc)
+        bound += 2.0 * float(np.abs(s).sum())
+    _add_mode(modes, (0,) * n, np.full(nc, margin + bound), nc)
+    k, v = taps_from_dict(modes, n, nc)
+    P = random_P(d, n, seed + 7919)
+    return Instance("star_d%dn%d_%s_s%d" % (d, n, kind, seed), P, N, Coefficient(kind, k, v))
+
+
 def random_instance(d: int, n: int, N, kind: str = "scalar", repr_: str = "taps", seed: int = 0,
                     P: np.ndarray | None = None, radius: int = 1, nmodes: int | None = None,
                     nonlinear: bool = False) -> Instance:

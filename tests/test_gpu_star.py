@@ -1,0 +1,109 @@
+"""Star-1 plans (scalar or diagonal coefficient, taps only at m = 0 and m = +-e_j) take the specialised stencil
+of the compressed mat-vec (Sec. 4.2): the weight lambda(k)^T C_t lambda(k -+ e_j) is formed from |lambda|^2 and
+lambda . P_j, and each axis wraps with one compare and one select. Checked against the oracle's wraparound
+convolution across the frequency wrap (k = ceil(N/2) - 1 <-> ceil(N/2) - N) and the storage wrap (axes of length
+2 and 3, odd lengths, axes without taps), in every execution form, batched beside other plans, and with its kernel
+parameter and shared-memory data sources giving bitwise the same iterates."""
+import numpy as np
+import pytest
+
+import qp_workloads as W
+from oracle import qp_oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qp():
+    import paper_2404_06841_gb300 as qp
+    assert torch.cuda.is_available()
+    return qp
+
+
+# (d, n, N, kind, real tap values, axes with taps); a tap needs |m_j| < N_j / 2, so axes of length 2 carry none
+CASES = [
+    (1, 2, (3, 4), "scalar", False, None),
+    (2, 3, (5, 3, 4), "diag", False, None),
+    (2, 4, (6, 7, 2, 8), "scalar", True, (0, 1, 3)),
+    (3, 6, (4, 3, 2, 5, 3, 6), "diag", False, (0, 1, 3, 4, 5)),
+    (3, 5, (9, 4, 6, 2, 10), "diag", True, (1, 2, 4)),
+    (2, 4, (6, 4, 6, 5), "diag", False, None),          # odd last axis: the general stencil, runs of one
+]
+
+
+def _inst(case, seed):
+    d, n, N, kind, real, axes = case
+    return W.random_star_instance(d, n, N, kind, seed=seed, axes=axes, real=real)
+
+
+def _rand(nrhs, N, seed):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal((nrhs,) + tuple(N)) + 1j * rng.standard_normal((nrhs,) + tuple(N))
+
+
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("nrhs", [1, 3])
+def test_star_apply_matches_oracle(qp, case, nrhs):
+    inst = _inst(case, 11)
+    plan = qp.plan_from_instance(inst, max_rhs=4)
+    h = _rand(nrhs, inst.N, 3)
+    op = O.Operator(inst)
+    ref = np.stack([op(h[r]) for r in range(nrhs)])
+    for prec, dt, tol in ((qp.QP_FP64, torch.complex128, 1e-13), (qp.QP_FP32, torch.complex64, 2e-6)):
+        ht = torch.from_numpy(h).to("cuda", dt)
+        wt = torch.empty_like(ht)
+        qp.qp_apply_stiffness(plan, ht, wt, prec)
+        err = np.abs(wt.cpu().numpy().astype(np.complex128) - ref).max() / np.abs(ref).max()
+        assert err <= tol, (prec, err)
+
+
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("mode", ["fp64", "refine"])
+def test_star_solve_forms_bitwise_and_oracle(qp, case, mode):
+    inst = _inst(case, 12)
+    m = qp.QP_MODE_FP64 if mode == "fp64" else qp.QP_MODE_FP32_REFINE
+    nrhs = 2
+    F = _rand(nrhs, inst.N, 5)
+    F.reshape(nrhs, -1)[:, 0] = 0
+    out = {}
+    for ex in (qp.QP_EXEC_PERSISTENT, qp.QP_EXEC_GRAPH, qp.QP_EXEC_DIRECT):
+        plan = qp.plan_from_instance(inst, max_rhs=nrhs, exec_mode=ex)
+        Ft = torch.from_numpy(F).cuda()
+        Ut = torch.zeros_like(Ft)
+        infos = qp.qp_pcg_solve(plan, Ft, Ut, tol=1e-10, maxit=2000, mode=m)
+        out[ex] = (Ut.cpu().numpy(), infos)
+    Up, ip = out[qp.QP_EXEC_PERSISTENT]
+    for ex in (qp.QP_EXEC_GRAPH, qp.QP_EXEC_DIRECT):
+        assert np.array_equal(Up, out[ex][0]) and ip == out[ex][1]
+    op = O.Operator(inst)
+    for r in range(nrhs):
+        assert ip[r]["status"] == "QP_OK"
+        res = np.linalg.norm(F[r] - op(Up[r])) / np.linalg.norm(F[r])
+        assert res <= 1.2e-10, res
+
+
+def test_star_plans_batched_beside_others_bitwise(qp):
+    """Batched, a star-1 plan's stencil data comes from shared memory; alone, from the kernel parameter: the
+    iterates must not differ by a bit."""
+    insts = [_inst(CASES[1], 21), _inst(CASES[3], 22), W.cfg1(6), W.cfg4(4),
+             W.random_instance(2, 3, (6, 4, 8), "sym", "taps", seed=23)]
+    for mode in (qp.QP_MODE_FP64, qp.QP_MODE_FP32_REFINE):
+        plans = [qp.plan_from_instance(i) for i in insts]
+        batch = qp.qp_batch_create(plans)
+        As, infos = qp.qp_batch_homogenized(batch, tol=1e-10, mode=mode)
+        for inst, plan, A in zip(insts, plans, As):
+            A1, _ = qp.qp_homogenized(plan, tol=1e-10, mode=mode)
+            assert np.array_equal(A, A1.real), inst.name
+            A_ref, *_ = O.homogenized(inst, tol=1e-13)
+            assert np.abs(A - A_ref).max() <= 1e-10 * np.abs(A_ref).max(), inst.name
+
+
+def test_misaligned_vectors_are_rejected_before_any_launch(qp):
+    inst = W.cfg1(4)
+    plan = qp.plan_from_instance(inst)
+    buf = torch.zeros(inst.D + 1, dtype=torch.complex64, device="cuda")
+    good = torch.zeros(inst.D, dtype=torch.complex64, device="cuda")
+    with pytest.raises(qp.QPError) as ei:
+        qp.qp_apply_stiffness(plan, buf[1:], good, qp.QP_FP32, nrhs=1)   # 8-byte offset
+    assert ei.value.status == qp.QP_ERR_INVALID_ARG and "aligned" in str(ei.value)
