@@ -209,6 +209,23 @@ const char* qp_last_error(void);
 /* Number of CUDA kernels this library has launched in this process so far (all threads, all plans). */
 uint64_t qp_launch_count(void);
 
+/* FFT-backend apply schedules (the spec autotuner; not in the paper, which has no FFT backend on a GPU).
+ * The apply runs its n-dim transforms as passes over groups of consecutive axes staged in shared-memory tiles.
+ * At plan creation every feasible schedule (one group, every split into two or three groups, each at tile
+ * budgets of 48, 100 and 200 KB) and the per-axis path are timed on this GPU (CUDA events on the plan's
+ * stream, max_rhs right-hand sides, for each precision in the plan's workspace) and the fastest is kept; the
+ * choice is cached per (geometry, coefficient kind, max_rhs, precision) for the process, so later plans of the
+ * same shape are not re-timed. Schedules differ only in the rounding order of the transforms.
+ * qp_set_fft_autotune(0): later plans take the balanced-split heuristic instead (process-wide; cached choices
+ * still apply). qp_fft_schedule: the schedule in use for precision (QP_FP64 / QP_FP32): its candidate index
+ * (-1: the heuristic's), the number of candidates, its timed ms per apply (-1 if untimed) and a description
+ * (text, text_len bytes with the terminating 0; any output may be NULL). qp_fft_set_schedule: use candidate
+ * index (0 .. count - 1) from now on. Both return QP_ERR_UNSUPPORTED for a taps-backend plan. */
+qp_status qp_set_fft_autotune(int enabled);
+qp_status qp_fft_schedule(const qp_plan* plan, int precision, int* index, int* count, double* ms, char* text,
+                          int text_len);
+qp_status qp_fft_set_schedule(qp_plan* plan, int precision, int index);
+
 /* Limit, in seconds, of each grid-barrier wait of a persistent solve (QP_EXEC_PERSISTENT / AUTO); default 2.
  * A wait covers one phase (one stiffness apply or one vector update) of the slowest block, so the limit only
  * has to exceed the longest phase. A solve that exceeds it returns QP_ERR_TIMEOUT with its outputs undefined;

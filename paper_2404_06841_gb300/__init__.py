@@ -34,7 +34,8 @@ KIND_CODES = {"scalar": QP_COEF_SCALAR, "diag": QP_COEF_DIAG, "sym": QP_COEF_SYM
 EXPORTS = ("qp_plan_create", "qp_plan_destroy", "qp_plan_query", "qp_apply_stiffness", "qp_corrector_rhs",
            "qp_pcg_solve", "qp_homogenized_reduce", "qp_homogenized", "qp_fft", "qp_batch_create",
            "qp_batch_homogenized", "qp_batch_destroy", "qp_last_error", "qp_launch_count",
-           "qp_pcg_solve_taps_static", "qp_set_barrier_timeout", "qp_l2qp_error", "qp_plan_diagonal")
+           "qp_pcg_solve_taps_static", "qp_set_barrier_timeout", "qp_l2qp_error", "qp_plan_diagonal",
+           "qp_set_fft_autotune", "qp_fft_schedule", "qp_fft_set_schedule")
 
 
 class qp_coeff(C.Structure):
@@ -95,6 +96,9 @@ def load_library(path: str = LIB_PATH):
         "qp_set_barrier_timeout": [C.c_double],
         "qp_l2qp_error": [vp, i, vp, vp, dp, vp],
         "qp_plan_diagonal": [vp, i, vp, vp],
+        "qp_set_fft_autotune": [i],
+        "qp_fft_schedule": [vp, i, ip, ip, dp, C.c_char_p, i],
+        "qp_fft_set_schedule": [vp, i, i],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -356,6 +360,23 @@ def qp_l2qp_error(plan: Plan, U, Uref=None, stream=None) -> np.ndarray:
     _check(_lib.qp_l2qp_error(plan.handle, int(nrhs), _ptr(U), _ptr(Uref),
                               out.ctypes.data_as(C.POINTER(C.c_double)), _stream(stream)))
     return out
+
+
+def qp_set_fft_autotune(enabled: bool) -> None:
+    """Process-wide: time the FFT apply's candidate schedules at plan creation (default) or take the heuristic."""
+    _check(_lib.qp_set_fft_autotune(1 if enabled else 0))
+
+
+def qp_fft_schedule(plan: Plan, precision=QP_FP32) -> dict:
+    """The FFT-backend apply schedule in use: candidate index, candidate count, timed ms per apply, description."""
+    idx, cnt, ms = C.c_int(0), C.c_int(0), C.c_double(0.0)
+    buf = C.create_string_buffer(256)
+    _check(_lib.qp_fft_schedule(plan.handle, int(precision), C.byref(idx), C.byref(cnt), C.byref(ms), buf, 256))
+    return {"index": idx.value, "count": cnt.value, "ms": ms.value, "text": buf.value.decode()}
+
+
+def qp_fft_set_schedule(plan: Plan, precision, index: int) -> None:
+    _check(_lib.qp_fft_set_schedule(plan.handle, int(precision), int(index)))
 
 
 def qp_set_barrier_timeout(seconds: float) -> None:

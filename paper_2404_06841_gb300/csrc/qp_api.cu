@@ -968,6 +968,41 @@ qp_status qp_l2qp_error(qp_plan* p, int nrhs, const void* U, const void* Uref, d
   API_END
 }
 
+qp_status qp_set_fft_autotune(int enabled) {
+  API_BEGIN
+  fft_set_autotune(enabled != 0);
+  API_END
+}
+
+qp_status qp_fft_schedule(const qp_plan* p, int precision, int* index, int* count, double* ms, char* text,
+                          int text_len) {
+  API_BEGIN
+  if (!p) raise(QP_ERR_INVALID_ARG, "plan must be non-null");
+  if (p->backend != QP_BACKEND_FFT || !p->fft) raise(QP_ERR_UNSUPPORTED, "the plan has no FFT backend");
+  if (precision != QP_FP64 && precision != QP_FP32) raise(QP_ERR_INVALID_ARG, "precision must be QP_FP64 or QP_FP32");
+  std::string t;
+  float m = -1.f;
+  const int idx = fft_schedule_get(p->fft, precision == QP_FP64, t, m);
+  if (index) *index = idx;
+  if (count) *count = fft_schedule_count(p->fft, precision == QP_FP64);
+  if (ms) *ms = (double)m;
+  if (text && text_len > 0) {
+    const size_t nb = std::min<size_t>(t.size(), (size_t)text_len - 1);
+    std::memcpy(text, t.data(), nb);
+    text[nb] = 0;
+  }
+  API_END
+}
+
+qp_status qp_fft_set_schedule(qp_plan* p, int precision, int index) {
+  API_BEGIN
+  if (!p) raise(QP_ERR_INVALID_ARG, "plan must be non-null");
+  if (p->backend != QP_BACKEND_FFT || !p->fft) raise(QP_ERR_UNSUPPORTED, "the plan has no FFT backend");
+  if (precision != QP_FP64 && precision != QP_FP32) raise(QP_ERR_INVALID_ARG, "precision must be QP_FP64 or QP_FP32");
+  fft_schedule_set(p->fft, precision == QP_FP64, index);
+  API_END
+}
+
 qp_status qp_set_barrier_timeout(double seconds) {
   API_BEGIN
   if (!(seconds > 0.0 && seconds <= 3600.0)) raise(QP_ERR_INVALID_ARG, "barrier timeout must be in (0, 3600] s");
@@ -1023,6 +1058,7 @@ qp_status qp_plan_create(int d, int n, const double* P, const int* N, const qp_c
     p->fft = fft_plan_create(p->host_pd, p->precisions, p->max_rhs, s);
     if (coeff->repr == QP_REPR_GRID) fft_set_grid(p->fft, p->host_pd, p->pd, coeff->grid, s);
     else fft_set_taps(p->fft, p->host_pd, p->pd, s);
+    fft_autotune(p->fft, p->host_pd, p->pd, s);
     fft_diag(p->fft, &p->host_pd, p->pd, p->jac64, p->frob64, p->jac32, p->frob32, p->small, s);
     CK_LAUNCH();
   }

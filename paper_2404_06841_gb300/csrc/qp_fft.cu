@@ -11,9 +11,12 @@
 // the tile back. Twiddles for N <= 32 come from a constant-memory table filled once per device from host
 // cos/sin; larger sizes call sincospi in the kernel.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "qp_device.cuh"
@@ -393,9 +396,17 @@ struct GroupPass {
 enum { GP_GRAD_INV = 0, GP_PLAIN = 1, GP_INV_COEF_FWD = 2, GP_FWD_DIV = 3, GP_SINGLE = 4 };
 
 struct FusedSchedule {
-  bool ok = false;
+  bool ok = false;            // false: the per-axis path (gradient, n-dim FFT, coefficient, FFT, divergence)
   int npass = 0;
+  int kb = 0;                 // tile budget (KB of shared memory per block) the passes were sized for
   GroupPass pass[5];
+};
+
+// The FFT-backend apply's candidate schedules for one precision, the one in use, and the autotuner's timings.
+struct ScheduleSet {
+  std::vector<FusedSchedule> cand;   // deterministic order; the last one is the per-axis path
+  std::vector<float> ms;             // measured ms per apply (empty: not tuned)
+  int chosen = -1;
 };
 
 struct FftPlan {
@@ -411,6 +422,7 @@ struct FftPlan {
   double* part = nullptr;       // reduction partials
   int nblk = 0;
   FusedSchedule fused64, fused32;   // group-pass schedules of the apply (ok = false: per-axis passes)
+  ScheduleSet sched64, sched32;     // their candidates (autotuner)
   cudaStream_t stream = nullptr;   // the creating stream (allocations are ordered on it)
   void* take(size_t b) {
     void* p = dev_alloc(b, stream);
@@ -423,7 +435,8 @@ struct FftPlan {
   }
 };
 
-static FusedSchedule plan_fused(const PlanDev& pd, int esize);
+static FusedSchedule plan_fused(const PlanDev& pd, int esize, int kb = 100);
+static std::vector<FusedSchedule> fused_candidates(const PlanDev& pd, int esize);
 
 FftPlan* fft_plan_create(const PlanDev& pd, int precisions, int max_rhs, cudaStream_t s) {
   for (int j = 0; j < pd.n; ++j)
@@ -450,6 +463,8 @@ FftPlan* fft_plan_create(const PlanDev& pd, int precisions, int max_rhs, cudaStr
     f->nblk = (int)std::min<int64_t>((pd.D + BLOCK - 1) / BLOCK, 152 * 8);
     f->fused64 = plan_fused(pd, (int)sizeof(double2));
     f->fused32 = plan_fused(pd, (int)sizeof(float2));
+    f->sched64.cand = fused_candidates(pd, (int)sizeof(double2));
+    f->sched32.cand = fused_candidates(pd, (int)sizeof(float2));
     f->part = (double*)f->take((size_t)f->nblk * 2 * MAXD * MAXD * sizeof(double) + 1024);
   } catch (...) {
     delete f;
@@ -1183,14 +1198,14 @@ static long long largest_divisor_le(long long x, long long cap) {
   return 1;
 }
 
-// Elements per tile that a pass may stage: ntile tiles (with padding) in about 100 KB, so that two blocks fit
-// on an SM, and at most GP_EPT elements per thread.
-static int tile_budget(int esize, int ntile) {
-  const int by_smem = (100 * 1024) / (esize * ntile) * 32 / 33 - 1;
+// Elements per tile that a pass may stage: ntile tiles (with padding) in about kb KB of shared memory (100 KB:
+// two blocks per SM), and at most GP_EPT elements per thread.
+static int tile_budget(int esize, int ntile, int kb) {
+  const int by_smem = (kb * 1024) / (esize * ntile) * 32 / 33 - 1;
   return std::min(by_smem, GP_EPT * BLOCK);
 }
 
-static bool make_pass(const PlanDev& pd, int j0, int ng, int mode, int sign, int esize, GroupPass& gp) {
+static bool make_pass(const PlanDev& pd, int j0, int ng, int mode, int sign, int esize, int kb, GroupPass& gp) {
   gp = GroupPass();
   if (ng < 1 || ng > MAXN || j0 + ng > pd.n) return false;
   gp.mode = mode;
@@ -1211,7 +1226,7 @@ static bool make_pass(const PlanDev& pd, int j0, int ng, int mode, int sign, int
   for (int t = 0; t < ng; ++t) gp.nhi[t] = (int)(M / (gp.Ng[t] * gp.sg[t]));
   for (int j = 0; j < j0; ++j) O *= pd.N[j];
   for (int j = j0 + ng; j < pd.n; ++j) I *= pd.N[j];
-  const int budget = tile_budget(esize, gp.ntile);
+  const int budget = tile_budget(esize, gp.ntile, kb);
   if (M > budget) return false;
   gp.M = (int)M;
   gp.O = O;
@@ -1237,13 +1252,14 @@ static bool make_pass(const PlanDev& pd, int j0, int ng, int mode, int sign, int
 }
 
 // Groups of consecutive axes and the passes over them (see above); ok = false leaves the per-axis path.
-static FusedSchedule plan_fused(const PlanDev& pd, int esize) {
+static FusedSchedule plan_fused(const PlanDev& pd, int esize, int kb) {
   FusedSchedule fs;
+  fs.kb = kb;
   const int n = pd.n;
   for (int j = 0; j < n; ++j)
     if (pd.N[j] > 32) return fs;
   GroupPass a, b, c, m1, m2;
-  if (make_pass(pd, 0, n, GP_SINGLE, 0, esize, a)) {
+  if (make_pass(pd, 0, n, GP_SINGLE, 0, esize, kb, a)) {
     fs.pass[0] = a;
     fs.npass = 1;
     fs.ok = true;
@@ -1253,7 +1269,8 @@ static FusedSchedule plan_fused(const PlanDev& pd, int esize) {
   int best = -1;
   long long best_max = 0;
   for (int s = 1; s < n; ++s) {
-    if (!make_pass(pd, 0, s, GP_GRAD_INV, 0, esize, a) || !make_pass(pd, s, n - s, GP_INV_COEF_FWD, 0, esize, b))
+    if (!make_pass(pd, 0, s, GP_GRAD_INV, 0, esize, kb, a) ||
+        !make_pass(pd, s, n - s, GP_INV_COEF_FWD, 0, esize, kb, b))
       continue;
     const long long mx = std::max(a.M, b.M);
     if (best < 0 || mx < best_max) {
@@ -1262,9 +1279,9 @@ static FusedSchedule plan_fused(const PlanDev& pd, int esize) {
     }
   }
   if (best > 0) {
-    make_pass(pd, 0, best, GP_GRAD_INV, 0, esize, a);
-    make_pass(pd, best, n - best, GP_INV_COEF_FWD, 0, esize, b);
-    make_pass(pd, 0, best, GP_FWD_DIV, 0, esize, c);
+    make_pass(pd, 0, best, GP_GRAD_INV, 0, esize, kb, a);
+    make_pass(pd, best, n - best, GP_INV_COEF_FWD, 0, esize, kb, b);
+    make_pass(pd, 0, best, GP_FWD_DIV, 0, esize, kb, c);
     fs.pass[0] = a;
     fs.pass[1] = b;
     fs.pass[2] = c;
@@ -1276,8 +1293,9 @@ static FusedSchedule plan_fused(const PlanDev& pd, int esize) {
   int b1 = -1, b2 = -1;
   for (int s1 = 1; s1 < n - 1; ++s1)
     for (int s2 = s1 + 1; s2 < n; ++s2) {
-      if (!make_pass(pd, 0, s1, GP_GRAD_INV, 0, esize, a) || !make_pass(pd, s1, s2 - s1, GP_PLAIN, 1, esize, m1) ||
-          !make_pass(pd, s2, n - s2, GP_INV_COEF_FWD, 0, esize, b))
+      if (!make_pass(pd, 0, s1, GP_GRAD_INV, 0, esize, kb, a) ||
+          !make_pass(pd, s1, s2 - s1, GP_PLAIN, 1, esize, kb, m1) ||
+          !make_pass(pd, s2, n - s2, GP_INV_COEF_FWD, 0, esize, kb, b))
         continue;
       const long long mx = std::max<long long>(std::max(a.M, m1.M), b.M);
       if (b1 < 0 || mx < best_max) {
@@ -1287,11 +1305,11 @@ static FusedSchedule plan_fused(const PlanDev& pd, int esize) {
       }
     }
   if (b1 < 0) return fs;
-  make_pass(pd, 0, b1, GP_GRAD_INV, 0, esize, a);
-  make_pass(pd, b1, b2 - b1, GP_PLAIN, +1, esize, m1);
-  make_pass(pd, b2, n - b2, GP_INV_COEF_FWD, 0, esize, b);
-  make_pass(pd, b1, b2 - b1, GP_PLAIN, -1, esize, m2);
-  make_pass(pd, 0, b1, GP_FWD_DIV, 0, esize, c);
+  make_pass(pd, 0, b1, GP_GRAD_INV, 0, esize, kb, a);
+  make_pass(pd, b1, b2 - b1, GP_PLAIN, +1, esize, kb, m1);
+  make_pass(pd, b2, n - b2, GP_INV_COEF_FWD, 0, esize, kb, b);
+  make_pass(pd, b1, b2 - b1, GP_PLAIN, -1, esize, kb, m2);
+  make_pass(pd, 0, b1, GP_FWD_DIV, 0, esize, kb, c);
   fs.pass[0] = a;
   fs.pass[1] = m1;
   fs.pass[2] = b;
@@ -1300,6 +1318,84 @@ static FusedSchedule plan_fused(const PlanDev& pd, int esize) {
   fs.npass = 5;
   fs.ok = true;
   return fs;
+}
+
+// Every schedule the group passes can run: one group, every split into two and into three groups of
+// consecutive axes, each sized for tile budgets of 48, 100 and 200 KB; distinct by the passes' geometry, in a
+// fixed order, followed by the per-axis path (ok = false). The autotuner times them all.
+static std::vector<FusedSchedule> fused_candidates(const PlanDev& pd, int esize) {
+  std::vector<FusedSchedule> out;
+  std::vector<std::string> seen;
+  auto add = [&](const FusedSchedule& fs) {
+    std::string key = std::to_string(fs.npass);
+    for (int i = 0; i < fs.npass; ++i) {
+      const GroupPass& g = fs.pass[i];
+      key += ":" + std::to_string(g.j0) + "," + std::to_string(g.ng) + "," + std::to_string(g.mode) + "," +
+             std::to_string(g.L) + "," + std::to_string(g.R);
+    }
+    if (std::find(seen.begin(), seen.end(), key) != seen.end()) return;
+    seen.push_back(key);
+    out.push_back(fs);
+  };
+  const int n = pd.n;
+  bool small = true;
+  for (int j = 0; j < n; ++j) small = small && pd.N[j] <= 32;
+  const int budgets[3] = {48, 100, 200};
+  for (int bi = 0; bi < 3 && small; ++bi) {
+    const int kb = budgets[bi];
+    FusedSchedule fs;
+    fs.ok = true;
+    fs.kb = kb;
+    GroupPass a, b, c, m1, m2;
+    if (make_pass(pd, 0, n, GP_SINGLE, 0, esize, kb, a)) {
+      fs.pass[0] = a;
+      fs.npass = 1;
+      add(fs);
+    }
+    for (int s1 = 1; s1 < n; ++s1) {
+      if (make_pass(pd, 0, s1, GP_GRAD_INV, 0, esize, kb, a) &&
+          make_pass(pd, s1, n - s1, GP_INV_COEF_FWD, 0, esize, kb, b) &&
+          make_pass(pd, 0, s1, GP_FWD_DIV, 0, esize, kb, c)) {
+        fs.pass[0] = a;
+        fs.pass[1] = b;
+        fs.pass[2] = c;
+        fs.npass = 3;
+        add(fs);
+      }
+    }
+    for (int s1 = 1; s1 < n - 1; ++s1)
+      for (int s2 = s1 + 1; s2 < n; ++s2) {
+        if (make_pass(pd, 0, s1, GP_GRAD_INV, 0, esize, kb, a) &&
+            make_pass(pd, s1, s2 - s1, GP_PLAIN, +1, esize, kb, m1) &&
+            make_pass(pd, s2, n - s2, GP_INV_COEF_FWD, 0, esize, kb, b) &&
+            make_pass(pd, s1, s2 - s1, GP_PLAIN, -1, esize, kb, m2) &&
+            make_pass(pd, 0, s1, GP_FWD_DIV, 0, esize, kb, c)) {
+          fs.pass[0] = a;
+          fs.pass[1] = m1;
+          fs.pass[2] = b;
+          fs.pass[3] = m2;
+          fs.pass[4] = c;
+          fs.npass = 5;
+          add(fs);
+        }
+      }
+  }
+  out.push_back(FusedSchedule());   // the per-axis path
+  return out;
+}
+
+static std::string schedule_text(const FusedSchedule& fs) {
+  if (!fs.ok) return "per-axis passes";
+  std::string t;
+  for (int i = 0; i < fs.npass; ++i) {
+    const GroupPass& g = fs.pass[i];
+    if (g.mode == GP_FWD_DIV || (g.mode == GP_PLAIN && g.sign < 0)) continue;   // mirrors of earlier passes
+    t += "[" + std::to_string(g.j0) + "," + std::to_string(g.j0 + g.ng) + ")";
+  }
+  const GroupPass& g0 = fs.pass[0];
+  return "axis groups " + t + ", " + std::to_string(fs.npass) + " passes, tile budget " + std::to_string(fs.kb) +
+         " KB (first pass: tiles of " + std::to_string(g0.L) + " x " + std::to_string(g0.M) + " x " +
+         std::to_string(g0.R) + ")";
 }
 
 template <typename T, int MODE>
@@ -1335,18 +1431,11 @@ template <typename T> static const T* coef_of(FftPlan* f);
 template <> const double* coef_of<double>(FftPlan* f) { return f->coef64; }
 template <> const float* coef_of<float>(FftPlan* f) { return f->coef32; }
 
+// The per-axis path: gradient, n-dim inverse FFT of the d fields, coefficient product, forward FFT, divergence.
 template <typename T>
-void fft_apply(FftPlan* f, const PlanDev& pd, const PlanDev* pdp, const cplx<T>* h, cplx<T>* w, int nrhs,
-               cudaStream_t s) {
+static void run_axis(FftPlan* f, const PlanDev& pd, const PlanDev* pdp, const cplx<T>* h, cplx<T>* w, int nrhs,
+                     cudaStream_t s) {
   cplx<T>* g = fields_of<T>(f);
-  if (!g || nrhs > f->max_rhs)
-    raise(QP_ERR_INVALID_ARG, "FFT plan has no workspace for this precision / number of right-hand sides");
-  const FusedSchedule& fs = (sizeof(T) == 8) ? f->fused64 : f->fused32;
-  if (fs.ok) {
-    run_fused<T>(fs, pd, pdp, h, g, w, coef_of<T>(f), nrhs, s);
-    CK_LAUNCH();
-    return;
-  }
   k_grad<T><<<f->nblk, BLOCK, 0, s>>>(pdp, nrhs, h, g);
   count_launch();
   fft_nd<T>(g, pd.n, pd.N, (long long)pd.d * nrhs, +1, s);
@@ -1355,7 +1444,122 @@ void fft_apply(FftPlan* f, const PlanDev& pd, const PlanDev* pdp, const cplx<T>*
   fft_nd<T>(g, pd.n, pd.N, (long long)pd.d * nrhs, -1, s);
   k_div<T><<<f->nblk, BLOCK, 0, s>>>(pdp, nrhs, g, w);
   count_launch();
+}
+
+template <typename T>
+void fft_apply(FftPlan* f, const PlanDev& pd, const PlanDev* pdp, const cplx<T>* h, cplx<T>* w, int nrhs,
+               cudaStream_t s) {
+  cplx<T>* g = fields_of<T>(f);
+  if (!g || nrhs > f->max_rhs)
+    raise(QP_ERR_INVALID_ARG, "FFT plan has no workspace for this precision / number of right-hand sides");
+  const FusedSchedule& fs = (sizeof(T) == 8) ? f->fused64 : f->fused32;
+  if (fs.ok) run_fused<T>(fs, pd, pdp, h, g, w, coef_of<T>(f), nrhs, s);
+  else run_axis<T>(f, pd, pdp, h, w, nrhs, s);
   CK_LAUNCH();
+}
+
+// ---- autotuner of the apply schedule
+
+namespace {
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune_cache;   // geometry and precision -> chosen candidate
+std::atomic<int> g_autotune{1};
+}  // namespace
+
+void fft_set_autotune(bool on) { g_autotune.store(on ? 1 : 0); }
+
+template <typename T>
+static void tune_precision(FftPlan* f, const PlanDev& pd, const PlanDev* pdp, cudaStream_t s) {
+  ScheduleSet& ss = sizeof(T) == 8 ? f->sched64 : f->sched32;
+  FusedSchedule& use = sizeof(T) == 8 ? f->fused64 : f->fused32;
+  if (!fields_of<T>(f) || ss.cand.empty()) return;
+  std::string key = std::to_string(sizeof(T)) + "/" + std::to_string(pd.d) + "/" + std::to_string(pd.kind) + "/" +
+                    std::to_string(f->max_rhs);
+  for (int j = 0; j < pd.n; ++j) key += "/" + std::to_string(pd.N[j]);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end() && it->second < (int)ss.cand.size()) {
+      ss.chosen = it->second;
+      use = ss.cand[ss.chosen];
+      return;
+    }
+  }
+  if (!g_autotune.load()) return;   // keep the balanced-split heuristic
+  const int nr = f->max_rhs;
+  const size_t bytes = (size_t)nr * pd.D * sizeof(cplx<T>);
+  cplx<T>* h = static_cast<cplx<T>*>(dev_alloc(bytes, s));
+  cplx<T>* w = static_cast<cplx<T>*>(dev_alloc(bytes, s));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  ss.ms.assign(ss.cand.size(), INFINITY);
+  try {
+    CK(cudaMemsetAsync(h, 0, bytes, s));
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    for (size_t i = 0; i < ss.cand.size(); ++i) {
+      const FusedSchedule& fs = ss.cand[i];
+      auto run = [&]() {
+        if (fs.ok) run_fused<T>(fs, pd, pdp, h, fields_of<T>(f), w, coef_of<T>(f), nr, s);
+        else run_axis<T>(f, pd, pdp, h, w, nr, s);
+      };
+      try {
+        run();   // warm-up (and the shared-memory opt-in of its kernels)
+        CK(cudaEventRecord(e0, s));
+        for (int rep = 0; rep < 3; ++rep) run();
+        CK(cudaEventRecord(e1, s));
+        CK(cudaEventSynchronize(e1));
+        CK_LAUNCH();
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        ss.ms[i] = ms / 3.f;
+      } catch (const QpError&) {
+        // a configuration this device refuses (launch error, nothing ran): not a candidate here
+        if (cudaStreamSynchronize(s) != cudaSuccess) throw;
+        cudaGetLastError();
+      }
+    }
+  } catch (...) {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaStreamSynchronize(s);
+    dev_free(h);
+    dev_free(w);
+    throw;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CK(cudaStreamSynchronize(s));
+  dev_free(h);
+  dev_free(w);
+  int best = 0;
+  for (size_t i = 1; i < ss.ms.size(); ++i)
+    if (ss.ms[i] < ss.ms[best]) best = (int)i;
+  ss.chosen = best;
+  use = ss.cand[best];
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[key] = best;
+}
+
+void fft_autotune(FftPlan* f, const PlanDev& pd, const PlanDev* pdp, cudaStream_t s) {
+  if (f->precisions & 1) tune_precision<double>(f, pd, pdp, s);
+  if (f->precisions & 2) tune_precision<float>(f, pd, pdp, s);
+}
+
+int fft_schedule_count(const FftPlan* f, bool fp64) { return (int)(fp64 ? f->sched64 : f->sched32).cand.size(); }
+
+int fft_schedule_get(const FftPlan* f, bool fp64, std::string& text, float& ms) {
+  const ScheduleSet& ss = fp64 ? f->sched64 : f->sched32;
+  const FusedSchedule& use = fp64 ? f->fused64 : f->fused32;
+  text = schedule_text(use);
+  ms = (ss.chosen >= 0 && ss.chosen < (int)ss.ms.size()) ? ss.ms[ss.chosen] : -1.f;
+  return ss.chosen;
+}
+
+void fft_schedule_set(FftPlan* f, bool fp64, int index) {
+  ScheduleSet& ss = fp64 ? f->sched64 : f->sched32;
+  if (index < 0 || index >= (int)ss.cand.size()) raise(QP_ERR_INVALID_ARG, "schedule index out of range");
+  ss.chosen = index;
+  (fp64 ? f->fused64 : f->fused32) = ss.cand[index];
 }
 template void fft_apply<double>(FftPlan*, const PlanDev&, const PlanDev*, const double2*, double2*, int, cudaStream_t);
 template void fft_apply<float>(FftPlan*, const PlanDev&, const PlanDev*, const float2*, float2*, int, cudaStream_t);

@@ -1,6 +1,8 @@
 // n-dimensional complex FFT kernels and the FFT-backend stiffness apply (declarations).
 #pragma once
 
+#include <string>
+
 #include "qp_internal.cuh"
 
 namespace qp {
@@ -25,6 +27,15 @@ void fft_frobenius(FftPlan* f, const PlanDev& pd, const PlanDev* pdp, double* fr
 template <typename T>
 void fft_apply(FftPlan* f, const PlanDev& pd, const PlanDev* pdp, const cplx<T>* h, cplx<T>* w, int nrhs,
                cudaStream_t s);
+// Autotuner of the apply (per precision in the plan's workspace): times every candidate group schedule and the
+// per-axis path on this GPU and keeps the fastest; the choice is cached per geometry for the process. Off
+// (fft_set_autotune(false)): the balanced-split heuristic.
+void fft_autotune(FftPlan* f, const PlanDev& pd, const PlanDev* pdp, cudaStream_t s);
+void fft_set_autotune(bool on);
+int fft_schedule_count(const FftPlan* f, bool fp64);
+// the schedule in use: its candidate index (-1: the heuristic's, untimed), description and timed ms per apply
+int fft_schedule_get(const FftPlan* f, bool fp64, std::string& text, float& ms);
+void fft_schedule_set(FftPlan* f, bool fp64, int index);
 void fft_rhs(FftPlan* f, const PlanDev& pd, const PlanDev* pdp, int j0, int nrhs, double2* F, cudaStream_t s);
 void fft_astar(FftPlan* f, const PlanDev& pd, const PlanDev* pdp, const double2* U, double* out, cudaStream_t s);
 void fft_standalone(int n, const int* N, int count, void* data, int sign, int precision, cudaStream_t s);

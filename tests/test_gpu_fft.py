@@ -45,8 +45,8 @@ def test_fft_matches_numpy(qp, shape, prec):
         assert err <= tol, (shape, sign, err)
 
 
-# Small grids take the one-pass fused apply; (16, 12, 16, 24) and the 6-axis grid split into two groups of axes
-# (three passes); (64, 48) has axes above 32 and takes the per-axis passes.
+# Grids with every axis <= 32 run group passes (the schedule the autotuner timed fastest; test_gpu_autotune checks
+# every candidate); (64, 48) has axes above 32 and takes the per-axis passes.
 GRID_CASES = [(1, 2, (8, 12), "scalar"), (2, 2, (16, 8), "sym"), (2, 3, (8, 6, 4), "diag"), (3, 3, (4, 6, 8), "sym"),
               (2, 4, (6, 4, 8, 4), "sym"), (1, 1, (32,), "scalar"), (2, 4, (16, 12, 16, 24), "sym"),
               (3, 6, (6, 6, 6, 6, 6, 6), "diag"), (1, 2, (64, 48), "scalar")]
@@ -72,9 +72,9 @@ def test_fft_apply_matches_oracle_on_full_support_grids(qp, d, n, N, kind, prec)
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_fft_apply_three_group_schedule_sampled(qp, prec):
-    """16^5 x 8 modes: in FP64 no split into two groups of axes fits the tiles, so the apply runs five passes
-    (gradient + inverse over the first group, plain passes over the middle one). Compared with the taps backend
-    on the whole vector and with the oracle's pointwise sum at sampled modes."""
+    """16^5 x 8 modes: the autotuner's schedule, and forced a five-pass schedule (three groups of axes: gradient
+    + inverse over the first group, plain passes over the middle one), compared with the taps backend on the
+    whole vector and with the oracle's pointwise sum at sampled modes."""
     N = (16, 16, 16, 16, 16, 8)
     inst = W.random_instance(1, 6, N, "scalar", "taps", seed=23, nmodes=6)
     p_f = qp.plan_from_instance(inst, backend=qp.QP_BACKEND_FFT, max_rhs=1)
@@ -84,18 +84,25 @@ def test_fft_apply_three_group_schedule_sampled(qp, prec):
     pr = qp.QP_FP64 if prec == "fp64" else qp.QP_FP32
     h = torch.complex(torch.randn((1,) + N, dtype=torch.float64), torch.randn((1,) + N, dtype=torch.float64))
     h = h.to("cuda", dt)
-    w_f, w_t = torch.empty_like(h), torch.empty_like(h)
-    qp.qp_apply_stiffness(p_f, h, w_f, pr)
+    w_t = torch.empty_like(h)
     qp.qp_apply_stiffness(p_t, h, w_t, pr)
     tol = 1e-12 if prec == "fp64" else 2e-5
     scale = float(w_t.abs().max())
-    assert float((w_f - w_t).abs().max()) <= tol * scale
     pts = [tuple(int(x) for x in (rng.integers(0, Nj) for Nj in N)) for _ in range(64)]
     pts += [(0,) * 6, tuple(Nj // 2 for Nj in N), tuple(Nj - 1 for Nj in N)]
     hc = h[0].cpu().numpy().astype(np.complex128)
     ref = O.apply_taps_at(inst.P, N, inst.coeff.taps_k, inst.coeff.taps_val, "scalar", hc, pts)
-    got = np.array([complex(w_f[(0,) + p].item()) for p in pts])
-    assert np.abs(got - ref).max() <= tol * scale
+    chosen = qp.qp_fft_schedule(p_f, pr)
+    five = [i for i in range(chosen["count"]) if (qp.qp_fft_set_schedule(p_f, pr, i) or True)
+            and "5 passes" in qp.qp_fft_schedule(p_f, pr)["text"]]
+    assert five, "no three-group schedule among the candidates"
+    for idx in (chosen["index"], five[0]):
+        qp.qp_fft_set_schedule(p_f, pr, idx)
+        w_f = torch.empty_like(h)
+        qp.qp_apply_stiffness(p_f, h, w_f, pr)
+        assert float((w_f - w_t).abs().max()) <= tol * scale
+        got = np.array([complex(w_f[(0,) + p].item()) for p in pts])
+        assert np.abs(got - ref).max() <= tol * scale
 
 
 @pytest.mark.parametrize("d,n,N,kind", [(2, 3, (8, 6, 4), "sym"), (1, 2, (12, 16), "scalar"), (3, 3, (6, 4, 8), "diag")])
