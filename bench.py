@@ -72,11 +72,12 @@ def peaks():
 
 # ---------------------------------------------------------------------------------------------- roofline model
 
-def apply_flops_per_dof(kind, d, ntaps, real, nrhs):
-    """Algorithmic flops of one stiffness apply per mode, taps backend: per tap the weight
-    lambda(k)^T C_t lambda(k -N m_t) (scalar: 2d, diag: 3d, sym: 3d^2; doubled for complex taps) and, per
-    right-hand side, the complex multiply-accumulate with h (4 flops real weight, 8 complex)."""
-    w = {"scalar": 2 * d, "diag": 3 * d, "sym": 3 * d * d}[kind] * (1 if real else 2)
+def apply_flops_per_dof(kind, d, ntaps, real, nrhs, stored=False):
+    """Algorithmic flops of one stiffness apply per mode, taps backend: per tap and right-hand side the complex
+    multiply-accumulate with h (4 flops real weight, 8 complex), and unless the plan stores its weights Q_ij
+    (formed once at plan creation, then only read) per tap the weight lambda(k)^T C_t lambda(k -N m_t)
+    (scalar: 2d, diag: 3d, sym: 3d^2; doubled for complex taps)."""
+    w = 0 if stored else {"scalar": 2 * d, "diag": 3 * d, "sym": 3 * d * d}[kind] * (1 if real else 2)
     return ntaps * (w + nrhs * (4 if real else 8))
 
 
@@ -115,10 +116,10 @@ def fft_apply_bytes(d, ncomp, nrhs, D, es):
 # of the current kernel each (summaries and commands under profiles/); None where no capture of the current kernel
 # exists.
 TRAFFIC = {
-    # cfg1: one solve (33 iterations, 2 correctors) in k_pcg_persistent; vectors stay in L2
-    ("k_pcg_persistent", "cfg1"): 4966400 + 452096,
-    # cfg4: captured at N = 14 (7.53 M modes; h and w exceed L2), scaled by 16^6 / 14^6 to the full launch
-    ("k_apply_plain", "cfg4"): int((207264512 + 150830592) * (16 ** 6 / 14 ** 6)),
+    # cfg1: one solve (33 iterations, 2 correctors) in k_pcg_persistent; vectors and stored weights stay in L2
+    ("k_pcg_persistent", "cfg1"): 9568512 + 367616,
+    # cfg4: k_apply_plain_star captured at N = 14 (7.53 M modes; h and w exceed L2), scaled by 16^6 / 14^6
+    ("k_apply_plain", "cfg4"): int((207585792 + 153159424) * (16 ** 6 / 14 ** 6)),
     # cfg2: the three fused passes of one FP32 apply (the gradient fields stay in L2 between passes)
     ("k_fft_group", "cfg2"): 16874752 + 9472 + 46255616 + 0 + 33646848 + 0,
 }
@@ -157,7 +158,8 @@ def persistent_roofline(qp, plan, inst, pinfo, real, tol, stream, dev):
     c = inst.coeff
     # every iteration applies Q to all right-hand sides; plus the warm-start apply and the final true residual
     applies = max(its) + 2
-    flops = (applies * apply_flops_per_dof(c.kind, inst.d, pinfo["ntaps"], real, nrhs) * inst.D
+    stored = bool(pinfo.get("stored_weights"))
+    flops = (applies * apply_flops_per_dof(c.kind, inst.d, pinfo["ntaps"], real, nrhs, stored) * inst.D
              + sum(its) * update_flops_per_dof() * inst.D)
     achieved = flops / (ms / 1e3) / 1e12
     return {"bound": "alu", "achieved": round(achieved, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -165,7 +167,8 @@ def persistent_roofline(qp, plan, inst, pinfo, real, tol, stream, dev):
             "kernel": "k_pcg_persistent (whole FP64 PCG solve in one cooperative launch), timed alone on the bench "
                       "stream (the events also bracket two 4-byte memsets and the solver-state read-back)",
             "kernel_key": "k_pcg_persistent", "launch_us": round(ms * 1e3, 2), "flops_per_launch": flops,
-            "iterations": its, "peak_source": "nominal FP64 1.25 TFLOP/s (FMA-loop probe on GB300: 1.196)"}
+            "iterations": its, "stored_weights": stored,
+            "peak_source": "nominal FP64 1.25 TFLOP/s (FMA-loop probe on GB300: 1.196)"}
 
 
 def apply_roofline(qp, plan, inst, pinfo, real, mode_name, stream, dev):
@@ -190,7 +193,8 @@ def apply_roofline(qp, plan, inst, pinfo, real, mode_name, stream, dev):
     c = inst.coeff
     pk = peaks()
     if prec == qp.QP_FP64 and c.taps_k is not None:
-        flops = apply_flops_per_dof(c.kind, inst.d, pinfo["ntaps"], real, nrhs) * inst.D
+        stored = bool(pinfo.get("stored_weights"))
+        flops = apply_flops_per_dof(c.kind, inst.d, pinfo["ntaps"], real, nrhs, stored) * inst.D
         achieved = flops / (apply_ms / 1e3) / 1e12
         return {"bound": "alu", "achieved": round(achieved, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": None,

@@ -114,6 +114,10 @@ typedef struct {
   int max_rhs;
   double min_abs_lambda; /* min over k != 0 of |P k| */
   int64_t device_bytes;  /* device memory the plan holds */
+  int star;              /* 1: taps only at m = 0 and m = +-e_j with a scalar or diagonal coefficient (the star-1
+                            stencil of the taps backend) */
+  int stored_weights;    /* 1: the plan stores the FP64 stiffness entries Q_ij per (tap, mode) (Sec. 4.2's
+                            compressed format Q~), which single-plan FP64 applies read instead of forming */
 } qp_plan_info;
 
 /* Creates a plan: validates d (1..3), n (d..6), P (host double d x n, row-major, Sec. 2.1 projection

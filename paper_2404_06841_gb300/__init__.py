@@ -63,7 +63,8 @@ class qp_solve_info(C.Structure):
 
 class qp_plan_info(C.Structure):
     _fields_ = [("D", C.c_int64), ("backend", C.c_int), ("ntaps", C.c_int), ("max_rhs", C.c_int),
-                ("min_abs_lambda", C.c_double), ("device_bytes", C.c_int64)]
+                ("min_abs_lambda", C.c_double), ("device_bytes", C.c_int64), ("star", C.c_int),
+                ("stored_weights", C.c_int)]
 
 
 class QPError(RuntimeError):
@@ -204,7 +205,8 @@ def qp_plan_query(plan: Plan) -> dict:
     info = qp_plan_info()
     _check(_lib.qp_plan_query(plan.handle, C.byref(info)))
     return {"D": info.D, "backend": {1: "taps", 2: "fft"}.get(info.backend, info.backend), "ntaps": info.ntaps,
-            "max_rhs": info.max_rhs, "min_abs_lambda": info.min_abs_lambda, "device_bytes": info.device_bytes}
+            "max_rhs": info.max_rhs, "min_abs_lambda": info.min_abs_lambda, "device_bytes": info.device_bytes,
+            "star": bool(info.star), "stored_weights": bool(info.stored_weights)}
 
 
 def qp_apply_stiffness(plan: Plan, U, QU, precision=QP_FP64, nrhs=None, stream=None):

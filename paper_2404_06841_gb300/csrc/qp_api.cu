@@ -64,6 +64,7 @@ struct qp_plan {
 
   PlanDev host_pd{};           // host copy of the device plan description
   StarParams star_host{};      // star-1 stencil data (host_pd.star1), passed by value to single-plan kernels
+  void* w64 = nullptr;         // star-1 plans: stored FP64 weights (star_host.w64), or null
   PlanDev* pd = nullptr;       // device copy
   bool real_coef = false;
   int coef_count = 0;          // ntaps * ncomp
@@ -404,6 +405,24 @@ void build_taps(qp_plan* p, const qp_coeff* c) {
   if (pd.star1) pd.star = (const StarParams*)up(&p->star_host, sizeof(StarParams));
 }
 
+// FP64 weights of a star-1 plan stored per (tap slot, mode). The compressed format of Sec. 4.2 keeps the nonzero
+// entries Q_ij of the stiffness matrix; on this GPU, where FP64 arithmetic runs at 1/64 of the FP32 rate, reading
+// them once per apply is cheaper than forming them, so FP64 applies of a single plan read them. They are formed
+// by the stencil's own arithmetic, so stored and formed weights agree bit for bit (a batch of several plans forms
+// them). Built when the plan has FP64 vectors and the table takes at most a quarter of the free device memory.
+void build_star_weights(qp_plan* p, cudaStream_t s) {
+  const PlanDev& pd = p->host_pd;
+  if (!pd.star1 || !(p->precisions & 1) || pd.N[pd.n - 1] % 2 != 0) return;
+  const size_t bytes = (size_t)(1 + 2 * pd.n) * (size_t)p->D * (p->real_coef ? sizeof(double) : sizeof(double2));
+  size_t fr = 0, tot = 0;
+  CK(cudaMemGetInfo(&fr, &tot));
+  if (bytes > fr / 4) return;
+  p->w64 = p->dalloc(bytes);
+  p->star_host.w64 = p->w64;
+  launch_star_weights(p->star_host, p->real_coef, p->kind, p->D, p->w64, s);
+  CK_LAUNCH();
+}
+
 void alloc_workspace(qp_plan* p) {
   const size_t D = (size_t)p->D, R = (size_t)p->max_rhs;
   p->jac64 = (double*)p->dalloc(D * sizeof(double));
@@ -462,9 +481,11 @@ void record_apply(const Units& us, const Entry& en, int level, int epi, int refi
     else if (epi == EPI_DOT_HW) fft_apply<double>(p->fft, p->host_pd, p->pd, p->v64.h, p->v64.w, nr, s);
     else fft_apply<double>(p->fft, p->host_pd, p->pd, p->v64.X, p->v64.w, nr, s);
   }
-  // a single star-1 unit with an even last axis takes its stencil data as a kernel parameter
+  // a single star-1 unit with an even last axis takes its stencil data as a kernel parameter (FP64: only with
+  // its stored weights)
   const qp_plan* p0 = us.plans.size() == 1 ? us.plans[0] : nullptr;
-  const bool st = p0 && p0->backend == QP_BACKEND_TAPS && p0->host_pd.star1 && last_axis_run(p0) == 2;
+  const bool st = p0 && p0->backend == QP_BACKEND_TAPS && p0->host_pd.star1 && last_axis_run(p0) == 2 &&
+                  (level == LEVEL_FP32 || p0->w64);
   launch_apply(en.bd, us.all_real, us.max_coef, us.max_rhs, level, epi, refine, cond, en.nblk,
                st ? &p0->star_host : nullptr, p0 ? p0->kind : 0, s);
   CK_LAUNCH();
@@ -729,7 +750,8 @@ Entry& get_entry(Solver* sv, const Units& us, const Key& key, cudaStream_t s) {
     // kernels run at higher occupancy.
     const size_t smem = persistent_smem(us.max_coef);
     const qp_plan* p0 = us.plans[0];
-    const int sk = (p0->backend == QP_BACKEND_TAPS && p0->host_pd.star1) ? (p0->kind == QP_COEF_DIAG ? 2 : 1) : 0;
+    const int sk = (p0->backend == QP_BACKEND_TAPS && p0->host_pd.star1 && p0->w64)
+                       ? (p0->kind == QP_COEF_DIAG ? 2 : 1) : 0;
     int capn = 0;
     try {
       capn = persistent_capacity(us.all_real, us.max_rhs, sk, smem);
@@ -1053,6 +1075,7 @@ qp_status qp_plan_create(int d, int n, const double* P, const int* N, const qp_c
                 p->small, p->nblk, s);
     CK_LAUNCH();
     p->frob_ready = true;
+    build_star_weights(p.get(), s);
   } else {
     CK(cudaMemcpyAsync(p->pd, &p->host_pd, sizeof(PlanDev), cudaMemcpyHostToDevice, s));
     p->fft = fft_plan_create(p->host_pd, p->precisions, p->max_rhs, s);
@@ -1093,6 +1116,8 @@ qp_status qp_plan_query(const qp_plan* p, qp_plan_info* info) {
   info->max_rhs = p->max_rhs;
   info->min_abs_lambda = p->min_abs_lambda;
   info->device_bytes = p->bytes + (p->fft ? fft_plan_bytes(p->fft) : 0);
+  info->star = p->host_pd.star1;
+  info->stored_weights = p->w64 ? 1 : 0;
   API_END
 }
 
@@ -1105,7 +1130,7 @@ qp_status qp_apply_stiffness(qp_plan* p, int nrhs, const void* U, void* QU, int 
   if (precision != QP_FP64 && precision != QP_FP32) raise(QP_ERR_INVALID_ARG, "precision must be QP_FP64 or QP_FP32");
   cudaStream_t s = S(stream);
   if (p->backend == QP_BACKEND_TAPS) {
-    const StarParams* st1 = p->host_pd.star1 ? &p->star_host : nullptr;
+    const StarParams* st1 = (p->host_pd.star1 && (precision == QP_FP32 || p->w64)) ? &p->star_host : nullptr;
     if (precision == QP_FP64)
       launch_apply_plain<double>(p->pd, p->real_coef, p->coef_count, p->D, nrhs, (const double2*)U, (double2*)QU,
                                  last_axis_run(p), st1, p->kind, s);

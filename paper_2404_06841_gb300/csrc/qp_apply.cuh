@@ -29,7 +29,8 @@ __device__ __forceinline__ void apply_chunk(const PlanDev& sp, const cplx<T>* sc
 #pragma unroll
         for (int r = 0; r < NR; ++r) acc[s][r] = (r < nrhs) ? dst[(size_t)r * D + e0 + s] : mk<T>(0, 0);
     } else if constexpr (SK != 0 && RUN == 2) {
-      apply_run_star<T, REALC, NR, true, SK == 2>(st, e0, src, D, nrhs, acc);
+      // FP64: the plan's stored weights; FP32: formed
+      apply_run_star<T, REALC, NR, true, SK == 2, sizeof(T) == 8 ? 1 : 0>(st, e0, src, D, nrhs, acc);
     } else {
       apply_run<T, REALC, NR, RUN>(sp, scoef, e0, src, D, nrhs, acc);
     }
@@ -231,7 +232,7 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 3)
   const int e0 = (blockIdx.x * BLOCK + threadIdx.x) * 2;
   if (e0 >= D) return;
   cplx<T> acc[2][NR];
-  apply_run_star<T, REALC, NR, true, SK == 2>(st, e0, h, D, nrhs, acc);
+  apply_run_star<T, REALC, NR, true, SK == 2, sizeof(T) == 8 ? 1 : 0>(st, e0, h, D, nrhs, acc);
 #pragma unroll
   for (int r = 0; r < NR; ++r) {
     if (r < nrhs) {
@@ -268,6 +269,15 @@ static void plain_nr(int nrhs, const PlanDev* plan_dev, int D, const cplx<T>* h,
     case 3: k_apply_plain<T, REALC, 3, RUN><<<nblk, BLOCK, smem, s>>>(plan_dev, D, nrhs, h, w); break;
     default: k_apply_plain<T, REALC, 4, RUN><<<nblk, BLOCK, smem, s>>>(plan_dev, D, nrhs, h, w); break;
   }
+}
+
+// The stored FP64 weights of a star-1 plan: one run of two modes per thread, the stencil's own arithmetic.
+template <bool REALC, bool DIAGK>
+__global__ void __launch_bounds__(BLOCK) k_star_weights(const __grid_constant__ StarParams st, int D, void* out) {
+  const int e0 = (blockIdx.x * BLOCK + threadIdx.x) * 2;
+  if (e0 >= D) return;
+  double2 acc[2][1];
+  apply_run_star<double, REALC, 1, true, DIAGK, 2>(st, e0, nullptr, D, 0, acc, out);
 }
 
 // run: modes per thread (2 when the last axis has even length, else 1). st1: the plan's StarParams when it is

@@ -93,7 +93,8 @@ struct alignas(16) StarParams {
   int woff[MAXN];               // (N_j - 1) stride_j
   int half[MAXN];               // ceil(N_j / 2)
   int has[MAXN];                // 1: the axis has the taps m = +-e_j
-  int n, d, pad_[2];
+  int n, d;
+  const void* w64;              // the plan's stored FP64 weights (see star_slots), or null
 };
 static_assert(sizeof(StarParams) % 16 == 0, "StarParams is copied to shared memory in 16-byte words");
 
@@ -226,6 +227,8 @@ void launch_apply(const BatchDev& b, bool realc, int mc, int maxr, int level, in
 template <typename T>
 void launch_apply_plain(const PlanDev* plan_dev, bool realc, int mc, int D, int nrhs, const cplx<T>* h, cplx<T>* w,
                         int run, const StarParams* st1, int kind, cudaStream_t s);
+// Writes a star-1 plan's FP64 weights per (tap slot, mode) to out: [1 + 2n][D] complex (double when realc).
+void launch_star_weights(const StarParams& st, bool realc, int kind, int D, void* out, cudaStream_t s);
 void launch_diag(const PlanDev* plan_dev, int mc, int D, double* jac, double* frob, float* jac32, float* frob32,
                  double* partials, unsigned* counter, double* out, int nblk, cudaStream_t s);
 void launch_rhs_taps(const PlanDev* plan_dev, int mc, int j0, int nrhs, int D, double2* F, cudaStream_t s);
@@ -263,8 +266,8 @@ struct PersistArgs {
   StarParams star;     // the unit's star-1 stencil data (kernels with sk != 0)
 };
 size_t persistent_smem(int coef_count);
-// sk: 0 the plan's stencil from shared memory; 1 / 2 a star-1 plan with a scalar / diagonal coefficient (its
-// StarParams st passed by value).
+// sk: 0 the plan's stencil from shared memory; 1 / 2 a star-1 plan with a scalar / diagonal coefficient and
+// stored FP64 weights (its StarParams st passed by value).
 int persistent_capacity(bool realc, int nr, int sk, size_t smem);
 void launch_persistent(const BatchDev& b, bool realc, int nr, int sk, const StarParams* st, int mode, bool warm,
                        unsigned* bar, int* err, double timeout_s, int grid, size_t smem, cudaStream_t s);

@@ -301,7 +301,9 @@ extern "C" qp_status qp_pcg_solve_taps_static(int d, int n, const double* P, con
 
     // warm start from U: w = Q U, r = F - w, then Algorithm 2 with the host polling the done count
     const bool realc = ht.real;
-    const StarParams* st1 = (ht.pd.star1 && run == 2) ? &ht.star : nullptr;   // passed by value to the kernels
+    // FP64 applies of a single star-1 unit take the kernel-parameter form only with stored weights, which this
+    // entry point has no room for: its kernels read the plan's star data from shared memory
+    const StarParams* st1 = nullptr;
     launch_level_reset(bd, 0, s);
     launch_apply(bd, realc, G * nc, nrhs, LEVEL_FP64, EPI_NONE, false, 0, nchunks, st1, ht.pd.kind, s);
     launch_pcg_init(bd, nrhs, LEVEL_FP64, true, 0, nchunks, s);

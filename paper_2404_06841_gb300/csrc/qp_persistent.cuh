@@ -150,7 +150,7 @@ __device__ __forceinline__ void ph_init(const BatchDev& b, const UnitDev& un, in
 // dst = Q src with the epilogue: EPI_DOT_HW reduces (src, dst); EPI_RESIDUAL writes F - Q src (0 at k = 0) and
 // reduces its norm and ||F||^2 over k != 0; EPI_NONE writes Q src.
 // SK: 0 the plan's stencil from shared memory; 1 / 2 the star-1 stencil of a scalar / diagonal coefficient
-// from st (the kernel parameter).
+// from st (the kernel parameter; FP64 from the plan's stored weights).
 template <typename T, bool REALC, int NR, int EPI, int SK>
 __device__ __forceinline__ void ph_apply(const BatchDev& b, const UnitDev& un, int c, const PlanDev& sp,
                                          const cplx<T>* scoef, const StarParams& st, const cplx<T>* src,
@@ -172,9 +172,10 @@ __device__ __forceinline__ void ph_apply(const BatchDev& b, const UnitDev& un, i
 #pragma unroll
         for (int r = 0; r < NR; ++r) acc[s][r] = mk<T>(0, 0);
     } else if constexpr (SK != 0) {
-      apply_run_star<T, REALC, NR, false, SK == 2>(st, e0, src, D, nrhs, acc);
+      // FP64 level: the plan's stored weights; FP32 level: formed
+      apply_run_star<T, REALC, NR, false, SK == 2, sizeof(T) == 8 ? 1 : 0>(st, e0, src, D, nrhs, acc);
     } else {
-      apply_run<T, REALC, NR, PRUN, false, false>(sp, scoef, e0, src, D, nrhs, acc);
+      apply_run<T, REALC, NR, PRUN, false>(sp, scoef, e0, src, D, nrhs, acc);   // star-1 plans: shared copy
     }
 #pragma unroll
     for (int s = 0; s < PRUN; ++s) {
@@ -422,7 +423,7 @@ __global__ void __launch_bounds__(BLOCK, NR >= 3 ? 1 : 2) k_pcg_persistent(const
   const bool refine = a.mode == QP_MODE_FP32_REFINE;
   // coefficient tables in shared memory: FP64, then (refinement) FP32
   double2* sc64 = reinterpret_cast<double2*>(smraw);
-  load_plan<double>(un.plan, sp, sc64);
+  load_plan<double, SK == 0>(un.plan, sp, sc64);
   const int nc = sp.ntaps * sp.ncomp;
   float2* sc32 = reinterpret_cast<float2*>(smraw + (size_t)nc * sizeof(double2));
   if (refine)

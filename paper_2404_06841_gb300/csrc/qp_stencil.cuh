@@ -98,10 +98,41 @@ template <typename T> __device__ __forceinline__ cplx<T> sp_c0(const StarParams&
 template <> __device__ __forceinline__ double2 sp_c0<double>(const StarParams& s, int a) { return s.c064[a]; }
 template <> __device__ __forceinline__ float2 sp_c0<float>(const StarParams& s, int a) { return s.c032[a]; }
 
-template <typename T, bool REALC, int NR, bool RO, bool DIAGK>
+// Weight slots of a star-1 plan's stored weights (StarParams.w64): 0 the mean tap, 1 + 2j / 2 + 2j the taps
+// m = +e_j / -e_j; [slot][D] complex (real for real tap values).
+__host__ __device__ constexpr int star_slots() { return 1 + 2 * MAXN; }
+
+template <bool REALC>
+__device__ __forceinline__ void wload(const StarParams& sp, int slot, int e0, int D, double2 (&c)[2]) {
+  if (REALC) {
+    const double2 v = __ldg(reinterpret_cast<const double2*>(static_cast<const double*>(sp.w64) + (size_t)slot * D + e0));
+    c[0] = make_double2(v.x, 0.0);
+    c[1] = make_double2(v.y, 0.0);
+  } else {
+    const double2* w = static_cast<const double2*>(sp.w64) + (size_t)slot * D + e0;
+    c[0] = __ldg(w);
+    c[1] = __ldg(w + 1);
+  }
+}
+template <bool REALC>
+__device__ __forceinline__ void wstore(void* out, int slot, int e0, int D, const double2 (&c)[2]) {
+  if (REALC) {
+    *reinterpret_cast<double2*>(static_cast<double*>(out) + (size_t)slot * D + e0) = make_double2(c[0].x, c[1].x);
+  } else {
+    double2* w = static_cast<double2*>(out) + (size_t)slot * D + e0;
+    w[0] = c[0];
+    w[1] = c[1];
+  }
+}
+
+// WM: 0 the weights are formed here; 1 (T = double) they are read from sp.w64; 2 (T = double) they are formed and
+// written to wout (the same arithmetic as WM = 0, so stored and formed weights agree bit for bit) and nothing
+// else is done.
+template <typename T, bool REALC, int NR, bool RO, bool DIAGK, int WM = 0>
 __device__ __forceinline__ void apply_run_star(const StarParams& sp, int e0, const cplx<T>* h, int D, int nrhs,
-                                               cplx<T> (&acc)[2][NR]) {
+                                               cplx<T> (&acc)[2][NR], void* wout = nullptr) {
   constexpr int NQ = DIAGK ? MAXD : 1;   // weight terms per mode: q_a (diagonal) or q (scalar)
+  constexpr bool FORM = WM != 1;         // the weights are formed from lambda
   const int d = sp.d, n = sp.n, jl = n - 1, Nl = sp.N[jl];
   // storage digits and signed modes of the run's first mode
   int ib[MAXN], k[MAXN];
@@ -131,7 +162,8 @@ __device__ __forceinline__ void apply_run_star(const StarParams& sp, int e0, con
 #pragma unroll
   for (int r = 0; r < NR; ++r) hr[r] = h + (size_t)r * D;
   T lk[2][MAXD];
-  {
+  T q[2][NQ];
+  if constexpr (FORM) {
     T lr[MAXD];
 #pragma unroll
     for (int a = 0; a < MAXD; ++a) {
@@ -147,18 +179,17 @@ __device__ __forceinline__ void apply_run_star(const StarParams& sp, int e0, con
       lk[0][a] = (a < d) ? fma(pl, (T)kl0, lr[a]) : T(0);
       lk[1][a] = (a < d) ? fma(pl, (T)kl1, lr[a]) : T(0);
     }
-  }
-  T q[2][NQ];
 #pragma unroll
-  for (int s = 0; s < 2; ++s) {
-    if (DIAGK) {
+    for (int s = 0; s < 2; ++s) {
+      if (DIAGK) {
 #pragma unroll
-      for (int a = 0; a < NQ; ++a) q[s][a] = lk[s][a] * lk[s][a];
-    } else {
-      q[s][0] = T(0);
+        for (int a = 0; a < NQ; ++a) q[s][a] = lk[s][a] * lk[s][a];
+      } else {
+        q[s][0] = T(0);
 #pragma unroll
-      for (int a = 0; a < MAXD; ++a)
-        if (a < d) q[s][0] = fma(lk[s][a], lk[s][a], q[s][0]);
+        for (int a = 0; a < MAXD; ++a)
+          if (a < d) q[s][0] = fma(lk[s][a], lk[s][a], q[s][0]);
+      }
     }
   }
   auto rterms = [&](int j, T (&rt)[2][NQ]) {
@@ -197,64 +228,83 @@ __device__ __forceinline__ void apply_run_star(const StarParams& sp, int e0, con
     }
     return c;
   };
+  // the weights of the taps m = +-e_j at the run's two modes: formed (dp, dm per mode) or read
+  auto pair_weights = [&](int j, const T (&dp)[2], const T (&dm)[2], cplx<T> (&wp)[2], cplx<T> (&wm)[2]) {
+    if constexpr (FORM) {
+      T rt[2][NQ];
+      rterms(j, rt);
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        wp[s] = wgt(j, 0, dp[s], q[s], rt[s]);
+        wm[s] = wgt(j, 1, dm[s], q[s], rt[s]);
+      }
+      if constexpr (WM == 2) {
+        wstore<REALC>(wout, 1 + 2 * j, e0, D, reinterpret_cast<const double2(&)[2]>(wp));
+        wstore<REALC>(wout, 2 + 2 * j, e0, D, reinterpret_cast<const double2(&)[2]>(wm));
+      }
+    } else {
+      wload<REALC>(sp, 1 + 2 * j, e0, D, reinterpret_cast<double2(&)[2]>(wp));
+      wload<REALC>(sp, 2 + 2 * j, e0, D, reinterpret_cast<double2(&)[2]>(wm));
+    }
+  };
   // mean tap and the last axis' taps, from the run's own values and one neighbour on each side
   {
     cplx<T> c0[2];
+    if constexpr (FORM) {
 #pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      if (DIAGK) {
-        c0[s] = mk<T>(0, 0);
+      for (int s = 0; s < 2; ++s) {
+        if (DIAGK) {
+          c0[s] = mk<T>(0, 0);
 #pragma unroll
-        for (int a = 0; a < MAXD; ++a) {
-          if (a < d) {
-            const cplx<T> ca = sp_c0<T>(sp, a);
-            c0[s].x = fma(ca.x, q[s][a], c0[s].x);
-            if (!REALC) c0[s].y = fma(ca.y, q[s][a], c0[s].y);
+          for (int a = 0; a < MAXD; ++a) {
+            if (a < d) {
+              const cplx<T> ca = sp_c0<T>(sp, a);
+              c0[s].x = fma(ca.x, q[s][a], c0[s].x);
+              if (!REALC) c0[s].y = fma(ca.y, q[s][a], c0[s].y);
+            }
           }
+        } else {
+          const cplx<T> ca = sp_c0<T>(sp, 0);
+          c0[s].x = ca.x * q[s][0];
+          c0[s].y = REALC ? T(0) : ca.y * q[s][0];
         }
-      } else {
-        const cplx<T> ca = sp_c0<T>(sp, 0);
-        c0[s].x = ca.x * q[s][0];
-        c0[s].y = REALC ? T(0) : ca.y * q[s][0];
       }
+      if constexpr (WM == 2) wstore<REALC>(wout, 0, e0, D, reinterpret_cast<const double2(&)[2]>(c0));
+    } else {
+      wload<REALC>(sp, 0, e0, D, reinterpret_cast<double2(&)[2]>(c0));
     }
     const bool has = sp.has[jl] != 0;
     cplx<T> wp[2], wm[2];
     int il = e0, ir = e0;
     if (has) {
-      T rt[2][NQ];
-      rterms(jl, rt);
       const int hl = sp.half[jl];
-      const T dp0 = (ibl == hl) ? T(Nl - 1) : T(-1);
-      const T dp1 = (ibl + 1 == hl) ? T(Nl - 1) : T(-1);
-      const T dm0 = (ibl == hl - 1) ? T(1 - Nl) : T(1);
-      const T dm1 = (ibl + 1 == hl - 1) ? T(1 - Nl) : T(1);
-      wp[0] = wgt(jl, 0, dp0, q[0], rt[0]);
-      wp[1] = wgt(jl, 0, dp1, q[1], rt[1]);
-      wm[0] = wgt(jl, 1, dm0, q[0], rt[0]);
-      wm[1] = wgt(jl, 1, dm1, q[1], rt[1]);
+      const T dp[2] = {(ibl == hl) ? T(Nl - 1) : T(-1), (ibl + 1 == hl) ? T(Nl - 1) : T(-1)};
+      const T dm[2] = {(ibl == hl - 1) ? T(1 - Nl) : T(1), (ibl + 1 == hl - 1) ? T(1 - Nl) : T(1)};
+      pair_weights(jl, dp, dm, wp, wm);
       il = e0 + ((ibl == 0) ? Nl - 1 : -1);       // k - e_l of the run's first mode
       ir = e0 + ((ibl + 2 == Nl) ? 2 - Nl : 2);   // k + e_l of its second mode
     }
+    if constexpr (WM != 2) {
 #pragma unroll
-    for (int r = 0; r < NR; ++r) {
-      if (r < nrhs) {
-        cplx<T> hv[2];
-        ld_run<RO, T, 2>(hr[r] + e0, hv);
-        cplx<T> a0 = mk<T>(0, 0), a1 = mk<T>(0, 0);
-        mac<T, REALC>(a0, c0[0], hv[0]);
-        mac<T, REALC>(a1, c0[1], hv[1]);
-        if (has) {
-          mac<T, REALC>(a0, wm[0], hv[1]);
-          mac<T, REALC>(a1, wp[1], hv[0]);
-          mac<T, REALC>(a0, wp[0], ldh<RO>(hr[r] + il));
-          mac<T, REALC>(a1, wm[1], ldh<RO>(hr[r] + ir));
+      for (int r = 0; r < NR; ++r) {
+        if (r < nrhs) {
+          cplx<T> hv[2];
+          ld_run<RO, T, 2>(hr[r] + e0, hv);
+          cplx<T> a0 = mk<T>(0, 0), a1 = mk<T>(0, 0);
+          mac<T, REALC>(a0, c0[0], hv[0]);
+          mac<T, REALC>(a1, c0[1], hv[1]);
+          if (has) {
+            mac<T, REALC>(a0, wm[0], hv[1]);
+            mac<T, REALC>(a1, wp[1], hv[0]);
+            mac<T, REALC>(a0, wp[0], ldh<RO>(hr[r] + il));
+            mac<T, REALC>(a1, wm[1], ldh<RO>(hr[r] + ir));
+          }
+          acc[0][r] = a0;
+          acc[1][r] = a1;
+        } else {
+          acc[0][r] = mk<T>(0, 0);
+          acc[1][r] = mk<T>(0, 0);
         }
-        acc[0][r] = a0;
-        acc[1][r] = a1;
-      } else {
-        acc[0][r] = mk<T>(0, 0);
-        acc[1][r] = mk<T>(0, 0);
       }
     }
   }
@@ -263,28 +313,25 @@ __device__ __forceinline__ void apply_run_star(const StarParams& sp, int e0, con
   for (int j = 0; j < MAXN - 1; ++j) {
     if (j < jl && sp.has[j]) {
       const int Nj = sp.N[j], ibj = ib[j], hj = sp.half[j];
-      T rt[2][NQ];
-      rterms(j, rt);
       const int ep = e0 + ((ibj == 0) ? sp.woff[j] : -sp.stride[j]);        // k - e_j (tap m = +e_j)
       const int em = e0 + ((ibj == Nj - 1) ? -sp.woff[j] : sp.stride[j]);   // k + e_j (tap m = -e_j)
-      const T dp = (ibj == hj) ? T(Nj - 1) : T(-1);
-      const T dm = (ibj == hj - 1) ? T(1 - Nj) : T(1);
+      const T dpj = (ibj == hj) ? T(Nj - 1) : T(-1);
+      const T dmj = (ibj == hj - 1) ? T(1 - Nj) : T(1);
+      const T dp[2] = {dpj, dpj}, dm[2] = {dmj, dmj};
       cplx<T> wp[2], wm[2];
+      pair_weights(j, dp, dm, wp, wm);
+      if constexpr (WM != 2) {
 #pragma unroll
-      for (int s = 0; s < 2; ++s) {
-        wp[s] = wgt(j, 0, dp, q[s], rt[s]);
-        wm[s] = wgt(j, 1, dm, q[s], rt[s]);
-      }
-#pragma unroll
-      for (int r = 0; r < NR; ++r) {
-        if (r < nrhs) {
-          cplx<T> hv[2];
-          ld_run<RO, T, 2>(hr[r] + ep, hv);
-          mac<T, REALC>(acc[0][r], wp[0], hv[0]);
-          mac<T, REALC>(acc[1][r], wp[1], hv[1]);
-          ld_run<RO, T, 2>(hr[r] + em, hv);
-          mac<T, REALC>(acc[0][r], wm[0], hv[0]);
-          mac<T, REALC>(acc[1][r], wm[1], hv[1]);
+        for (int r = 0; r < NR; ++r) {
+          if (r < nrhs) {
+            cplx<T> hv[2];
+            ld_run<RO, T, 2>(hr[r] + ep, hv);
+            mac<T, REALC>(acc[0][r], wp[0], hv[0]);
+            mac<T, REALC>(acc[1][r], wp[1], hv[1]);
+            ld_run<RO, T, 2>(hr[r] + em, hv);
+            mac<T, REALC>(acc[0][r], wm[0], hv[0]);
+            mac<T, REALC>(acc[1][r], wm[1], hv[1]);
+          }
         }
       }
     }

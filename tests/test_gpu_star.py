@@ -3,7 +3,8 @@ of the compressed mat-vec (Sec. 4.2): the weight lambda(k)^T C_t lambda(k -+ e_j
 lambda . P_j, and each axis wraps with one compare and one select. Checked against the oracle's wraparound
 convolution across the frequency wrap (k = ceil(N/2) - 1 <-> ceil(N/2) - N) and the storage wrap (axes of length
 2 and 3, odd lengths, axes without taps), in every execution form, batched beside other plans, and with its kernel
-parameter and shared-memory data sources giving bitwise the same iterates."""
+parameter and shared-memory data sources, and its stored FP64 entries Q_ij and the ones it forms, giving bitwise
+the same iterates."""
 import numpy as np
 import pytest
 
@@ -47,6 +48,9 @@ def _rand(nrhs, N, seed):
 def test_star_apply_matches_oracle(qp, case, nrhs):
     inst = _inst(case, 11)
     plan = qp.plan_from_instance(inst, max_rhs=4)
+    info = qp.qp_plan_query(plan)
+    # FP64 entries Q_ij are stored for star-1 plans with runs of two modes (even last axis)
+    assert info["star"] and info["stored_weights"] == (inst.N[-1] % 2 == 0)
     h = _rand(nrhs, inst.N, 3)
     op = O.Operator(inst)
     ref = np.stack([op(h[r]) for r in range(nrhs)])
@@ -97,6 +101,14 @@ def test_star_plans_batched_beside_others_bitwise(qp):
             assert np.array_equal(A, A1.real), inst.name
             A_ref, *_ = O.homogenized(inst, tol=1e-13)
             assert np.abs(A - A_ref).max() <= 1e-10 * np.abs(A_ref).max(), inst.name
+
+
+def test_general_taps_are_not_star(qp):
+    inst = W.random_instance(2, 3, (6, 4, 8), "sym", "taps", seed=23)
+    info = qp.qp_plan_query(qp.plan_from_instance(inst))
+    assert not info["star"] and not info["stored_weights"]
+    inst = W.random_instance(2, 3, (6, 4, 8), "scalar", "taps", seed=24)   # taps off the axes (|m|_inf <= 1)
+    assert not qp.qp_plan_query(qp.plan_from_instance(inst))["star"]
 
 
 def test_misaligned_vectors_are_rejected_before_any_launch(qp):
