@@ -173,9 +173,11 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 3) k_apply(BatchDe
   apply_units<T, EPI, REALC, NR, 0>(b, level, refine, cond, star_smem());
 }
 
-// Batch apply of a single star-1 unit (even last axis): the stencil data as a kernel parameter.
+// Batch apply of a single star-1 unit (even last axis): the stencil data as a kernel parameter. The FP32 star
+// stencil waits on L2 latency of its neighbour reads: four blocks per SM (64 registers) hide it best on GB300
+// (cfg4: 435 us at four blocks, 470 at three, 474 at five).
 template <typename T, int EPI, bool REALC, int NR, int SK>
-__global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 3)
+__global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 4)
     k_apply_star(BatchDev b, int level, int refine, unsigned long long cond, const __grid_constant__ StarParams st) {
   apply_units<T, EPI, REALC, NR, SK>(b, level, refine, cond, st);
 }
@@ -227,7 +229,7 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 3) k_apply_plain(c
 // Plain apply of a star-1 plan with an even last axis: the stencil data as a kernel parameter; one run of two
 // modes per thread.
 template <typename T, bool REALC, int NR, int SK>
-__global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 3)
+__global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 4)
     k_apply_plain_star(const __grid_constant__ StarParams st, int D, int nrhs, const cplx<T>* h, cplx<T>* w) {
   const int e0 = (blockIdx.x * BLOCK + threadIdx.x) * 2;
   if (e0 >= D) return;
