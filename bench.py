@@ -589,7 +589,9 @@ def run_solve_only(args):
     import paper_2404_06841_gb300 as qp
     inst = instance(args.workload, args.N)
     mode = qp.QP_MODE_FP64 if (args.mode or WORKLOADS[args.workload][1]) == "fp64" else qp.QP_MODE_FP32_REFINE
-    plan = qp.plan_from_instance(inst)
+    exec_mode = {"auto": qp.QP_EXEC_AUTO, "graph": qp.QP_EXEC_GRAPH, "direct": qp.QP_EXEC_DIRECT,
+                 "persistent": qp.QP_EXEC_PERSISTENT}[args.exec]
+    plan = qp.plan_from_instance(inst, exec_mode=exec_mode)
     F = torch.zeros((inst.d, inst.D), dtype=torch.complex128, device="cuda")
     qp.qp_corrector_rhs(plan, 0, inst.d, F)
     U = torch.zeros_like(F)

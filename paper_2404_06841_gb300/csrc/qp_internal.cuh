@@ -62,11 +62,13 @@ struct FastDiv {
   uint32_t p;
 };
 
-// Modes per chunk of a unit (a chunk is reduced by one block): 256..8192 modes, about 8 chunks per SM. It depends
-// on D only, so that a unit reduces in the same order alone or batched. (About two chunks per SM for small D,
-// which balances the FP64 apply across the SMs, measured no faster: per-iteration latency dominates there.)
+// Modes per chunk of a unit (a chunk is reduced by one block): 256..65536 modes, about 8 chunks per SM, so that a
+// large unit's chunked kernels run in about one wave of resident blocks (16^6 modes: 1214 chunks of 13,824; a cap
+// of 8192 gave 2048 chunks, 1.7 waves). It depends on D only, so that a unit reduces in the same order alone or
+// batched. (About two chunks per SM for small D, which balances the FP64 apply across the SMs, measured no
+// faster: per-iteration latency dominates there.)
 inline int64_t chunk_modes(int64_t D) {
-  return std::max<int64_t>(BLOCK, std::min<int64_t>(8192, (D / (152 * 8) + BLOCK - 1) / BLOCK * BLOCK));
+  return std::max<int64_t>(BLOCK, std::min<int64_t>(65536, (D / (152 * 8) + BLOCK - 1) / BLOCK * BLOCK));
 }
 
 inline FastDiv make_fastdiv(uint32_t d) {
