@@ -8,15 +8,17 @@ namespace qp {
 
 // ------------------------------------------------------------------------------------------------ batch apply
 
-// One chunk [base, end) of a unit: dst = Q src with the epilogue, per-thread partials into vt. Thread t takes
-// runs of RUN consecutive modes: e0 = base + RUN t, base + RUN (t + BLOCK), ...
+// One chunk (cl) of a unit: dst = Q src with the epilogue, per-thread partials into vt. Thread t takes the runs
+// of RUN consecutive modes chunk_runs gives it.
 // SK: the stencil's data source: 0 the plan in shared memory (apply_run), 1 / 2 the star-1 stencil of a scalar /
 // diagonal coefficient from st (a kernel parameter).
 template <typename T, int EPI, bool REALC, int NR, int RUN, int NV, int SK = 0>
-__device__ __forceinline__ void apply_chunk(const PlanDev& sp, const cplx<T>* scoef, const StarParams& st, int base,
-                                            int end, int D, int nrhs, int refine, bool fft_unit, const cplx<T>* src,
-                                            cplx<T>* dst, const cplx<T>* F, T (&vt)[NV]) {
-  for (int e0 = base + RUN * threadIdx.x; e0 < end; e0 += RUN * BLOCK) {
+__device__ __forceinline__ void apply_chunk(const PlanDev& sp, const cplx<T>* scoef, const StarParams& st,
+                                            const UnitDev& un, int cl, int D, int nrhs, int refine, bool fft_unit,
+                                            const cplx<T>* src, cplx<T>* dst, const cplx<T>* F, T (&vt)[NV]) {
+  int start, stride, limit;
+  chunk_runs(un, cl, RUN, start, stride, limit);
+  for (int e0 = start; e0 < limit; e0 += stride) {
     cplx<T> acc[RUN][NR];
     if (EPI == EPI_RESIDUAL && refine == REFINE_ZERO_U) {
 #pragma unroll
@@ -101,16 +103,15 @@ __device__ __forceinline__ void apply_units(const BatchDev& b, int level, int re
     double v[NV];
 #pragma unroll
     for (int q = 0; q < NV; ++q) vt[q] = T(0);
-    const int base = (c - un.chunk0) * un.chunk;
-    const int end = min(base + un.chunk, D);
+    const int cl = c - un.chunk0;
     // the unit's own run length (so that its reduction order does not depend on the batch)
     if constexpr (SK != 0) {
-      apply_chunk<T, EPI, REALC, NR, 2, NV, SK>(sp, scoef, stp, base, end, D, nrhs, refine, fft_unit, src, dst, F, vt);
+      apply_chunk<T, EPI, REALC, NR, 2, NV, SK>(sp, scoef, stp, un, cl, D, nrhs, refine, fft_unit, src, dst, F, vt);
     } else {
       if (un.run == 2)
-        apply_chunk<T, EPI, REALC, NR, 2, NV>(sp, scoef, stp, base, end, D, nrhs, refine, fft_unit, src, dst, F, vt);
+        apply_chunk<T, EPI, REALC, NR, 2, NV>(sp, scoef, stp, un, cl, D, nrhs, refine, fft_unit, src, dst, F, vt);
       else
-        apply_chunk<T, EPI, REALC, NR, 1, NV>(sp, scoef, stp, base, end, D, nrhs, refine, fft_unit, src, dst, F, vt);
+        apply_chunk<T, EPI, REALC, NR, 1, NV>(sp, scoef, stp, un, cl, D, nrhs, refine, fft_unit, src, dst, F, vt);
     }
     if (EPI == EPI_NONE) continue;
     block_reduce_mixed<T, NV>(vt, v);

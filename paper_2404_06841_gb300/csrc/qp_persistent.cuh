@@ -161,10 +161,10 @@ __device__ __forceinline__ void ph_apply(const BatchDev& b, const UnitDev& un, i
   double v[NV];
 #pragma unroll
   for (int q = 0; q < NV; ++q) vt[q] = T(0);
-  int base, end;
-  chunk_range(un, c, base, end);
   constexpr int PRUN = prun<T>();
-  for (int e0 = base + PRUN * threadIdx.x; e0 < end; e0 += PRUN * BLOCK) {
+  int start, stride, limit;
+  chunk_runs(un, c - un.chunk0, PRUN, start, stride, limit);   // the graph form's runs of this chunk
+  for (int e0 = start; e0 < limit; e0 += stride) {
     cplx<T> acc[PRUN][NR];
     if (zero_src) {   // src = 0: Q src = 0
 #pragma unroll
