@@ -84,7 +84,7 @@ __device__ __forceinline__ void apply_units(const BatchDev& b, int level, int re
     if (!active) continue;
     if (un.plan != cur) {
       cur = un.plan;
-      load_plan<T, SK == 0>(cur, sp, scoef);
+      load_plan<T>(cur, sp, scoef);
     }
     const int D = un.D;
     const cplx<T>* src;
@@ -168,10 +168,13 @@ __device__ __forceinline__ void apply_units(const BatchDev& b, int level, int re
   }
 }
 
+// Stands in for the kernel-parameter StarParams in kernels that read each plan's own (never dereferenced).
+static __device__ StarParams g_no_star;
+
 // Batch apply over every chunk of the batch (plans from the unit table, in shared memory).
 template <typename T, int EPI, bool REALC, int NR>
 __global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 3) k_apply(BatchDev b, int level, int refine, unsigned long long cond) {
-  apply_units<T, EPI, REALC, NR, 0>(b, level, refine, cond, star_smem());
+  apply_units<T, EPI, REALC, NR, 0>(b, level, refine, cond, g_no_star);
 }
 
 // Batch apply of a single star-1 unit (even last axis): the stencil data as a kernel parameter. The FP32 star
@@ -215,7 +218,7 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 3) k_apply_plain(c
   __shared__ __align__(16) PlanDev sp;
   extern __shared__ __align__(16) unsigned char smraw[];
   cplx<T>* scoef = reinterpret_cast<cplx<T>*>(smraw);
-  load_plan<T, true>(plan, sp, scoef);
+  load_plan<T>(plan, sp, scoef);
   const int e0 = (blockIdx.x * BLOCK + threadIdx.x) * RUN;   // one run per thread: blocks sweep memory in order
   if (e0 >= D) return;
   cplx<T> acc[RUN][NR];

@@ -423,7 +423,7 @@ __global__ void __launch_bounds__(BLOCK, NR >= 3 ? 1 : 2) k_pcg_persistent(const
   const bool refine = a.mode == QP_MODE_FP32_REFINE;
   // coefficient tables in shared memory: FP64, then (refinement) FP32
   double2* sc64 = reinterpret_cast<double2*>(smraw);
-  load_plan<double, SK == 0>(un.plan, sp, sc64);
+  load_plan<double>(un.plan, sp, sc64);
   const int nc = sp.ntaps * sp.ncomp;
   float2* sc32 = reinterpret_cast<float2*>(smraw + (size_t)nc * sizeof(double2));
   if (refine)

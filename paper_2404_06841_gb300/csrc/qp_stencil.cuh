@@ -29,26 +29,14 @@ __device__ __forceinline__ void ld_run(const cplx<T>* p, cplx<T> (&v)[RUN]) {
 }
 
 
-// The block's shared copy of the plan's StarParams (kernels that serve several plans).
-__device__ __forceinline__ StarParams& star_smem() {
-  __shared__ StarParams s_star;
-  return s_star;
-}
-
-// Copies the plan description and its coefficient table (precision T) to shared memory; STAR: also the
-// plan's StarParams (star-1 plans), which the stencil kernels read through star_smem().
-template <typename T, bool STAR = false>
+// Copies the plan description and its coefficient table (precision T) to shared memory.
+template <typename T>
 __device__ __forceinline__ void load_plan(const PlanDev* src, PlanDev& dst, cplx<T>* coef) {
   __syncthreads();
   const int4* s = reinterpret_cast<const int4*>(src);
   int4* d = reinterpret_cast<int4*>(&dst);
   for (int i = threadIdx.x; i < (int)(sizeof(PlanDev) / sizeof(int4)); i += BLOCK) d[i] = s[i];
   __syncthreads();
-  if (STAR && dst.star1) {
-    const int4* ss = reinterpret_cast<const int4*>(dst.star);
-    int4* sd = reinterpret_cast<int4*>(&star_smem());
-    for (int i = threadIdx.x; i < (int)(sizeof(StarParams) / sizeof(int4)); i += BLOCK) sd[i] = ss[i];
-  }
   const int nc = dst.ntaps * dst.ncomp;
   if (sizeof(T) == 8) {
     const double2* c = dst.coef64;
@@ -338,8 +326,22 @@ __device__ __forceinline__ void apply_run_star(const StarParams& sp, int e0, con
   }
 }
 
+// The star-1 run as a call of its own in kernels that also run the general stencil (batches of several plans):
+// its registers are then allocated apart from the general stencil's, which keeps that one's register budget.
+template <typename T, bool REALC, int NR, bool RO>
+__device__ __noinline__ void star_run_call(const StarParams* st, bool diag, int e0, const cplx<T>* h, int D, int nrhs,
+                                           cplx<T>* out) {
+  cplx<T> acc[2][NR];
+  if (diag) apply_run_star<T, REALC, NR, RO, true>(*st, e0, h, D, nrhs, acc);
+  else apply_run_star<T, REALC, NR, RO, false>(*st, e0, h, D, nrhs, acc);
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+#pragma unroll
+    for (int r = 0; r < NR; ++r) out[s * NR + r] = acc[s][r];
+}
+
 // acc[s][r] = (Q h_r)(e0 + s), s < RUN: the whole tap sum at RUN consecutive modes (STAR: a star-1 plan takes the
-// star-1 stencil from the block's shared StarParams; kernels that never see one leave it out) of one row of the last
+// star-1 stencil with its StarParams from global memory; kernels that never see one leave it out) of one row of the last
 // axis (e0 a multiple of RUN, RUN dividing N_{n-1}). Everything that depends only on the row is done once per
 // run: the digits of e0, lambda over the other axes, and for every tap along another axis its wrapped offset and
 // its mode step dk; that tap then reads RUN consecutive entries of h. The weights are formed per mode:
@@ -348,9 +350,8 @@ template <typename T, bool REALC, int NR, int RUN, bool RO = true, bool STAR = t
 __device__ __forceinline__ void apply_run(const PlanDev& p, const cplx<T>* __restrict__ sc, int e0,
                                           const cplx<T>* h, int D, int nrhs, cplx<T> (&acc)[RUN][NR]) {
   if constexpr (RUN == 2 && STAR) {
-    if (p.star1) {   // the block's shared StarParams (load_plan<T, true>)
-      if (p.kind == QP_COEF_DIAG) apply_run_star<T, REALC, NR, RO, true>(star_smem(), e0, h, D, nrhs, acc);
-      else apply_run_star<T, REALC, NR, RO, false>(star_smem(), e0, h, D, nrhs, acc);
+    if (p.star1) {   // the plan's StarParams read from global memory (L1-resident across the block)
+      star_run_call<T, REALC, NR, RO>(p.star, p.kind == QP_COEF_DIAG, e0, h, D, nrhs, &acc[0][0]);
       return;
     }
   }
