@@ -62,13 +62,16 @@ struct FastDiv {
   uint32_t p;
 };
 
-// Modes per chunk of a unit (a chunk is reduced by one block): 256..65536 modes, about 8 chunks per SM, so that a
-// large unit's chunked kernels run in about one wave of resident blocks (16^6 modes: 1214 chunks of 13,824; a cap
-// of 8192 gave 2048 chunks, 1.7 waves). It depends on D only, so that a unit reduces in the same order alone or
-// batched. (About two chunks per SM for small D, which balances the FP64 apply across the SMs, measured no
-// faster: per-iteration latency dominates there.)
+// Modes per chunk of a unit (a chunk is reduced by one block): about 8 chunks per SM, at most 65,536 modes, so that
+// a large unit's chunked kernels run in about one wave of resident blocks (16^6 modes: 1214 chunks of 13,824; a
+// cap of 8192 gave 2048 chunks, 1.7 waves); at least 512 modes from 32,768 modes up, so that the stencil's runs of
+// two modes keep every thread of a block busy (256-mode chunks left half of each block idle: cfg1's FP64 solve
+// 1.12 -> 0.98 ms, the batched cfg3 24.5 -> 19.6 ms), and 256 below, where fewer blocks would cost more than the idle
+// threads (1,024 modes: 0.51 -> 0.58 ms with 512). It depends on D only, so that a unit reduces in the same order
+// alone or batched.
 inline int64_t chunk_modes(int64_t D) {
-  return std::max<int64_t>(BLOCK, std::min<int64_t>(65536, (D / (152 * 8) + BLOCK - 1) / BLOCK * BLOCK));
+  const int64_t lo = D >= 32768 ? 2 * BLOCK : BLOCK;
+  return std::max<int64_t>(lo, std::min<int64_t>(65536, (D / (152 * 8) + BLOCK - 1) / BLOCK * BLOCK));
 }
 
 inline FastDiv make_fastdiv(uint32_t d) {
