@@ -36,6 +36,25 @@ __device__ __forceinline__ void apply_chunk(const PlanDev& sp, const cplx<T>* sc
     } else {
       apply_run<T, REALC, NR, RUN>(sp, scoef, e0, src, D, nrhs, acc);
     }
+    if constexpr (RUN == 2 && sizeof(T) == 4 && EPI != EPI_RESIDUAL) {
+      // FP32 runs of two: one 16-byte store (and load of h) per right-hand side; the sums in the order below
+      if (!fft_unit) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          if (r < nrhs) {
+            const size_t o = (size_t)r * D + e0;
+            *reinterpret_cast<float4*>(dst + o) = make_float4((float)acc[0][r].x, (float)acc[0][r].y,
+                                                              (float)acc[1][r].x, (float)acc[1][r].y);
+            if (EPI == EPI_DOT_HW) {
+              const float4 hv = __ldg(reinterpret_cast<const float4*>(src + o));
+              vt[r] = fma((T)hv.x, acc[0][r].x, fma((T)hv.y, acc[0][r].y, vt[r]));
+              vt[r] = fma((T)hv.z, acc[1][r].x, fma((T)hv.w, acc[1][r].y, vt[r]));
+            }
+          }
+        }
+        continue;
+      }
+    }
 #pragma unroll
     for (int s = 0; s < RUN; ++s) {
       const int e = e0 + s;

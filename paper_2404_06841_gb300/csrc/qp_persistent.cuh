@@ -175,7 +175,23 @@ __device__ __forceinline__ void ph_apply(const BatchDev& b, const UnitDev& un, i
       // FP64 level: the plan's stored weights; FP32 level: formed
       apply_run_star<T, REALC, NR, false, SK == 2, sizeof(T) == 8 ? 1 : 0>(st, e0, src, D, nrhs, acc);
     } else {
-      apply_run<T, REALC, NR, PRUN, false>(sp, scoef, e0, src, D, nrhs, acc);   // star-1 plans: shared copy
+      apply_run<T, REALC, NR, PRUN, false>(sp, scoef, e0, src, D, nrhs, acc);
+    }
+    if constexpr (sizeof(T) == 4 && EPI == EPI_DOT_HW) {
+      // FP32: one 16-byte store and load per right-hand side, the sums in the graph form's order (plain loads:
+      // this kernel writes h in another phase)
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        if (r < nrhs) {
+          const size_t o = (size_t)r * D + e0;
+          *reinterpret_cast<float4*>(dst + o) = make_float4((float)acc[0][r].x, (float)acc[0][r].y,
+                                                            (float)acc[1][r].x, (float)acc[1][r].y);
+          const float4 hv = *reinterpret_cast<const float4*>(src + o);
+          vt[r] = fma((T)hv.x, acc[0][r].x, fma((T)hv.y, acc[0][r].y, vt[r]));
+          vt[r] = fma((T)hv.z, acc[1][r].x, fma((T)hv.w, acc[1][r].y, vt[r]));
+        }
+      }
+      continue;
     }
 #pragma unroll
     for (int s = 0; s < PRUN; ++s) {
