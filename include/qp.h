@@ -92,8 +92,8 @@ typedef struct {
 typedef struct {
   double tol;         /* stop when ||F - Q U||_2 <= tol ||F||_2 (Fourier coefficients; Parseval) */
   int maxit;          /* PCG iteration cap (all inner iterations in refinement mode) */
-  int precond;        /* QP_PRECOND_JACOBI (diagonal of Q) or QP_PRECOND_FROBENIUS (eq. preconditioner; on the FFT
-                         backend built on first use, see qp_plan_diagonal) */
+  int precond;        /* QP_PRECOND_JACOBI (diagonal of Q) or QP_PRECOND_FROBENIUS (eq. preconditioner; built on
+                         first use, see qp_plan_diagonal) */
   int mode;           /* QP_MODE_FP64: FP64 vectors and operator; QP_MODE_FP32_REFINE: FP32 inner PCG in an
                          FP64 iterative-refinement loop (FP64 true residual, FP64 dot products) */
   double inner_tol;   /* refinement: relative tolerance of each inner FP32 solve (0 = 1e-5) */
@@ -122,8 +122,10 @@ typedef struct {
 
 /* Creates a plan: validates d (1..3), n (d..6), P (host double d x n, row-major, Sec. 2.1 projection
  * matrix), N (host int[n], 2..1024 each, products of 2 and 3 for the FFT backend), the coefficient, and builds
- * the per-axis lambda tables, the coefficient representation, and the Jacobi and Frobenius diagonals
- * (Sec. 4.3, eq. preconditioner; O(gD) for taps). Work runs on "stream"; the call synchronises it. */
+ * the per-axis lambda tables, the coefficient representation, the Jacobi diagonal (Sec. 4.3; the Frobenius-optimal
+ * one, eq. preconditioner, is built on first use), for a star-1 taps plan its stored FP64 entries Q_ij (see
+ * qp_plan_info), and for the FFT backend its autotuned apply schedule. Work runs on "stream"; the call
+ * synchronises it. */
 qp_status qp_plan_create(int d, int n, const double* P, const int* N, const qp_coeff* coeff,
                          const qp_options* opt, void* stream, qp_plan** out);
 /* Waits for all work on the device (no stream may still use the plan), then returns the plan's device memory to
@@ -194,8 +196,8 @@ qp_status qp_pcg_solve_taps_static(int d, int n, const double* P, const int* N, 
 /* The diagonal preconditioner of a solve, z = M r (Sec. 4.3): QP_PRECOND_JACOBI gives M(k) = 1/q(k), q the diagonal
  * of Q; QP_PRECOND_FROBENIUS gives the Frobenius-optimal M(k) = q(k)/||Q e_k||^2 (eq. preconditioner): on the taps
  * backend from the O(gD) column sums, on the FFT backend from FFT cross-correlations of lambda_a lambda_a' with
- * A~^{ab} conj(A~^{a'b'}) (d^4 + d(d+1) FP64 n-dim DFTs plus ~(5 + d(d+1)/2) x 16 B x D of temporary device memory,
- * done once, on this call or the first Frobenius solve). M(0) = 0 (the excluded mode). out: device double[D].
+ * A~^{ab} conj(A~^{a'b'}) (d^4 + d(d+1) FP64 n-dim DFTs plus ~(5 + d(d+1)/2) x 16 B x D of temporary device memory);
+ * on either backend done once, on this call or the first Frobenius solve. M(0) = 0 (the excluded mode). out: device double[D].
  * Synchronises stream. */
 qp_status qp_plan_diagonal(qp_plan* plan, int precond, double* out, void* stream);
 

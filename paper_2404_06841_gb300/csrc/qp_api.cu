@@ -73,7 +73,7 @@ struct qp_plan {
 
   double* jac64 = nullptr;
   double* frob64 = nullptr;
-  bool frob_ready = false;          // the Frobenius diagonal is built (taps: at creation; FFT: on first use)
+  bool frob_ready = false;          // the Frobenius diagonal is built (on first use)
   float* jac32 = nullptr;
   float* frob32 = nullptr;
 
@@ -896,7 +896,13 @@ void check_opts(const qp_solve_opts* o, const qp_plan* p) {
 // diagonal, on first request).
 void prepare_precond(qp_plan* p, int precond, cudaStream_t s) {
   if (precond != QP_PRECOND_FROBENIUS || p->frob_ready) return;
-  fft_frobenius(p->fft, p->host_pd, p->pd, p->frob64, p->frob32, s);
+  if (p->backend == QP_BACKEND_TAPS) {
+    launch_diag(p->pd, p->coef_count, p->D, p->jac64, p->frob64, p->jac32, p->frob32, p->scratch, p->counter,
+                p->small, p->nblk, true, s);
+    CK_LAUNCH();
+  } else {
+    fft_frobenius(p->fft, p->host_pd, p->pd, p->frob64, p->frob32, s);
+  }
   p->frob_ready = true;
 }
 
@@ -1072,9 +1078,8 @@ qp_status qp_plan_create(int d, int n, const double* P, const int* N, const qp_c
   if (p->backend == QP_BACKEND_TAPS) {
     CK(cudaMemcpyAsync(p->pd, &p->host_pd, sizeof(PlanDev), cudaMemcpyHostToDevice, s));
     launch_diag(p->pd, p->coef_count, p->D, p->jac64, p->frob64, p->jac32, p->frob32, p->scratch, p->counter,
-                p->small, p->nblk, s);
+                p->small, p->nblk, false, s);
     CK_LAUNCH();
-    p->frob_ready = true;
     build_star_weights(p.get(), s);
   } else {
     CK(cudaMemcpyAsync(p->pd, &p->host_pd, sizeof(PlanDev), cudaMemcpyHostToDevice, s));

@@ -234,8 +234,9 @@ void launch_apply_plain(const PlanDev* plan_dev, bool realc, int mc, int D, int 
                         int run, const StarParams* st1, int kind, cudaStream_t s);
 // Writes a star-1 plan's FP64 weights per (tap slot, mode) to out: [1 + 2n][D] complex (double when realc).
 void launch_star_weights(const StarParams& st, bool realc, int kind, int D, void* out, cudaStream_t s);
+// with_frob: also the Frobenius-optimal diagonal (else frob / frob32 are not written).
 void launch_diag(const PlanDev* plan_dev, int mc, int D, double* jac, double* frob, float* jac32, float* frob32,
-                 double* partials, unsigned* counter, double* out, int nblk, cudaStream_t s);
+                 double* partials, unsigned* counter, double* out, int nblk, bool with_frob, cudaStream_t s);
 void launch_rhs_taps(const PlanDev* plan_dev, int mc, int j0, int nrhs, int D, double2* F, cudaStream_t s);
 void launch_astar_taps(const PlanDev* plan_dev, int mc, int D, const double2* U, double* out, cudaStream_t s);
 

@@ -253,7 +253,8 @@ extern "C" qp_status qp_pcg_solve_taps_static(int d, int n, const double* P, con
     if (ht.pd.star1) CK(cudaMemcpyAsync(d_star, &ht.star, sizeof(StarParams), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(d_c64, ht.c64, (size_t)G * nc * sizeof(double2), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(d_c32, ht.c32, (size_t)G * nc * sizeof(float2), cudaMemcpyHostToDevice, s));
-    launch_diag(d_pd, G * nc, D, jac64, frob64, jac32, frob32, partials, counters + 2, small, nblk_diag, s);
+    launch_diag(d_pd, G * nc, D, jac64, frob64, jac32, frob32, partials, counters + 2, small, nblk_diag,
+                opts->precond == QP_PRECOND_FROBENIUS, s);
     CK_LAUNCH();
     double chk[2] = {0.0, 0.0};
     CK(cudaMemcpyAsync(chk, small, sizeof(chk), cudaMemcpyDeviceToHost, s));

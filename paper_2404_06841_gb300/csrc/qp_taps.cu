@@ -67,8 +67,10 @@ __device__ __forceinline__ void lambda_shift(const PlanDev& p, const int (&ib)[M
 // Jacobi diagonal q(k) = lambda(k)^T A~_0 lambda(k) and the Frobenius-optimal diagonal q(k) / ||Q e_k||^2
 // (eq. preconditioner) with ||Q e_k||^2 = sum_t |lambda(k +N m_t)^T C_t lambda(k)|^2 (O(gD), Sec. 4.3).
 // Stored as M (z = M r), M(0) = 0. out[0] = min over k != 0 of |lambda(k)|^2, out[1] = min q / |lambda|^2.
+// with_frob = 0: the Jacobi diagonal only (the Frobenius one costs a weight per tap and mode: built on first use).
 __global__ void __launch_bounds__(BLOCK) k_diag(const PlanDev* plan, int D, double* jac, double* frob, float* jac32,
-                                                float* frob32, double* partials, unsigned* counter, double* out) {
+                                                float* frob32, double* partials, unsigned* counter, double* out,
+                                                int with_frob) {
   __shared__ __align__(16) PlanDev sp;
   extern __shared__ __align__(16) unsigned char smraw[];
   double2* scoef = reinterpret_cast<double2*>(smraw);
@@ -85,7 +87,7 @@ __global__ void __launch_bounds__(BLOCK) k_diag(const PlanDev* plan, int D, doub
     for (int a = 0; a < d; ++a) l2sum += lk[a] * lk[a];
     const double q = weight_general<double>(sp.kind, d, scoef, lk, lk).x;
     double cn = 0.0;
-    for (int t = 0; t < sp.ntaps; ++t) {
+    for (int t = 0; with_frob && t < sp.ntaps; ++t) {
       double lv[MAXD];
       lambda_shift(sp, ib, k, sp.m[t], +1, lk, lv);
       const double2 c = weight_general<double>(sp.kind, d, scoef + t * sp.ncomp, lv, lk);
@@ -99,9 +101,11 @@ __global__ void __launch_bounds__(BLOCK) k_diag(const PlanDev* plan, int D, doub
       red[1] = fmin(red[1], l2sum > 0.0 ? q / l2sum : -1.0);
     }
     jac[e] = mj;
-    frob[e] = mf;
     jac32[e] = (float)mj;
-    frob32[e] = (float)mf;
+    if (with_frob) {
+      frob[e] = mf;
+      frob32[e] = (float)mf;
+    }
   }
   block_reduce<2, true>(red);
   __shared__ int is_last;
@@ -124,9 +128,9 @@ __global__ void __launch_bounds__(BLOCK) k_diag(const PlanDev* plan, int D, doub
 }
 
 void launch_diag(const PlanDev* plan_dev, int mc, int D, double* jac, double* frob, float* jac32, float* frob32,
-                 double* partials, unsigned* counter, double* out, int nblk, cudaStream_t s) {
+                 double* partials, unsigned* counter, double* out, int nblk, bool with_frob, cudaStream_t s) {
   const size_t smem = (size_t)mc * sizeof(double2);
-  k_diag<<<nblk, BLOCK, smem, s>>>(plan_dev, D, jac, frob, jac32, frob32, partials, counter, out);
+  k_diag<<<nblk, BLOCK, smem, s>>>(plan_dev, D, jac, frob, jac32, frob32, partials, counter, out, with_frob ? 1 : 0);
   count_launch();
 }
 
