@@ -129,7 +129,8 @@ typedef struct {
 qp_status qp_plan_create(int d, int n, const double* P, const int* N, const qp_coeff* coeff,
                          const qp_options* opt, void* stream, qp_plan** out);
 /* Waits for all work on the device (no stream may still use the plan), then returns the plan's device memory to
- * the library's pool (blocks are kept cached for the next plans; beyond 1 GiB they go back to the device). */
+ * the library's pool (blocks are kept cached for the next plans; beyond an eighth of the device's memory, at
+ * least 1 GiB, they go back to the device). */
 qp_status qp_plan_destroy(qp_plan* plan);
 qp_status qp_plan_query(const qp_plan* plan, qp_plan_info* info);
 

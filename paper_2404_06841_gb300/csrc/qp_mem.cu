@@ -1,8 +1,10 @@
 // Memory for plans, solvers and batches. Device buffers come from a library-owned stream-ordered pool per device
 // whose release threshold keeps freed blocks cached, so creating and destroying plans repeatedly (one plan per
 // request) reuses memory instead of calling cudaMalloc / cudaFree, each of which synchronises the device; a
-// destroy trims the pool back to 1 GiB, so a large plan's memory returns to the device. Small page-locked host
+// destroy trims the pool back to an eighth of the device's memory (at least 1 GiB: 35 GB on a GB300), so a
+// request-sized plan is reused whole while the memory of an exceptionally large one returns to the device. Small page-locked host
 // mirrors (solver state, a*) come from a process-wide cache by size class for the same reason.
+#include <algorithm>
 #include <cstdint>
 #include <map>
 #include <mutex>
@@ -63,13 +65,17 @@ void dev_free(void* p) {
   if (p) cudaFreeAsync(p, 0);
 }
 
-// After a plan's buffers went back to the pool: keep up to 1 GiB cached for the next plans, return the rest.
+// After a plan's buffers went back to the pool: keep up to an eighth of the device memory (at least 1 GiB)
+// cached for the next plans, return the rest.
 void dev_trim() {
   cudaStreamSynchronize(0);
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) tot = 0;
+  const size_t keep = std::max<size_t>((size_t)1 << 30, tot / 8);
   std::lock_guard<std::mutex> lock(g_pool_mutex);
-  if (g_pools[dev]) cudaMemPoolTrimTo(g_pools[dev], (size_t)1 << 30);
+  if (g_pools[dev]) cudaMemPoolTrimTo(g_pools[dev], keep);
 }
 
 void* pinned_alloc(size_t bytes) {
