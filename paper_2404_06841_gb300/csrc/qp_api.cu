@@ -407,9 +407,10 @@ void build_taps(qp_plan* p, const qp_coeff* c) {
 
 // FP64 weights of a star-1 plan stored per (tap slot, mode). The compressed format of Sec. 4.2 keeps the nonzero
 // entries Q_ij of the stiffness matrix; on this GPU, where FP64 arithmetic runs at 1/64 of the FP32 rate, reading
-// them once per apply is cheaper than forming them, so FP64 applies of a single plan read them. They are formed
-// by the stencil's own arithmetic, so stored and formed weights agree bit for bit (a batch of several plans forms
-// them). Built when the plan has FP64 vectors and the table takes at most a quarter of the free device memory.
+// them once per apply is cheaper than forming them, so every FP64 apply of the plan reads them (single-plan
+// kernels through the kernel-parameter StarParams, batches of several plans through its device copy). They are
+// formed by the stencil's own arithmetic, so stored and formed weights agree bit for bit. Built when the plan has
+// FP64 vectors and the table takes at most a quarter of the free device memory.
 void build_star_weights(qp_plan* p, cudaStream_t s) {
   const PlanDev& pd = p->host_pd;
   if (!pd.star1 || !(p->precisions & 1) || pd.N[pd.n - 1] % 2 != 0) return;
@@ -419,8 +420,11 @@ void build_star_weights(qp_plan* p, cudaStream_t s) {
   if (bytes > fr / 4) return;
   p->w64 = p->dalloc(bytes);
   p->star_host.w64 = p->w64;
+  p->star_host.wreal = p->real_coef ? 1 : 0;
   launch_star_weights(p->star_host, p->real_coef, p->kind, p->D, p->w64, s);
   CK_LAUNCH();
+  // the device copy of the StarParams (read by batches of several plans) points at the table too
+  CK(cudaMemcpyAsync(const_cast<StarParams*>(pd.star), &p->star_host, sizeof(StarParams), cudaMemcpyHostToDevice, s));
 }
 
 void alloc_workspace(qp_plan* p) {

@@ -85,7 +85,7 @@ inline FastDiv make_fastdiv(uint32_t d) {
 // Everything the star-1 stencil reads besides the vectors: the geometry, P, and the coefficients of the mean
 // tap and of the taps m = +e_j, m = -e_j of every axis, at fixed offsets. A kernel that serves one plan takes it
 // by value as a kernel parameter (read from the constant bank, so that the stencil's only L1 traffic is the
-// vectors); a kernel over several plans copies it to shared memory.
+// vectors); a kernel over several plans reads the plan's device copy.
 struct alignas(16) StarParams {
   double2 c64[MAXN][2][MAXD];   // [axis j][0: m = +e_j, 1: m = -e_j][component]
   double2 c064[MAXD];           // the mean tap
@@ -99,9 +99,11 @@ struct alignas(16) StarParams {
   int half[MAXN];               // ceil(N_j / 2)
   int has[MAXN];                // 1: the axis has the taps m = +-e_j
   int n, d;
+  int wreal, pad_;              // 1: w64 holds real weights (8 bytes each; real tap values), else complex (16 bytes)
   const void* w64;              // the plan's stored FP64 weights (see star_slots), or null
+  const void* pad_ptr_;
 };
-static_assert(sizeof(StarParams) % 16 == 0, "StarParams is copied to shared memory in 16-byte words");
+static_assert(sizeof(StarParams) % 16 == 0, "StarParams is uploaded and passed as 16-byte words");
 
 // Device description of one plan's geometry and (for the taps backend) its taps, sorted as
 // [mean tap][star taps of axis 0] .. [star taps of axis n-1][taps with several nonzero axes].

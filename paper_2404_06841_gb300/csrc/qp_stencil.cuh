@@ -90,9 +90,10 @@ template <> __device__ __forceinline__ float2 sp_c0<float>(const StarParams& s, 
 // m = +e_j / -e_j; [slot][D] complex (real for real tap values).
 __host__ __device__ constexpr int star_slots() { return 1 + 2 * MAXN; }
 
+// (a kernel for complex taps may serve a plan with real ones, whose table then has the real layout)
 template <bool REALC>
 __device__ __forceinline__ void wload(const StarParams& sp, int slot, int e0, int D, double2 (&c)[2]) {
-  if (REALC) {
+  if (REALC || sp.wreal) {
     const double2 v = __ldg(reinterpret_cast<const double2*>(static_cast<const double*>(sp.w64) + (size_t)slot * D + e0));
     c[0] = make_double2(v.x, 0.0);
     c[1] = make_double2(v.y, 0.0);
@@ -328,10 +329,22 @@ __device__ __forceinline__ void apply_run_star(const StarParams& sp, int e0, con
 
 // The star-1 run as a call of its own in kernels that also run the general stencil (batches of several plans):
 // its registers are then allocated apart from the general stencil's, which keeps that one's register budget.
+// FP64 runs read the plan's stored entries Q_ij where it has them (bitwise the weights formed here).
 template <typename T, bool REALC, int NR, bool RO>
 __device__ __noinline__ void star_run_call(const StarParams* st, bool diag, int e0, const cplx<T>* h, int D, int nrhs,
                                            cplx<T>* out) {
   cplx<T> acc[2][NR];
+  if constexpr (sizeof(T) == 8) {
+    if (st->w64 != nullptr) {
+      if (diag) apply_run_star<T, REALC, NR, RO, true, 1>(*st, e0, h, D, nrhs, acc);
+      else apply_run_star<T, REALC, NR, RO, false, 1>(*st, e0, h, D, nrhs, acc);
+#pragma unroll
+      for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int r = 0; r < NR; ++r) out[s * NR + r] = acc[s][r];
+      return;
+    }
+  }
   if (diag) apply_run_star<T, REALC, NR, RO, true>(*st, e0, h, D, nrhs, acc);
   else apply_run_star<T, REALC, NR, RO, false>(*st, e0, h, D, nrhs, acc);
 #pragma unroll
