@@ -12,7 +12,7 @@ namespace qp {
 // of RUN consecutive modes chunk_runs gives it.
 // SK: the stencil's data source: 0 the plan in shared memory (apply_run), 1 / 2 the star-1 stencil of a scalar /
 // diagonal coefficient from st (a kernel parameter).
-template <typename T, int EPI, bool REALC, int NR, int RUN, int NV, int SK = 0>
+template <typename T, int EPI, bool REALC, int NR, int RUN, int NV, int SK = 0, int NAX = 0, int DC = 0>
 __device__ __forceinline__ void apply_chunk(const PlanDev& sp, const cplx<T>* scoef, const StarParams& st,
                                             const UnitDev& un, int cl, int D, int nrhs, int refine, bool fft_unit,
                                             const cplx<T>* src, cplx<T>* dst, const cplx<T>* F, T (&vt)[NV]) {
@@ -32,7 +32,7 @@ __device__ __forceinline__ void apply_chunk(const PlanDev& sp, const cplx<T>* sc
         for (int r = 0; r < NR; ++r) acc[s][r] = (r < nrhs) ? dst[(size_t)r * D + e0 + s] : mk<T>(0, 0);
     } else if constexpr (SK != 0 && RUN == 2) {
       // FP64: the plan's stored weights; FP32: formed
-      apply_run_star<T, REALC, NR, true, SK == 2, sizeof(T) == 8 ? 1 : 0>(st, e0, src, D, nrhs, acc);
+      apply_run_star<T, REALC, NR, true, SK == 2, sizeof(T) == 8 ? 1 : 0, NAX, DC>(st, e0, src, D, nrhs, acc);
     } else {
       apply_run<T, REALC, NR, RUN>(sp, scoef, e0, src, D, nrhs, acc);
     }
@@ -81,7 +81,7 @@ __device__ __forceinline__ void apply_chunk(const PlanDev& sp, const cplx<T>* sc
   }
 }
 
-template <typename T, int EPI, bool REALC, int NR, int SK>
+template <typename T, int EPI, bool REALC, int NR, int SK, int NAX = 0, int DC = 0>
 __device__ __forceinline__ void apply_units(const BatchDev& b, int level, int refine, unsigned long long cond,
                                             const StarParams& stp) {
   __shared__ __align__(16) PlanDev sp;
@@ -125,7 +125,8 @@ __device__ __forceinline__ void apply_units(const BatchDev& b, int level, int re
     const int cl = c - un.chunk0;
     // the unit's own run length (so that its reduction order does not depend on the batch)
     if constexpr (SK != 0) {
-      apply_chunk<T, EPI, REALC, NR, 2, NV, SK>(sp, scoef, stp, un, cl, D, nrhs, refine, fft_unit, src, dst, F, vt);
+      apply_chunk<T, EPI, REALC, NR, 2, NV, SK, NAX, DC>(sp, scoef, stp, un, cl, D, nrhs, refine, fft_unit, src, dst,
+                                                        F, vt);
     } else {
       if (un.run == 2)
         apply_chunk<T, EPI, REALC, NR, 2, NV>(sp, scoef, stp, un, cl, D, nrhs, refine, fft_unit, src, dst, F, vt);
@@ -199,11 +200,16 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 3) k_apply(BatchDe
 // Batch apply of a single star-1 unit (even last axis): the stencil data as a kernel parameter. The FP32 star
 // stencil waits on L2 latency of its neighbour reads: four blocks per SM (64 registers) hide it best on GB300
 // (cfg4: 435 us at four blocks, 470 at three, 474 at five).
-template <typename T, int EPI, bool REALC, int NR, int SK>
+template <typename T, int EPI, bool REALC, int NR, int SK, int NAX = 0, int DC = 0>
 __global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 4)
     k_apply_star(BatchDev b, int level, int refine, unsigned long long cond, const __grid_constant__ StarParams st) {
-  apply_units<T, EPI, REALC, NR, SK>(b, level, refine, cond, st);
+  apply_units<T, EPI, REALC, NR, SK, NAX, DC>(b, level, refine, cond, st);
 }
+
+// Plain FP32 star-1 apply of the common fixed geometries (qp_apply_fixed.cu); false: not one of them, nothing
+// launched.
+bool launch_plain_star_fixed(const StarParams& st, bool realc, int nrhs, int kind, int D, const float2* h, float2* w,
+                             cudaStream_t s);
 
 template <typename T, int EPI, int NR, bool REALC>
 static void apply_launch_rc(const BatchDev& b, int level, int refine, unsigned long long cond, int nblk, size_t smem,
@@ -251,13 +257,13 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 3) k_apply_plain(c
 
 // Plain apply of a star-1 plan with an even last axis: the stencil data as a kernel parameter; one run of two
 // modes per thread.
-template <typename T, bool REALC, int NR, int SK>
+template <typename T, bool REALC, int NR, int SK, int NAX = 0, int DC = 0>
 __global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 4)
     k_apply_plain_star(const __grid_constant__ StarParams st, int D, int nrhs, const cplx<T>* h, cplx<T>* w) {
   const int e0 = (blockIdx.x * BLOCK + threadIdx.x) * 2;
   if (e0 >= D) return;
   cplx<T> acc[2][NR];
-  apply_run_star<T, REALC, NR, true, SK == 2, sizeof(T) == 8 ? 1 : 0>(st, e0, h, D, nrhs, acc);
+  apply_run_star<T, REALC, NR, true, SK == 2, sizeof(T) == 8 ? 1 : 0, NAX, DC>(st, e0, h, D, nrhs, acc);
 #pragma unroll
   for (int r = 0; r < NR; ++r) {
     if (r < nrhs) {
@@ -275,6 +281,9 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 4)
 
 template <typename T, bool REALC, int SK>
 static void plain_star_nr(int nrhs, const StarParams& st, int D, const cplx<T>* h, cplx<T>* w, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    if (launch_plain_star_fixed(st, REALC, nrhs, SK == 2 ? QP_COEF_DIAG : QP_COEF_SCALAR, D, h, w, s)) return;
+  }
   const int nblk = (D / 2 + BLOCK - 1) / BLOCK;
   switch (nrhs) {
     case 1: k_apply_plain_star<T, REALC, 1, SK><<<nblk, BLOCK, 0, s>>>(st, D, nrhs, h, w); break;

@@ -117,12 +117,14 @@ __device__ __forceinline__ void wstore(void* out, int slot, int e0, int D, const
 // WM: 0 the weights are formed here; 1 (T = double) they are read from sp.w64; 2 (T = double) they are formed and
 // written to wout (the same arithmetic as WM = 0, so stored and formed weights agree bit for bit) and nothing
 // else is done.
-template <typename T, bool REALC, int NR, bool RO, bool DIAGK, int WM = 0>
+// NAX, DC (0: from sp at run time): the number of axes, every one of them with taps, and d known at compile time,
+// so that the axis loop is straight-line code whose neighbour reads the compiler can issue early.
+template <typename T, bool REALC, int NR, bool RO, bool DIAGK, int WM = 0, int NAX = 0, int DC = 0>
 __device__ __forceinline__ void apply_run_star(const StarParams& sp, int e0, const cplx<T>* h, int D, int nrhs,
                                                cplx<T> (&acc)[2][NR], void* wout = nullptr) {
   constexpr int NQ = DIAGK ? MAXD : 1;   // weight terms per mode: q_a (diagonal) or q (scalar)
   constexpr bool FORM = WM != 1;         // the weights are formed from lambda
-  const int d = sp.d, n = sp.n, jl = n - 1, Nl = sp.N[jl];
+  const int d = DC ? DC : sp.d, n = NAX ? NAX : sp.n, jl = n - 1, Nl = sp.N[jl];
   // storage digits and signed modes of the run's first mode
   int ib[MAXN], k[MAXN];
   {
@@ -262,7 +264,7 @@ __device__ __forceinline__ void apply_run_star(const StarParams& sp, int e0, con
     } else {
       wload<REALC>(sp, 0, e0, D, reinterpret_cast<double2(&)[2]>(c0));
     }
-    const bool has = sp.has[jl] != 0;
+    const bool has = NAX != 0 || sp.has[jl] != 0;
     cplx<T> wp[2], wm[2];
     int il = e0, ir = e0;
     if (has) {
@@ -300,7 +302,7 @@ __device__ __forceinline__ void apply_run_star(const StarParams& sp, int e0, con
   // the other axes: one neighbour offset and one dk per tap for the whole run
 #pragma unroll
   for (int j = 0; j < MAXN - 1; ++j) {
-    if (j < jl && sp.has[j]) {
+    if (j < jl && (NAX != 0 || sp.has[j])) {
       const int Nj = sp.N[j], ibj = ib[j], hj = sp.half[j];
       const int ep = e0 + ((ibj == 0) ? sp.woff[j] : -sp.stride[j]);        // k - e_j (tap m = +e_j)
       const int em = e0 + ((ibj == Nj - 1) ? -sp.woff[j] : sp.stride[j]);   // k + e_j (tap m = -e_j)

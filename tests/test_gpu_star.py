@@ -103,6 +103,29 @@ def test_star_plans_batched_beside_others_bitwise(qp):
             assert np.abs(A - A_ref).max() <= 1e-10 * np.abs(A_ref).max(), inst.name
 
 
+@pytest.mark.parametrize("d,n,N,kind,real", [(1, 2, (5, 8), "scalar", False), (2, 4, (6, 5, 4, 8), "diag", True),
+                                             (3, 6, (4, 3, 4, 5, 4, 6), "diag", False),
+                                             (2, 4, (4, 6, 5, 4), "scalar", False)])
+def test_fixed_geometry_plain_apply_is_the_general_one(qp, d, n, N, kind, real):
+    """Every axis with taps and d right-hand sides: the plain FP32 apply takes the kernel with the geometry compiled
+    in; its first right-hand side must equal, bit for bit, the general kernel's (another right-hand-side count),
+    and match the oracle."""
+    inst = W.random_star_instance(d, n, N, kind, seed=40 + n, real=real)
+    plan = qp.plan_from_instance(inst, max_rhs=4)
+    h = _rand(4, inst.N, 9)
+    ht = torch.from_numpy(h).to("cuda", torch.complex64)
+    w_fixed = torch.empty((d,) + tuple(N), dtype=torch.complex64, device="cuda")
+    qp.qp_apply_stiffness(plan, ht[:d].contiguous(), w_fixed, qp.QP_FP32, nrhs=d)
+    other = d + 1
+    w_gen = torch.empty((other,) + tuple(N), dtype=torch.complex64, device="cuda")
+    qp.qp_apply_stiffness(plan, ht[:other].contiguous(), w_gen, qp.QP_FP32, nrhs=other)
+    assert torch.equal(w_fixed, w_gen[:d])
+    op = O.Operator(inst)
+    ref = np.stack([op(h[r]) for r in range(d)])
+    err = np.abs(w_fixed.cpu().numpy().astype(np.complex128) - ref).max() / np.abs(ref).max()
+    assert err <= 2e-6, err
+
+
 def test_general_taps_are_not_star(qp):
     inst = W.random_instance(2, 3, (6, 4, 8), "sym", "taps", seed=23)
     info = qp.qp_plan_query(qp.plan_from_instance(inst))
