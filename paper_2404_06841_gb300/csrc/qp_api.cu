@@ -65,6 +65,7 @@ struct qp_plan {
   PlanDev host_pd{};           // host copy of the device plan description
   StarParams star_host{};      // star-1 stencil data (host_pd.star1), passed by value to single-plan kernels
   void* w64 = nullptr;         // star-1 plans: stored FP64 weights (star_host.w64), or null
+  StarParams* star_dev = nullptr;   // device copy of star_host (host_pd.star), read by batches of several plans
   PlanDev* pd = nullptr;       // device copy
   bool real_coef = false;
   int coef_count = 0;          // ntaps * ncomp
@@ -402,7 +403,10 @@ void build_taps(qp_plan* p, const qp_coeff* c) {
   p->real_coef = real_coef;
   p->coef_count = G * nc;
   make_star(pd, coef64.data(), coef32.data(), p->star_host);
-  if (pd.star1) pd.star = (const StarParams*)up(&p->star_host, sizeof(StarParams));
+  if (pd.star1) {
+    p->star_dev = (StarParams*)up(&p->star_host, sizeof(StarParams));
+    pd.star = p->star_dev;
+  }
 }
 
 // FP64 weights of a star-1 plan stored per (tap slot, mode). The compressed format of Sec. 4.2 keeps the nonzero
@@ -424,7 +428,7 @@ void build_star_weights(qp_plan* p, cudaStream_t s) {
   launch_star_weights(p->star_host, p->real_coef, p->kind, p->D, p->w64, s);
   CK_LAUNCH();
   // the device copy of the StarParams (read by batches of several plans) points at the table too
-  CK(cudaMemcpyAsync(const_cast<StarParams*>(pd.star), &p->star_host, sizeof(StarParams), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(p->star_dev, &p->star_host, sizeof(StarParams), cudaMemcpyHostToDevice, s));
 }
 
 void alloc_workspace(qp_plan* p) {
