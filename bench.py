@@ -398,7 +398,47 @@ def run_ours(args, rank, world, local_rank):
         e2e = {"value": world * dof_iters_step / e2e_t, "unit": "DOF*iter/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": round(e2e_t * 1e3, 3),
                "what": "qp_plan_create(host taps) + f host->device + qp_pcg_solve + qp_l2qp_error + destroy"}
-    elif c.taps_k is not None and name != "cfg3":
+    elif name == "cfg3":
+        # every step: the batch's plans from host taps, the batch, the batched solve, a* on the host, destroy
+        hk = [(np.ascontiguousarray(i.coeff.taps_k, dtype=np.int32),
+               np.ascontiguousarray(np.asarray(i.coeff.taps_val, dtype=np.complex128))) for i in insts]
+        h2d = sum(k.nbytes + v.nbytes + i.P.nbytes + 4 * i.n for (k, v), i in zip(hk, insts))
+        d2h = sum(16 * i.d * i.d for i in insts)
+        e2e_steps = max(3, min(args.steps, 10))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            ps = [qp.qp_plan_create(i.d, i.n, i.P, i.N, W.Coefficient(i.coeff.kind, k, v))
+                  for (k, v), i in zip(hk, insts)]
+            b2 = qp.qp_batch_create(ps)
+            qp.qp_batch_homogenized(b2, tol=tol, mode=mode, maxit=2000)
+            qp.qp_batch_destroy(b2)
+            for p2 in ps:
+                qp.qp_plan_destroy(p2)
+        torch.cuda.synchronize()
+        e2e_t = (time.perf_counter() - t0) / e2e_steps
+        e2e = {"value": world * dof_iters_step / e2e_t, "unit": "DOF*iter/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": round(e2e_t * 1e3, 3),
+               "what": "64 x qp_plan_create(host taps) + qp_batch_create + qp_batch_homogenized + destroy per step"}
+    elif c.grid is not None:
+        # every step: the coefficient samples copied from pinned host memory, plan, a* on the host, destroy
+        gh = torch.from_numpy(np.ascontiguousarray(c.grid, dtype=np.float64)).pin_memory()
+        h2d = gh.numel() * 8 + inst.P.nbytes + 4 * inst.n
+        d2h = 16 * inst.d * inst.d
+        e2e_steps = max(3, min(args.steps, 20))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            gd = gh.to(dev, non_blocking=True)
+            p2 = qp.qp_plan_create(inst.d, inst.n, inst.P, inst.N, W.Coefficient(c.kind, grid=gd))
+            qp.qp_homogenized(p2, tol=tol, mode=mode, maxit=2000)
+            qp.qp_plan_destroy(p2)
+        torch.cuda.synchronize()
+        e2e_t = (time.perf_counter() - t0) / e2e_steps
+        e2e = {"value": world * dof_iters_step / e2e_t, "unit": "DOF*iter/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": round(e2e_t * 1e3, 3),
+               "what": "coefficient samples host->device + qp_plan_create(grid) + qp_homogenized + destroy per step"}
+    elif c.taps_k is not None:
         kk = np.ascontiguousarray(c.taps_k, dtype=np.int32)
         vv = np.ascontiguousarray(np.asarray(c.taps_val, dtype=np.complex128))
         h2d = kk.nbytes + vv.nbytes + inst.P.nbytes + 4 * inst.n
