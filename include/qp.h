@@ -76,7 +76,9 @@ typedef struct {
 } qp_coeff;
 
 typedef struct {
-  int backend;      /* QP_BACKEND_*: AUTO picks TAPS for a tap coefficient, FFT for a grid one */
+  int backend;      /* QP_BACKEND_*: AUTO takes FFT for a grid coefficient; for a tap coefficient the TAPS stencil,
+                       except that a dense tap list (>= 64 taps) on >= 65,536 modes that the FFT backend can
+                       transform has both backends' FP32 applies timed once per shape and keeps the faster */
   int max_rhs;      /* right-hand sides solved together, 1..QP_MAX_RHS; 0 = d */
   int precisions;   /* workspace: bit 0 = FP64 solve, bit 1 = FP32 (refinement inner) solve; 0 = both */
   int exec;         /* how a solve is driven (the iterates are bitwise the same in every mode):
@@ -227,7 +229,8 @@ uint64_t qp_launch_count(void);
  * still apply). qp_fft_schedule: the schedule in use for precision (QP_FP64 / QP_FP32): its candidate index
  * (-1: the heuristic's), the number of candidates, its timed ms per apply (-1 if untimed) and a description
  * (text, text_len bytes with the terminating 0; any output may be NULL). qp_fft_set_schedule: use candidate
- * index (0 .. count - 1) from now on. Both return QP_ERR_UNSUPPORTED for a taps-backend plan. */
+ * index (0 .. count - 1) from now on. Both return QP_ERR_UNSUPPORTED for a taps-backend plan. With the autotuner off,
+ * QP_BACKEND_AUTO also stops timing the stencil against the FFT backend for tap coefficients (taps are kept). */
 qp_status qp_set_fft_autotune(int enabled);
 qp_status qp_fft_schedule(const qp_plan* plan, int precision, int* index, int* count, double* ms, char* text,
                           int text_len);

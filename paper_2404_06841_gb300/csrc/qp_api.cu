@@ -13,6 +13,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -429,6 +430,80 @@ void build_star_weights(qp_plan* p, cudaStream_t s) {
   CK_LAUNCH();
   // the device copy of the StarParams (read by batches of several plans) points at the table too
   CK(cudaMemcpyAsync(p->star_dev, &p->star_host, sizeof(StarParams), cudaMemcpyHostToDevice, s));
+}
+
+// QP_BACKEND_AUTO with a tap coefficient: the stencil and the FFT backend are both exact for it (the taps are a
+// trigonometric polynomial), so the FP32 applies of both (max_rhs right-hand sides, the FFT one on its autotuned
+// schedule) are timed once per (geometry, kind, taps, max_rhs) on this GPU and the faster is kept; the choice is
+// cached for the process. The stencil costs about one multiply-add per tap and mode, the FFT passes about
+// log D of them, so dense tap lists go to the FFT. Returns the backend; for QP_BACKEND_FFT, p->fft holds the FFT
+// plan with the coefficient already transformed. The plan's tap tables and device description must be uploaded.
+std::mutex g_backend_mu;
+std::map<std::string, int> g_backend_cache;
+
+int tune_backend(qp_plan* p, cudaStream_t s) {
+  const PlanDev& pd = p->host_pd;
+  std::string key = std::to_string(pd.d) + "/" + std::to_string(pd.kind) + "/" + std::to_string(pd.ntaps) + "/" +
+                    std::to_string(p->max_rhs) + "/" + std::to_string(p->real_coef);
+  for (int j = 0; j < pd.n; ++j) key += "/" + std::to_string(pd.N[j]);
+  int cached = -1;
+  {
+    std::lock_guard<std::mutex> lk(g_backend_mu);
+    auto it = g_backend_cache.find(key);
+    if (it != g_backend_cache.end()) cached = it->second;
+  }
+  if (cached == QP_BACKEND_TAPS) return QP_BACKEND_TAPS;
+  FftPlan* f = fft_plan_create(pd, p->precisions, p->max_rhs, s);
+  try {
+    fft_set_taps(f, pd, p->pd, s);
+    if (cached == QP_BACKEND_FFT) {
+      p->fft = f;
+      return QP_BACKEND_FFT;
+    }
+    fft_autotune(f, pd, p->pd, s);
+    const int nr = p->max_rhs;
+    const size_t bytes = (size_t)nr * p->D * sizeof(float2);
+    float2* h = p->v32.h;
+    float2* w = p->v32.w;
+    CK(cudaMemsetAsync(h, 0, bytes, s));
+    const StarParams* st1 = pd.star1 ? &p->star_host : nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float ms[2] = {0.f, 0.f};
+    for (int b = 0; b < 2; ++b) {
+      auto run = [&]() {
+        if (b == 0) launch_apply_plain<float>(p->pd, p->real_coef, p->coef_count, p->D, nr, h, w,
+                                              pd.N[pd.n - 1] % 2 == 0 ? 2 : 1, st1, p->kind, s);
+        else fft_apply<float>(f, pd, p->pd, h, w, nr, s);
+      };
+      run();
+      CK(cudaEventRecord(e0, s));
+      for (int rep = 0; rep < 3; ++rep) run();
+      CK(cudaEventRecord(e1, s));
+      CK(cudaEventSynchronize(e1));
+      CK_LAUNCH();
+      CK(cudaEventElapsedTime(&ms[b], e0, e1));
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const int choice = (ms[1] < 0.9f * ms[0]) ? QP_BACKEND_FFT : QP_BACKEND_TAPS;
+    {
+      std::lock_guard<std::mutex> lk(g_backend_mu);
+      g_backend_cache[key] = choice;
+    }
+    if (choice == QP_BACKEND_FFT) {
+      p->fft = f;
+      return QP_BACKEND_FFT;
+    }
+  } catch (...) {
+    cudaStreamSynchronize(s);
+    fft_plan_destroy(f);
+    throw;
+  }
+  CK(cudaStreamSynchronize(s));
+  fft_plan_destroy(f);
+  return QP_BACKEND_TAPS;
 }
 
 void alloc_workspace(qp_plan* p) {
@@ -1083,6 +1158,19 @@ qp_status qp_plan_create(int d, int n, const double* P, const int* N, const qp_c
   if (coeff->repr == QP_REPR_TAPS) build_taps(p.get(), coeff);
   alloc_workspace(p.get());
   p->pd = (PlanDev*)p->dalloc(sizeof(PlanDev));
+  bool fft_ok = true;
+  for (int j = 0; j < n; ++j) fft_ok = fft_ok && fft_supported(N[j]);
+  // (only dense tap lists on grids large enough to time reliably: below that the stencil is taken outright)
+  if (p->backend == QP_BACKEND_TAPS && backend_req == QP_BACKEND_AUTO && fft_ok && (p->precisions & 2) &&
+      fft_autotune_on() && p->host_pd.ntaps >= 64 && p->D >= 65536) {
+    CK(cudaMemcpyAsync(p->pd, &p->host_pd, sizeof(PlanDev), cudaMemcpyHostToDevice, s));
+    p->backend = tune_backend(p.get(), s);
+    if (p->backend == QP_BACKEND_FFT) {   // the stencil's own data is not used from here on
+      p->host_pd.backend = QP_BACKEND_FFT;
+      p->host_pd.star1 = 0;
+      p->host_pd.star = nullptr;
+    }
+  }
   if (p->backend == QP_BACKEND_TAPS) {
     CK(cudaMemcpyAsync(p->pd, &p->host_pd, sizeof(PlanDev), cudaMemcpyHostToDevice, s));
     launch_diag(p->pd, p->coef_count, p->D, p->jac64, p->frob64, p->jac32, p->frob32, p->scratch, p->counter,
@@ -1091,9 +1179,11 @@ qp_status qp_plan_create(int d, int n, const double* P, const int* N, const qp_c
     build_star_weights(p.get(), s);
   } else {
     CK(cudaMemcpyAsync(p->pd, &p->host_pd, sizeof(PlanDev), cudaMemcpyHostToDevice, s));
-    p->fft = fft_plan_create(p->host_pd, p->precisions, p->max_rhs, s);
-    if (coeff->repr == QP_REPR_GRID) fft_set_grid(p->fft, p->host_pd, p->pd, coeff->grid, s);
-    else fft_set_taps(p->fft, p->host_pd, p->pd, s);
+    if (!p->fft) {   // (AUTO with taps that the FFT backend applies faster: made and transformed already)
+      p->fft = fft_plan_create(p->host_pd, p->precisions, p->max_rhs, s);
+      if (coeff->repr == QP_REPR_GRID) fft_set_grid(p->fft, p->host_pd, p->pd, coeff->grid, s);
+      else fft_set_taps(p->fft, p->host_pd, p->pd, s);
+    }
     fft_autotune(p->fft, p->host_pd, p->pd, s);
     fft_diag(p->fft, &p->host_pd, p->pd, p->jac64, p->frob64, p->jac32, p->frob32, p->small, s);
     CK_LAUNCH();

@@ -1467,6 +1467,7 @@ std::atomic<int> g_autotune{1};
 }  // namespace
 
 void fft_set_autotune(bool on) { g_autotune.store(on ? 1 : 0); }
+bool fft_autotune_on() { return g_autotune.load() != 0; }
 
 template <typename T>
 static void tune_precision(FftPlan* f, const PlanDev& pd, const PlanDev* pdp, cudaStream_t s) {

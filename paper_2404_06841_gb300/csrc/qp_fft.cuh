@@ -32,6 +32,7 @@ void fft_apply(FftPlan* f, const PlanDev& pd, const PlanDev* pdp, const cplx<T>*
 // (fft_set_autotune(false)): the balanced-split heuristic.
 void fft_autotune(FftPlan* f, const PlanDev& pd, const PlanDev* pdp, cudaStream_t s);
 void fft_set_autotune(bool on);
+bool fft_autotune_on();
 int fft_schedule_count(const FftPlan* f, bool fp64);
 // the schedule in use: its candidate index (-1: the heuristic's, untimed), description and timed ms per apply
 int fft_schedule_get(const FftPlan* f, bool fp64, std::string& text, float& ms);

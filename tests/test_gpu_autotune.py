@@ -72,3 +72,35 @@ def test_taps_plan_has_no_fft_schedule(qp):
     with pytest.raises(qp.QPError) as ei:
         qp.qp_fft_schedule(plan, qp.QP_FP32)
     assert ei.value.status == qp.QP_ERR_UNSUPPORTED
+
+
+def test_auto_backend_takes_the_fft_for_a_dense_tap_list(qp):
+    """255 taps (|m| <= 2 in 4-D) with a full 2x2 coefficient on 24^4 modes: the stencil's work per mode is
+    proportional to the tap count, so the timed choice of QP_BACKEND_AUTO is the FFT backend; its apply and a*
+    match the forced stencil's (and the apply the oracle's pointwise sum at sampled modes)."""
+    N = (24, 24, 24, 24)
+    inst = W.random_instance(2, 4, N, "sym", "taps", seed=71, radius=2, nmodes=127)
+    assert len(inst.coeff.taps_k) == 255
+    p_auto = qp.plan_from_instance(inst)
+    p_taps = qp.plan_from_instance(inst, backend=qp.QP_BACKEND_TAPS)
+    assert qp.qp_plan_query(p_auto)["backend"] == "fft" and qp.qp_plan_query(p_taps)["backend"] == "taps"
+    rng = np.random.default_rng(6)
+    h = torch.complex(torch.randn((2,) + N, dtype=torch.float64), torch.randn((2,) + N, dtype=torch.float64)).cuda()
+    wa, wt = torch.empty_like(h), torch.empty_like(h)
+    qp.qp_apply_stiffness(p_auto, h, wa, qp.QP_FP64)
+    qp.qp_apply_stiffness(p_taps, h, wt, qp.QP_FP64)
+    scale = float(wt.abs().max())
+    assert float((wa - wt).abs().max()) <= 1e-12 * scale
+    pts = [tuple(int(x) for x in (rng.integers(0, Nj) for Nj in N)) for _ in range(16)]
+    ref = O.apply_taps_at(inst.P, N, inst.coeff.taps_k, inst.coeff.taps_val, "sym", h[0].cpu().numpy(), pts)
+    got = np.array([complex(wa[(0,) + p].item()) for p in pts])
+    assert np.abs(got - ref).max() <= 1e-12 * scale
+    A1, i1 = qp.qp_homogenized(p_auto, tol=1e-10)
+    A2, i2 = qp.qp_homogenized(p_taps, tol=1e-10)
+    assert all(i["status"] == "QP_OK" for i in i1 + i2)
+    assert np.abs(A1 - A2).max() <= 1e-9 * np.abs(A2).max()
+
+
+def test_auto_backend_keeps_the_stencil_for_few_taps(qp):
+    for inst in (W.cfg1(), W.random_instance(2, 4, (16, 16, 16, 16), "sym", "taps", seed=72, nmodes=20)):
+        assert qp.qp_plan_query(qp.plan_from_instance(inst))["backend"] == "taps"
