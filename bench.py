@@ -117,9 +117,10 @@ def fft_apply_bytes(d, ncomp, nrhs, D, es):
 # exists.
 TRAFFIC = {
     # cfg1: one solve (33 iterations, 2 correctors) in k_pcg_persistent; vectors and stored weights stay in L2
-    ("k_pcg_persistent", "cfg1"): 9568768 + 290048,
-    # cfg4: k_apply_plain_star captured at N = 14 (7.53 M modes; h and w exceed L2), scaled by 16^6 / 14^6
-    ("k_apply_plain", "cfg4"): int((207552768 + 153182464) * (16 ** 6 / 14 ** 6)),
+    ("k_pcg_persistent", "cfg1"): 9614592 + 259584,
+    # cfg4: k_apply_plain_star (geometry compiled in) captured at N = 14 (7.53 M modes; h and w exceed L2), scaled
+    # by 16^6 / 14^6
+    ("k_apply_plain", "cfg4"): int((207640320 + 153260032) * (16 ** 6 / 14 ** 6)),
     # cfg2: the three fused passes of one FP32 apply (the gradient fields stay in L2 between passes)
     ("k_fft_group", "cfg2"): 16874752 + 9472 + 46255616 + 0 + 33646848 + 0,
 }
