@@ -83,7 +83,8 @@ def test_persistent_warm_start_and_zero_rhs(qp, mode):
 
 
 def test_persistent_more_chunks_than_resident_blocks(qp):
-    """D = 12^6 modes in 8192-mode chunks: more chunks than co-resident blocks, so every block walks several."""
+    """D = 12^6 modes in 1,167 chunks of 2,560 modes (each five interleaved 512-mode segments): more chunks than
+    co-resident blocks, so every block walks several."""
     inst = W.random_instance(2, 6, (12,) * 6, "diag", "taps", seed=31, nmodes=12)
     F = _rand_vecs(2, inst.N, 3)
     for m in (qp.QP_MODE_FP32_REFINE, qp.QP_MODE_FP64):
