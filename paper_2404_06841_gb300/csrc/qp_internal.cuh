@@ -62,16 +62,21 @@ struct FastDiv {
   uint32_t p;
 };
 
-// Modes per chunk of a unit (a chunk is reduced by one block): about 8 chunks per SM, at most 65,536 modes, so that
-// a large unit's chunked kernels run in about one wave of resident blocks (16^6 modes: 1214 chunks of 13,824; a
-// cap of 8192 gave 2048 chunks, 1.7 waves); at least 512 modes from 32,768 modes up, so that the stencil's runs of
-// two modes keep every thread of a block busy (256-mode chunks left half of each block idle: cfg1's FP64 solve
-// 1.12 -> 0.98 ms, the batched cfg3 24.5 -> 19.6 ms), and 256 below, where fewer blocks would cost more than the idle
-// threads (1,024 modes: 0.51 -> 0.58 ms with 512). It depends on D only, so that a unit reduces in the same order
-// alone or batched.
+// Modes per chunk of a unit (a chunk is reduced by one block), a function of D only, so that a unit reduces in the
+// same order alone or batched:
+//   D < 32,768: 256 (small units need the blocks: 1,024 modes took 0.51 ms with 256, 0.58 with 512);
+//   32,768 <= D < 65,536: 512, so that the stencil's runs of two modes keep every thread of a block busy;
+//   65,536 <= D < 622,592: one chunk per SM (152 chunks of 2 ceil(D / 304) modes), which evens the FP64 work of
+//     the persistent solve over all SMs (cfg1: 1.12 ms with 256 chunks of 256, 0.98 with 128 of 512, 0.94 with
+//     152 of 432; the batched cfg3: 24.5, 20.0, 17.9 ms);
+//   D >= 622,592: about 8 chunks per SM, at most 65,536 modes, so that a large unit's chunked kernels run in about
+//     one wave of resident blocks (16^6 modes: 1214 chunks of 13,824; a cap of 8192 gave 2048 chunks, 1.7 waves).
 inline int64_t chunk_modes(int64_t D) {
-  const int64_t lo = D >= 32768 ? 2 * BLOCK : BLOCK;
-  return std::max<int64_t>(lo, std::min<int64_t>(65536, (D / (152 * 8) + BLOCK - 1) / BLOCK * BLOCK));
+  constexpr int64_t SMS = 152;
+  if (D < 32768) return BLOCK;
+  if (D < 65536) return 2 * BLOCK;
+  if (D < SMS * 4096) return 2 * ((D + 2 * SMS - 1) / (2 * SMS));
+  return std::max<int64_t>(2 * BLOCK, std::min<int64_t>(65536, (D / (SMS * 8) + BLOCK - 1) / BLOCK * BLOCK));
 }
 
 inline FastDiv make_fastdiv(uint32_t d) {
