@@ -26,6 +26,7 @@ import json
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -228,7 +229,9 @@ class ClockSampler:
     def __init__(self, bus_id=None):
         self.bus_id = (bus_id or "").lower()
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+        # the raw samples (the JSON line carries their summary); QP_BENCH_CLOCKS_CSV chooses the file
+        self.path = os.environ.get("QP_BENCH_CLOCKS_CSV") or os.path.join(tempfile.gettempdir(),
+                                                                          "qp_bench_clocks.csv")
 
     def start(self):
         try:
