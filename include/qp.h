@@ -64,8 +64,8 @@ typedef struct qp_batch qp_batch;   /* opaque; a set of plans solved together */
  * repr: QP_REPR_TAPS - Fourier modes (taps): tap_k host int32 [ntaps x n], every |m_j| < N_j / 2;
  *       tap_val host double [ntaps x ncomp x 2] (re, im) with A~_{-m} = conj(A~_m) (so A is real).
  *       Values are the Fourier coefficients of Sec. 3.1.1; a mode listed twice is summed.
- *       QP_REPR_GRID - samples A(y_j) at y_j = 2 pi j / N: grid is DEVICE double [ncomp x D], C order; the
- *       plan copies it. Its Fourier coefficients are taken by the DFT with 1/D (Sec. 3.1.1). */
+ *       QP_REPR_GRID - samples A(y_j) at y_j = 2 pi j / N: grid is DEVICE double [ncomp x D], C order, 8-byte
+ *       aligned (else QP_ERR_INVALID_ARG); the plan copies it. Its Fourier coefficients are taken by the DFT with 1/D (Sec. 3.1.1). */
 typedef struct {
   int kind;
   int repr;
@@ -144,7 +144,7 @@ qp_status qp_apply_stiffness(qp_plan* plan, int nrhs, const void* U, void* QU, i
 
 /* F = the corrector right-hand sides F_j(k) = i sum_a lambda_a(k) A~^{aj}_k, F_j(0) = 0, for
  * j = j0 .. j0+nrhs-1 (0-based; Sec. 5.2 eq. corrector, App. D f_1 = d alpha/dx_1). F: device complex128
- * nrhs x D. */
+ * nrhs x D, 16-byte aligned (a misaligned pointer gives QP_ERR_INVALID_ARG). */
 qp_status qp_corrector_rhs(qp_plan* plan, int j0, int nrhs, void* F, void* stream);
 
 /* Solves Q U = F for nrhs right-hand sides with PCG (Algorithm 2, z = M r). F: device complex128 nrhs x D.
@@ -154,8 +154,8 @@ qp_status qp_pcg_solve(qp_plan* plan, int nrhs, const void* F, void* U, const qp
                        qp_solve_info* info, void* stream);
 
 /* Astar = the torus average A*_ij = A~^{ij}_0 + i sum_k sum_b A~^{ib}_{-k} lambda_b(k) U_j(k)
- * (eq. homcoefficient written in Fourier terms) from the d corrector solutions U (device complex128 d x D).
- * Astar_re, Astar_im: host double d x d row-major (Astar_im may be NULL). FP64 throughout. */
+ * (eq. homcoefficient written in Fourier terms) from the d corrector solutions U (device complex128 d x D,
+ * 16-byte aligned; a misaligned pointer gives QP_ERR_INVALID_ARG). Astar_re, Astar_im: host double d x d row-major (Astar_im may be NULL). FP64 throughout. */
 qp_status qp_homogenized_reduce(qp_plan* plan, const void* U, double* Astar_re, double* Astar_im, void* stream);
 
 /* The whole homogenization: the d corrector right-hand sides, their PCG solves (FP64 or FP32 + FP64
@@ -165,7 +165,8 @@ qp_status qp_homogenized(qp_plan* plan, const qp_solve_opts* opts, double* Astar
 
 /* Unnormalised in-place n-dimensional complex DFT of "count" contiguous arrays of shape N[0..n-1]:
  * X(k) = sum_j x(j) exp(sign * 2 pi i k.j / N), sign = -1 (forward) or +1 (inverse, without 1/D).
- * data: device complex128 (QP_FP64) or complex64 (QP_FP32). N_j products of 2 and 3, 2..1024. */
+ * data: device complex128 (QP_FP64) or complex64 (QP_FP32), aligned to its element (16 or 8 bytes; else
+ * QP_ERR_INVALID_ARG). N_j products of 2 and 3, 2..1024. */
 qp_status qp_fft(int n, const int* N, int count, void* data, int sign, int precision, void* stream);
 
 /* Batched homogenization: every corrector of every plan is solved in the same launches (one unit per

@@ -1147,6 +1147,7 @@ qp_status qp_plan_create(int d, int n, const double* P, const int* N, const qp_c
   } else if (coeff->repr == QP_REPR_GRID) {
     if (backend_req == QP_BACKEND_TAPS) raise(QP_ERR_INVALID_ARG, "a grid coefficient needs the FFT backend");
     if (!coeff->grid) raise(QP_ERR_INVALID_ARG, "grid must be a non-null device pointer");
+    if ((uintptr_t)coeff->grid & 7u) raise(QP_ERR_INVALID_ARG, "grid must be 8-byte aligned");
     p->backend = QP_BACKEND_FFT;
   } else {
     raise(QP_ERR_INVALID_ARG, "unknown coefficient representation");
@@ -1252,6 +1253,7 @@ qp_status qp_corrector_rhs(qp_plan* p, int j0, int nrhs, void* F, void* stream) 
   API_BEGIN
   if (!p || !F) raise(QP_ERR_INVALID_ARG, "plan and F must be non-null");
   if (j0 < 0 || nrhs < 1 || j0 + nrhs > p->d) raise(QP_ERR_INVALID_ARG, "need 0 <= j0 and j0 + nrhs <= d");
+  if ((uintptr_t)F & 15u) raise(QP_ERR_INVALID_ARG, "F must be 16-byte aligned");
   corrector_rhs(p, j0, nrhs, (double2*)F, S(stream));
   API_END
 }
@@ -1282,6 +1284,7 @@ qp_status qp_pcg_solve(qp_plan* p, int nrhs, const void* F, void* U, const qp_so
 qp_status qp_homogenized_reduce(qp_plan* p, const void* U, double* Are, double* Aim, void* stream) {
   API_BEGIN
   if (!p || !U || !Are) raise(QP_ERR_INVALID_ARG, "plan, U and Astar_re must be non-null");
+  if ((uintptr_t)U & 15u) raise(QP_ERR_INVALID_ARG, "U must be 16-byte aligned");
   astar_reduce(p, (const double2*)U, Are, Aim, S(stream));
   API_END
 }
@@ -1318,6 +1321,8 @@ qp_status qp_fft(int n, const int* N, int count, void* data, int sign, int preci
   }
   if (D * count > (int64_t(1) << 31)) raise(QP_ERR_INVALID_ARG, "too many elements");
   if (precision != QP_FP64 && precision != QP_FP32) raise(QP_ERR_INVALID_ARG, "bad precision");
+  if ((uintptr_t)data & (precision == QP_FP64 ? 15u : 7u))
+    raise(QP_ERR_INVALID_ARG, "data must be aligned to its complex element (16 bytes FP64, 8 bytes FP32)");
   fft_standalone(n, N, count, data, sign, precision, S(stream));
   CK_LAUNCH();
   API_END

@@ -142,3 +142,24 @@ def test_misaligned_vectors_are_rejected_before_any_launch(qp):
     with pytest.raises(qp.QPError) as ei:
         qp.qp_apply_stiffness(plan, buf[1:], good, qp.QP_FP32, nrhs=1)   # 8-byte offset
     assert ei.value.status == qp.QP_ERR_INVALID_ARG and "aligned" in str(ei.value)
+
+
+def test_misaligned_rhs_reduce_and_fft_pointers_are_rejected(qp):
+    """qp_corrector_rhs, qp_homogenized_reduce and qp_fft check their device pointers' alignment (16 bytes for
+    complex128 vectors) before any launch; the plan and the stream stay usable afterwards."""
+    inst = W.cfg1(4)
+    plan = qp.plan_from_instance(inst)
+    d, D = inst.d, inst.D
+    buf = torch.zeros(d * D + 1, dtype=torch.complex128, device="cuda")
+    raw = buf.view(torch.float64)[1:1 + 2 * d * D]          # 8 bytes past a 16-byte boundary
+    assert raw.data_ptr() % 16 == 8
+    for call in (lambda: qp.qp_corrector_rhs(plan, 0, d, raw),
+                 lambda: qp.qp_homogenized_reduce(plan, raw),
+                 lambda: qp.qp_fft(raw, inst.N, sign=-1, precision=qp.QP_FP64, count=d)):
+        with pytest.raises(qp.QPError) as ei:
+            call()
+        assert ei.value.status == qp.QP_ERR_INVALID_ARG and "aligned" in str(ei.value)
+    F = torch.zeros(d, D, dtype=torch.complex128, device="cuda")
+    qp.qp_corrector_rhs(plan, 0, d, F)
+    torch.cuda.synchronize()
+    assert torch.isfinite(torch.view_as_real(F)).all() and F.abs().max().item() > 0.0
