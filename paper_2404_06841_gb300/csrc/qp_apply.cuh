@@ -89,8 +89,9 @@ __device__ __forceinline__ void apply_units(const BatchDev& b, int level, int re
   cplx<T>* scoef = reinterpret_cast<cplx<T>*>(smraw);
   const PlanDev* cur = nullptr;
   for (int c = blockIdx.x; c < b.nchunks; c += gridDim.x) {
-    const int u = unit_of_chunk(b, c);
-    const UnitDev& un = unit_at(b, u);
+    // a star-1 kernel runs a batch of one unit: its description straight from the kernel parameter
+    const int u = SK != 0 ? 0 : unit_of_chunk(b, c);
+    const UnitDev& un = SK != 0 ? b.pu : unit_at(b, u);
     RhsSt* st = b.st + (size_t)u * MAXR;
     const int nrhs = un.nrhs;
     // skip units with nothing left to do at this level (same decision for every chunk of the unit)
@@ -101,9 +102,11 @@ __device__ __forceinline__ void apply_units(const BatchDev& b, int level, int re
       else active = true;
     }
     if (!active) continue;
-    if (un.plan != cur) {
-      cur = un.plan;
-      load_plan<T>(cur, sp, scoef);
+    if constexpr (SK == 0) {   // star-1 kernels take the stencil from their kernel parameter instead
+      if (un.plan != cur) {
+        cur = un.plan;
+        load_plan<T>(cur, sp, scoef);
+      }
     }
     const int D = un.D;
     const cplx<T>* src;
@@ -116,7 +119,7 @@ __device__ __forceinline__ void apply_units(const BatchDev& b, int level, int re
       dst = reinterpret_cast<cplx<T>*>(un.w);
     }
     const cplx<T>* F = reinterpret_cast<const cplx<T>*>(un.F);
-    const bool fft_unit = (sp.backend == QP_BACKEND_FFT);
+    const bool fft_unit = SK == 0 && (sp.backend == QP_BACKEND_FFT);
     constexpr int NV = (EPI == EPI_RESIDUAL) ? 2 * NR : NR;   // reduced quantities: (h,w) or (|F-w|^2, |F|^2)
     T vt[NV];                                                   // per-thread partials in the vector precision
     double v[NV];
