@@ -209,6 +209,21 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 4)
   apply_units<T, EPI, REALC, NR, SK, NAX, DC>(b, level, refine, cond, st);
 }
 
+// A star-1 plan of one of the fixed geometries compiled in: (n, d) = (6, 3), (4, 2), (2, 1), taps on every axis,
+// nr = d right-hand sides; n gets the number of axes.
+inline bool fixed_geometry(const StarParams& st, int nr, int& n) {
+  n = st.n;
+  if (!((n == 6 && st.d == 3) || (n == 4 && st.d == 2) || (n == 2 && st.d == 1)) || nr != st.d) return false;
+  for (int j = 0; j < n; ++j)
+    if (!st.has[j]) return false;
+  return true;
+}
+
+// Batch FP32 (h, Q h) apply of a single star-1 unit of a fixed geometry (qp_apply_fixed_batch.cu); false: not one
+// of them, nothing launched.
+bool launch_batch_star_fixed(const BatchDev& b, int level, int refine, unsigned long long cond, int nblk, size_t smem,
+                             const StarParams& st, bool realc, int nr, int kind, cudaStream_t s);
+
 // Plain FP32 star-1 apply of the common fixed geometries (qp_apply_fixed.cu); false: not one of them, nothing
 // launched.
 bool launch_plain_star_fixed(const StarParams& st, bool realc, int nrhs, int kind, int D, const float2* h, float2* w,
@@ -217,6 +232,9 @@ bool launch_plain_star_fixed(const StarParams& st, bool realc, int nrhs, int kin
 template <typename T, int EPI, int NR, bool REALC>
 static void apply_launch_rc(const BatchDev& b, int level, int refine, unsigned long long cond, int nblk, size_t smem,
                             const StarParams* st1, int kind, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4 && EPI == EPI_DOT_HW) {
+    if (st1 && launch_batch_star_fixed(b, level, refine, cond, nblk, smem, *st1, REALC, NR, kind, s)) return;
+  }
   if (!st1) k_apply<T, EPI, REALC, NR><<<nblk, BLOCK, smem, s>>>(b, level, refine, cond);
   else if (kind == QP_COEF_DIAG) k_apply_star<T, EPI, REALC, NR, 2><<<nblk, BLOCK, smem, s>>>(b, level, refine, cond, *st1);
   else k_apply_star<T, EPI, REALC, NR, 1><<<nblk, BLOCK, smem, s>>>(b, level, refine, cond, *st1);

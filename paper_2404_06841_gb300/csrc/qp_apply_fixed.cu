@@ -2,22 +2,13 @@
 // carrying the taps m = +-e_j), d and the right-hand-side count compiled in: (n, d) = (6, 3), (4, 2), (2, 1) with
 // d right-hand sides. The stencil's axis loop is then straight-line code and the compiler issues the neighbour
 // reads of later axes early (cfg4's apply: 384 us against 435 with the geometry read at run time); the arithmetic
-// and so the results are bit for bit those of the general star-1 kernel. (The batch apply of the solves keeps the
-// general form: with its chunk loop and epilogue the longer live ranges spilled and made the cfg4 solve slower,
-// 42.1-43.1 ms against 41.6.)
+// and so the results are bit for bit those of the general star-1 kernel. The batch apply's variants are in
+// qp_apply_fixed_batch.cu.
 #include "qp_apply.cuh"
 
 namespace qp {
 
 namespace {
-
-bool fixed_geometry(const StarParams& st, int nr, int& n) {
-  n = st.n;
-  if (!((n == 6 && st.d == 3) || (n == 4 && st.d == 2) || (n == 2 && st.d == 1)) || nr != st.d) return false;
-  for (int j = 0; j < n; ++j)
-    if (!st.has[j]) return false;
-  return true;
-}
 
 template <int NAX, int DC, bool REALC, int SK>
 void plain_fixed(const StarParams& st, int nrhs, int D, const float2* h, float2* w, cudaStream_t s) {
