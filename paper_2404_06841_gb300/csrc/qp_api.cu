@@ -837,7 +837,7 @@ Entry& get_entry(Solver* sv, const Units& us, const Key& key, cudaStream_t s) {
                        ? (p0->kind == QP_COEF_DIAG ? 2 : 1) : 0;
     int capn = 0;
     try {
-      capn = persistent_capacity(us.all_real, us.max_rhs, sk, smem);
+      capn = persistent_capacity(us.all_real, us.max_rhs, sk, sk ? &p0->star_host : nullptr, smem);
     } catch (const QpError&) {
       cudaGetLastError();
       capn = 0;

@@ -209,16 +209,6 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 4)
   apply_units<T, EPI, REALC, NR, SK, NAX, DC>(b, level, refine, cond, st);
 }
 
-// A star-1 plan of one of the fixed geometries compiled in: (n, d) = (6, 3), (4, 2), (2, 1), taps on every axis,
-// nr = d right-hand sides; n gets the number of axes.
-inline bool fixed_geometry(const StarParams& st, int nr, int& n) {
-  n = st.n;
-  if (!((n == 6 && st.d == 3) || (n == 4 && st.d == 2) || (n == 2 && st.d == 1)) || nr != st.d) return false;
-  for (int j = 0; j < n; ++j)
-    if (!st.has[j]) return false;
-  return true;
-}
-
 // Batch FP32 (h, Q h) apply of a single star-1 unit of a fixed geometry (qp_apply_fixed_batch.cu); false: not one
 // of them, nothing launched.
 bool launch_batch_star_fixed(const BatchDev& b, int level, int refine, unsigned long long cond, int nblk, size_t smem,

@@ -281,7 +281,17 @@ struct PersistArgs {
 size_t persistent_smem(int coef_count);
 // sk: 0 the plan's stencil from shared memory; 1 / 2 a star-1 plan with a scalar / diagonal coefficient and
 // stored FP64 weights (its StarParams st passed by value).
-int persistent_capacity(bool realc, int nr, int sk, size_t smem);
+// A star-1 plan of one of the fixed geometries compiled in: (n, d) = (6, 3), (4, 2), (2, 1), taps on every axis,
+// nr = d right-hand sides; n gets the number of axes.
+inline bool fixed_geometry(const StarParams& st, int nr, int& n) {
+  n = st.n;
+  if (!((n == 6 && st.d == 3) || (n == 4 && st.d == 2) || (n == 2 && st.d == 1)) || nr != st.d) return false;
+  for (int j = 0; j < n; ++j)
+    if (!st.has[j]) return false;
+  return true;
+}
+
+int persistent_capacity(bool realc, int nr, int sk, const StarParams* st, size_t smem);
 void launch_persistent(const BatchDev& b, bool realc, int nr, int sk, const StarParams* st, int mode, bool warm,
                        unsigned* bar, int* err, double timeout_s, int grid, size_t smem, cudaStream_t s);
 

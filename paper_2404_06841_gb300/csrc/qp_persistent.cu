@@ -12,10 +12,21 @@ const void* persistent_star_kernel_nr1(bool realc, int sk);
 const void* persistent_star_kernel_nr2(bool realc, int sk);
 const void* persistent_star_kernel_nr3(bool realc, int sk);
 const void* persistent_star_kernel_nr4(bool realc, int sk);
+const void* persistent_star_fixed_kernel_n2(bool realc, int sk);
+const void* persistent_star_fixed_kernel_n4(bool realc, int sk);
+const void* persistent_star_fixed_kernel_n6(bool realc, int sk);
 
 namespace {
 
-const void* pick(bool realc, int nr, int sk) {
+// The instantiation for (realc, nr, sk); a star-1 plan of a fixed geometry (st) takes the one with its number of
+// axes and d compiled in (bit for bit the same arithmetic).
+const void* pick(bool realc, int nr, int sk, const StarParams* st) {
+  int n = 0;
+  if (sk != 0 && st && fixed_geometry(*st, nr, n)) {
+    if (n == 6) return persistent_star_fixed_kernel_n6(realc, sk);
+    if (n == 4) return persistent_star_fixed_kernel_n4(realc, sk);
+    return persistent_star_fixed_kernel_n2(realc, sk);
+  }
   if (sk != 0) {
     switch (nr) {
       case 1: return persistent_star_kernel_nr1(realc, sk);
@@ -37,8 +48,8 @@ const void* pick(bool realc, int nr, int sk) {
 size_t persistent_smem(int coef_count) { return (size_t)coef_count * (sizeof(double2) + sizeof(float2)); }
 
 // Largest co-resident grid of the persistent solve for this instantiation (0: no cooperative launch).
-int persistent_capacity(bool realc, int nr, int sk, size_t smem) {
-  const void* fn = pick(realc, nr, sk);
+int persistent_capacity(bool realc, int nr, int sk, const StarParams* st, size_t smem) {
+  const void* fn = pick(realc, nr, sk, st);
   int dev = 0, coop = 0, sms = 0, per = 0;
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
@@ -50,7 +61,7 @@ int persistent_capacity(bool realc, int nr, int sk, size_t smem) {
 }
 
 // Launches the persistent solve of one unit (b.single). bar (2 unsigned) and err (1 int) are device words
-// zeroed here on the stream; grid must not exceed persistent_capacity (of the same realc, nr, sk).
+// zeroed here on the stream; grid must not exceed persistent_capacity (of the same realc, nr, sk, st).
 void launch_persistent(const BatchDev& b, bool realc, int nr, int sk, const StarParams* st, int mode, bool warm,
                        unsigned* bar, int* err, double timeout_s, int grid, size_t smem, cudaStream_t s) {
   PersistArgs a;
@@ -64,7 +75,7 @@ void launch_persistent(const BatchDev& b, bool realc, int nr, int sk, const Star
   CK(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
   CK(cudaMemsetAsync(err, 0, sizeof(int), s));
   void* args[] = {&a};
-  CK(cudaLaunchCooperativeKernel(pick(realc, nr, sk), dim3(grid), dim3(BLOCK), args, smem, s));
+  CK(cudaLaunchCooperativeKernel(pick(realc, nr, sk, sk != 0 ? st : nullptr), dim3(grid), dim3(BLOCK), args, smem, s));
   count_launch();
 }
 

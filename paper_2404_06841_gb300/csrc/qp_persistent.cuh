@@ -151,7 +151,7 @@ __device__ __forceinline__ void ph_init(const BatchDev& b, const UnitDev& un, in
 // reduces its norm and ||F||^2 over k != 0; EPI_NONE writes Q src.
 // SK: 0 the plan's stencil from shared memory; 1 / 2 the star-1 stencil of a scalar / diagonal coefficient
 // from st (the kernel parameter; FP64 from the plan's stored weights).
-template <typename T, bool REALC, int NR, int EPI, int SK>
+template <typename T, bool REALC, int NR, int EPI, int SK, int NAX = 0, int DC = 0>
 __device__ __forceinline__ void ph_apply(const BatchDev& b, const UnitDev& un, int c, const PlanDev& sp,
                                          const cplx<T>* scoef, const StarParams& st, const cplx<T>* src,
                                          cplx<T>* dst, const cplx<T>* F, bool zero_src = false) {
@@ -173,7 +173,7 @@ __device__ __forceinline__ void ph_apply(const BatchDev& b, const UnitDev& un, i
         for (int r = 0; r < NR; ++r) acc[s][r] = mk<T>(0, 0);
     } else if constexpr (SK != 0) {
       // FP64 level: the plan's stored weights; FP32 level: formed
-      apply_run_star<T, REALC, NR, false, SK == 2, sizeof(T) == 8 ? 1 : 0>(st, e0, src, D, nrhs, acc);
+      apply_run_star<T, REALC, NR, false, SK == 2, sizeof(T) == 8 ? 1 : 0, NAX, DC>(st, e0, src, D, nrhs, acc);
     } else {
       apply_run<T, REALC, NR, PRUN, false>(sp, scoef, e0, src, D, nrhs, acc);
     }
@@ -301,7 +301,7 @@ __device__ __forceinline__ LevelVecs<float> level_vecs(const UnitDev& un, float)
 // tolerance sqrt(tol2), at most maxit iterations. The solver state lives in ls (shared, written by thread 0).
 // zero_rhs marks right-hand sides started from F = 0 (refinement: already converged). zero_u: U = 0 first (T =
 // float always; FP64 without a warm start). Returns false on a barrier timeout.
-template <typename T, bool REALC, int NR, int SK>
+template <typename T, bool REALC, int NR, int SK, int NAX = 0, int DC = 0>
 __device__ __forceinline__ bool pcg_solve_block(const PersistArgs& a, const UnitDev& un, const PlanDev& sp, const cplx<T>* scoef,
                                 bool warm, bool zero_u, RhsSt* ls, const int* zero_rhs, double tol2, int maxit) {
   const BatchDev& b = a.b;
@@ -311,7 +311,7 @@ __device__ __forceinline__ bool pcg_solve_block(const PersistArgs& a, const Unit
   __shared__ T s_coef[MAXR];
   if (warm) {
     for (int c = blockIdx.x; c < b.nchunks; c += gridDim.x)
-      ph_apply<T, REALC, NR, EPI_NONE, SK>(b, un, c, sp, scoef, a.star, L.U, L.w, L.F);
+      ph_apply<T, REALC, NR, EPI_NONE, SK, NAX, DC>(b, un, c, sp, scoef, a.star, L.U, L.w, L.F);
     if (!grid_sync(a)) return false;
   }
   for (int c = blockIdx.x; c < b.nchunks; c += gridDim.x)
@@ -343,7 +343,7 @@ __device__ __forceinline__ bool pcg_solve_block(const PersistArgs& a, const Unit
     if (all) break;
     // w = Q h and (h, w); alpha = (r, z) / (h, Q h)
     for (int c = blockIdx.x; c < b.nchunks; c += gridDim.x)
-      ph_apply<T, REALC, NR, EPI_DOT_HW, SK>(b, un, c, sp, scoef, a.star, L.h, L.w, L.F);
+      ph_apply<T, REALC, NR, EPI_DOT_HW, SK, NAX, DC>(b, un, c, sp, scoef, a.star, L.h, L.w, L.F);
     if (!grid_sync(a)) return false;
     {
       double v[NR];
@@ -416,18 +416,20 @@ __device__ __forceinline__ bool pcg_solve_block(const PersistArgs& a, const Unit
 
 // FP64 true residual w = F - Q U and its reduction; every thread gets (|r|^2, |F|^2) per right-hand side.
 // zero_u: U = 0, so w = F without an apply.
-template <bool REALC, int NR, int SK>
+template <bool REALC, int NR, int SK, int NAX = 0, int DC = 0>
 __device__ __forceinline__ bool true_residual(const PersistArgs& a, const UnitDev& un, const PlanDev& sp, const double2* sc64,
                               double (&v)[2 * NR], bool zero_u = false) {
   const BatchDev& b = a.b;
   for (int c = blockIdx.x; c < b.nchunks; c += gridDim.x)
-    ph_apply<double, REALC, NR, EPI_RESIDUAL, SK>(b, un, c, sp, sc64, a.star, un.U, un.w, un.F, zero_u);
+    ph_apply<double, REALC, NR, EPI_RESIDUAL, SK, NAX, DC>(b, un, c, sp, sc64, a.star, un.U, un.w, un.F, zero_u);
   if (!grid_sync(a)) return false;
   all_sums<2 * NR>(b, un, S_RES, v);
   return true;
 }
 
-template <bool REALC, int NR, int SK>
+// NAX, DC (0: from the plan at run time): the number of axes (every one with taps) and d compiled into the FP32
+// level's star-1 stencil, and with FIX64 into the FP64 level's too.
+template <bool REALC, int NR, int SK, int NAX = 0, int DC = 0, bool FIX64 = false>
 __global__ void __launch_bounds__(BLOCK, NR >= 3 ? 1 : 2) k_pcg_persistent(const __grid_constant__ PersistArgs a) {
   __shared__ __align__(16) PlanDev sp;
   __shared__ RhsSt ls[MAXR];
@@ -456,11 +458,11 @@ __global__ void __launch_bounds__(BLOCK, NR >= 3 ? 1 : 2) k_pcg_persistent(const
   __syncthreads();
   bool ok = true;
   if (!refine) {
-    ok = pcg_solve_block<double, REALC, NR, SK>(a, un, sp, sc64, a.warm != 0, a.warm == 0, ls, s_zero, b.tol2,
+    ok = pcg_solve_block<double, REALC, NR, SK, FIX64 ? NAX : 0, FIX64 ? DC : 0>(a, un, sp, sc64, a.warm != 0, a.warm == 0, ls, s_zero, b.tol2,
                                                 b.maxit);
     if (ok) {
       double v[2 * NR];
-      ok = true_residual<REALC, NR, SK>(a, un, sp, sc64, v);
+      ok = true_residual<REALC, NR, SK, FIX64 ? NAX : 0, FIX64 ? DC : 0>(a, un, sp, sc64, v);
       if (ok && threadIdx.x == 0)
         for (int k = 0; k < nrhs && k < NR; ++k) {
           ls[k].orr = v[2 * k];
@@ -480,7 +482,9 @@ __global__ void __launch_bounds__(BLOCK, NR >= 3 ? 1 : 2) k_pcg_persistent(const
     for (int outer = 0; ok && outer <= b.max_outer + 1; ++outer) {
       // FP64 true residual: the outer convergence test and the scale of the next inner right-hand side
       double v[2 * NR];
-      if (!(ok = true_residual<REALC, NR, SK>(a, un, sp, sc64, v, outer == 0 && !a.warm))) break;
+      if (!(ok = true_residual<REALC, NR, SK, FIX64 ? NAX : 0, FIX64 ? DC : 0>(a, un, sp, sc64, v,
+                                                                              outer == 0 && !a.warm)))
+        break;
       if (threadIdx.x == 0) {
         for (int k = 0; k < nrhs && k < NR; ++k) {
           RhsSt& x = ls[k];
@@ -529,7 +533,7 @@ __global__ void __launch_bounds__(BLOCK, NR >= 3 ? 1 : 2) k_pcg_persistent(const
         }
       }
       // (the inner init reads F32 only at the modes this thread just wrote: no barrier needed before it)
-      if (!(ok = pcg_solve_block<float, REALC, NR, SK>(a, un, sp, sc32, false, true, ls, s_zero, b.tol2, b.maxit)))
+      if (!(ok = pcg_solve_block<float, REALC, NR, SK, NAX, DC>(a, un, sp, sc32, false, true, ls, s_zero, b.tol2, b.maxit)))
         break;
       // U64 += |r64| c32 for the right-hand sides still refining
       for (int c = blockIdx.x; c < b.nchunks; c += gridDim.x) {

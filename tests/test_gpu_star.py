@@ -129,28 +129,31 @@ def test_fixed_geometry_plain_apply_is_the_general_one(qp, d, n, N, kind, real):
 @pytest.mark.parametrize("d,n,N,kind,real", [(1, 2, (5, 8), "scalar", False), (2, 4, (6, 5, 4, 8), "diag", True),
                                              (3, 6, (4, 3, 4, 5, 4, 6), "diag", False),
                                              (2, 4, (4, 6, 5, 4), "scalar", False)])
-def test_fixed_geometry_batch_apply_in_refinement_is_the_general_one(qp, d, n, N, kind, real):
-    """Every axis with taps and d right-hand sides: the graph form's FP32 iterations take the batch kernel with the
-    geometry compiled in, the persistent form walks the same runs with the general stencil; the refined solutions
-    must agree bit for bit and reach the tolerance against the oracle."""
+def test_fixed_geometry_solves_are_the_general_ones(qp, d, n, N, kind, real):
+    """Every axis with taps and d right-hand sides: the persistent solve and the graph form's FP32 batch apply take
+    the kernels with the geometry compiled in; with d + 1 right-hand sides the general ones run. Each right-hand
+    side's iterates do not depend on the others, so the first d solutions must agree bit for bit across the four
+    runs, in FP64 and in refinement mode, and reach the tolerance against the oracle."""
     inst = W.random_star_instance(d, n, N, kind, seed=50 + n, real=real)
-    F = _rand(d, inst.N, 6)
-    F.reshape(d, -1)[:, 0] = 0
-    out = {}
-    for ex in (qp.QP_EXEC_PERSISTENT, qp.QP_EXEC_GRAPH):
-        plan = qp.plan_from_instance(inst, max_rhs=d, exec_mode=ex)
-        Ft = torch.from_numpy(F).cuda()
-        Ut = torch.zeros_like(Ft)
-        infos = qp.qp_pcg_solve(plan, Ft, Ut, tol=1e-10, maxit=2000, mode=qp.QP_MODE_FP32_REFINE)
-        out[ex] = (Ut.cpu().numpy(), infos)
-    Up, ip = out[qp.QP_EXEC_PERSISTENT]
-    Ug, ig = out[qp.QP_EXEC_GRAPH]
-    assert np.array_equal(Up, Ug) and ip == ig
+    F = _rand(d + 1, inst.N, 6)
+    F.reshape(d + 1, -1)[:, 0] = 0
     op = O.Operator(inst)
-    for r in range(d):
-        assert ip[r]["status"] == "QP_OK"
-        res = np.linalg.norm(F[r] - op(Up[r])) / np.linalg.norm(F[r])
-        assert res <= 1.2e-10, res
+    for m in (qp.QP_MODE_FP64, qp.QP_MODE_FP32_REFINE):
+        runs = []
+        for ex in (qp.QP_EXEC_PERSISTENT, qp.QP_EXEC_GRAPH):
+            plan = qp.plan_from_instance(inst, max_rhs=d + 1, exec_mode=ex)
+            for nr in (d, d + 1):
+                Ft = torch.from_numpy(F[:nr].copy()).cuda()
+                Ut = torch.zeros_like(Ft)
+                infos = qp.qp_pcg_solve(plan, Ft, Ut, tol=1e-10, maxit=2000, mode=m)
+                runs.append((Ut.cpu().numpy()[:d], infos[:d]))
+        U0, i0 = runs[0]
+        for U1, i1 in runs[1:]:
+            assert np.array_equal(U0, U1) and i0 == i1
+        for r in range(d):
+            assert i0[r]["status"] == "QP_OK"
+            res = np.linalg.norm(F[r] - op(U0[r])) / np.linalg.norm(F[r])
+            assert res <= 1.2e-10, res
 
 
 def test_general_taps_are_not_star(qp):
