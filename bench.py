@@ -118,7 +118,7 @@ def fft_apply_bytes(d, ncomp, nrhs, D, es):
 # exists.
 TRAFFIC = {
     # cfg1: one solve (33 iterations, 2 correctors) in k_pcg_persistent; vectors and stored weights stay in L2
-    ("k_pcg_persistent", "cfg1"): 9568512 + 261120,
+    ("k_pcg_persistent", "cfg1"): 9572352 + 236032,
     # cfg4: k_apply_plain_star (geometry compiled in) captured at N = 14 (7.53 M modes; h and w exceed L2), scaled
     # by 16^6 / 14^6
     ("k_apply_plain", "cfg4"): int((207640320 + 153260032) * (16 ** 6 / 14 ** 6)),
