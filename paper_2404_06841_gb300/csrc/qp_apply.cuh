@@ -202,7 +202,8 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 3) k_apply(BatchDe
 
 // Batch apply of a single star-1 unit (even last axis): the stencil data as a kernel parameter. The FP32 star
 // stencil waits on L2 latency of its neighbour reads: four blocks per SM (64 registers) hide it best on GB300
-// (cfg4: 435 us at four blocks, 470 at three, 474 at five).
+// (cfg4: 435 us at four blocks, 470 at three, 474 at five; the fixed-geometry variant, spill-free at three blocks,
+// took the cfg4 solve to 41.7 ms against 37.7 at four).
 template <typename T, int EPI, bool REALC, int NR, int SK, int NAX = 0, int DC = 0>
 __global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 4)
     k_apply_star(BatchDev b, int level, int refine, unsigned long long cond, const __grid_constant__ StarParams st) {
