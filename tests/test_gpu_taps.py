@@ -68,6 +68,36 @@ def test_apply_full_size_sampled_cfg4(qp):
         assert np.abs(got - ref).max() <= 2e-6 * scale
 
 
+def test_refinement_solve_of_a_unit_in_two_waves(qp):
+    """cfg4's geometry at N = 12 (2,985,984 modes: 1,167 chunks of 2,560, more than one wave of 608 resident
+    blocks, so the batch kernels walk their chunks in two waves over halves of the vector), refinement solve of
+    the three corrector right-hand sides built by the oracle. The residual is recomputed over the whole vector by
+    the plain FP64 apply (one run per thread, no chunks), and at sampled modes by the oracle's own sum."""
+    inst = W.cfg4(N=12)
+    Ahat = O.coefficient_modes(inst)
+    F = np.stack([O.corrector_rhs(inst.P, inst.N, Ahat, j).reshape(-1) for j in range(3)])
+    del Ahat
+    plan = qp.plan_from_instance(inst)
+    Ft = torch.from_numpy(F).cuda()
+    Ut = torch.zeros_like(Ft)
+    infos = qp.qp_pcg_solve(plan, Ft, Ut, tol=1e-10, maxit=2000, mode=qp.QP_MODE_FP32_REFINE)
+    assert all(i["status"] == "QP_OK" for i in infos), infos
+    QU = torch.empty_like(Ut)
+    qp.qp_apply_stiffness(plan, Ut, QU, qp.QP_FP64)
+    for r in range(3):
+        rel = float(torch.linalg.vector_norm(Ft[r] - QU[r]) / torch.linalg.vector_norm(Ft[r]))
+        assert rel <= 1.2e-10, (r, rel)
+    U = Ut.cpu().numpy()
+    D = inst.D
+    rng = np.random.default_rng(1)
+    flat = [1, D - 1, D // 2] + [int(x) for x in rng.integers(0, D, 40)]
+    pts = [np.unravel_index(i, inst.N) for i in flat]
+    for r in range(3):
+        qu = O.apply_taps_at(inst.P, inst.N, inst.coeff.taps_k, inst.coeff.taps_val, "diag",
+                             U[r].reshape(inst.N), pts)
+        assert np.abs(F[r][flat] - qu).max() <= 1.2e-10 * np.linalg.norm(F[r])
+
+
 @pytest.mark.parametrize("d,n,N,kind", [(2, 3, (6, 8, 4), "sym"), (3, 3, (4, 6, 8), "diag"), (1, 2, (10, 12), "scalar")])
 def test_corrector_rhs_and_astar_reduce(qp, d, n, N, kind):
     inst = W.random_instance(d, n, N, kind, "taps", seed=3)
