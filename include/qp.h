@@ -41,7 +41,7 @@ typedef enum {
   QP_ERR_BREAKDOWN = 4,       /* PCG met (h, Q h) <= 0 or a NaN */
   QP_ERR_NO_CONVERGENCE = 5,  /* maxit reached before the tolerance */
   QP_ERR_TIMEOUT = 6,         /* a bounded device wait gave up */
-  QP_ERR_UNSUPPORTED = 7,     /* valid request that this build does not implement */
+  QP_ERR_UNSUPPORTED = 7,     /* valid request that the library does not implement */
   QP_ERR_OOM = 8,             /* device allocation failed */
   QP_ERR_CUDA = 9             /* any other CUDA runtime error */
 } qp_status;

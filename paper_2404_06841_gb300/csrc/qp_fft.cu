@@ -308,7 +308,7 @@ static void axis_two(cplx<T>* data, long long O, int I, int sign, cudaStream_t s
   count_launch();
 }
 
-// True if this build transforms an axis of size N.
+// True if the library's FFT kernels transform an axis of size N.
 bool fft_supported(int N) {
   switch (N) {
     case 2: case 3: case 4: case 6: case 8: case 9: case 12: case 16: case 18: case 24: case 27: case 32:
