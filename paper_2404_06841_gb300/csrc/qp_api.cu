@@ -780,6 +780,7 @@ Entry& get_entry(Solver* sv, const Units& us, const Key& key, cudaStream_t s) {
     const int64_t chunk = chunk_modes(p->D);
     x.chunk = (int)chunk;
     x.run = last_axis_run(p);
+    x.fft = p->backend == QP_BACKEND_FFT ? 1 : 0;
     x.chunk0 = (int)chunk_unit.size();
     x.nchunk = (int)((p->D + chunk - 1) / chunk);
     for (int c = 0; c < x.nchunk; ++c) chunk_unit.push_back(u);

@@ -102,8 +102,10 @@ __device__ __forceinline__ void apply_units(const BatchDev& b, int level, int re
       else active = true;
     }
     if (!active) continue;
-    if constexpr (SK == 0) {   // star-1 kernels take the stencil from their kernel parameter instead
-      if (un.plan != cur) {
+    // star-1 kernels take the stencil from their kernel parameter instead; FFT units need no stencil
+    const bool fft_unit = SK == 0 && un.fft != 0;
+    if constexpr (SK == 0) {
+      if (!fft_unit && un.plan != cur) {
         cur = un.plan;
         load_plan<T>(cur, sp, scoef);
       }
@@ -119,7 +121,6 @@ __device__ __forceinline__ void apply_units(const BatchDev& b, int level, int re
       dst = reinterpret_cast<cplx<T>*>(un.w);
     }
     const cplx<T>* F = reinterpret_cast<const cplx<T>*>(un.F);
-    const bool fft_unit = SK == 0 && (sp.backend == QP_BACKEND_FFT);
     constexpr int NV = (EPI == EPI_RESIDUAL) ? 2 * NR : NR;   // reduced quantities: (h,w) or (|F-w|^2, |F|^2)
     T vt[NV];                                                   // per-thread partials in the vector precision
     double v[NV];

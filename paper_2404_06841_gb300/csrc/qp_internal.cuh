@@ -182,7 +182,9 @@ struct UnitDev {
   int D, nrhs, chunk0, nchunk;
   int chunk;           // modes per chunk: a function of D only, so a unit reduces in the same order alone or batched
   int run;             // stencil run along the last axis: 2 when its length is even, else 1
-  int pad_[2];
+  int fft;             // 1: FFT-backend unit (its applies write w in FFT passes; the batch kernels add only the
+                       // epilogue and need no plan in shared memory)
+  int pad_;
   const double2* F;   // right-hand side (FP64)
   double2* U;         // solution (FP64)
   double2* r;         // FP64 PCG residual
