@@ -1,7 +1,8 @@
-"""Writes tests/golden/astar_full_size.json: a* of the full-size workloads cfg2 and cfg4 computed by the FP64
-oracle only (C-PCG, Jacobi, tolerance 1e-13), for the GPU tests that cannot afford the oracle at run time.
+"""Writes tests/golden/astar_full_size.json: a* of the full-size workloads computed by the FP64 oracle only
+(C-PCG, Jacobi, tolerance 1e-13), for the GPU tests that cannot afford the oracle at run time:
+cfg2 and cfg4 (one instance each) and cfg3 (all 64 instances of the batched workload, in instance order).
 
-Run from the repository root: python tests/golden/make_golden.py [cfg2] [cfg4]
+Run from the repository root: python tests/golden/make_golden.py [cfg2] [cfg3] [cfg4]
 """
 import json
 import os
@@ -15,24 +16,31 @@ import qp_workloads as W  # noqa: E402
 from oracle import qp_oracle as O  # noqa: E402
 
 OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "astar_full_size.json")
+HOW = "oracle/qp_oracle.py homogenized(tol=1e-13), Jacobi C-PCG (Algorithm 2)"
+
+
+def one(inst):
+    t0 = time.time()
+    A, Us, infos, Ac = O.homogenized(inst, tol=1e-13)
+    rec = {"name": inst.name, "astar_re": A.tolist(), "astar_im": Ac.imag.tolist(),
+           "iterations": [i["iterations"] for i in infos],
+           "rel_residual": [i["rel_residual"] for i in infos],
+           "oracle_seconds": round(time.time() - t0, 1), "how": HOW}
+    if "clamped_fraction" in inst.meta:
+        rec["clamped_fraction"] = inst.meta["clamped_fraction"]
+    print(inst.name, A.tolist(), [i["iterations"] for i in infos], rec["oracle_seconds"], flush=True)
+    return rec
 
 
 def main(names):
     data = json.load(open(OUT)) if os.path.exists(OUT) else {}
     for name in names:
-        inst = getattr(W, name)()
-        t0 = time.time()
-        A, Us, infos, Ac = O.homogenized(inst, tol=1e-13)
-        data[name] = {"name": inst.name, "astar_re": A.tolist(), "astar_im": Ac.imag.tolist(),
-                      "iterations": [i["iterations"] for i in infos],
-                      "rel_residual": [i["rel_residual"] for i in infos],
-                      "oracle_seconds": round(time.time() - t0, 1),
-                      "how": "oracle/qp_oracle.py homogenized(tol=1e-13), Jacobi C-PCG (Algorithm 2)"}
-        if "clamped_fraction" in inst.meta:
-            data[name]["clamped_fraction"] = inst.meta["clamped_fraction"]
+        if name == "cfg3":
+            data[name] = {"instances": [one(inst) for inst in W.cfg3()], "how": HOW}
+        else:
+            data[name] = one(getattr(W, name)())
         json.dump(data, open(OUT, "w"), indent=1)
-        print(name, A.tolist(), infos, time.time() - t0, flush=True)
 
 
 if __name__ == "__main__":
-    main(sys.argv[1:] or ["cfg2", "cfg4"])
+    main(sys.argv[1:] or ["cfg2", "cfg3", "cfg4"])

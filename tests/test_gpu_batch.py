@@ -47,18 +47,27 @@ def test_batch_equals_single_solves_and_oracle(qp, mode):
 
 
 def test_cfg3_full_batch(qp):
-    """All 64 instances of the batched workload in one solve (FP32 + FP64 refinement to 1e-10)."""
+    """All 64 instances of the batched workload in one solve (FP32 + FP64 refinement to 1e-10): every entry of
+    every a* against the oracle's (tests/golden/astar_full_size.json, written by the oracle only), plus the exact
+    1D identity (P1) for the d = 1 instances and symmetry with the Voigt-Reuss bounds (P8) for the d = 2 ones."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                                       "astar_full_size.json")))["cfg3"]["instances"]
     insts = W.cfg3()
     plans = [qp.plan_from_instance(i) for i in insts]
     batch = qp.qp_batch_create(plans)
     As, infos = qp.qp_batch_homogenized(batch, tol=1e-10, mode=qp.QP_MODE_FP32_REFINE)
     assert len(infos) == sum(i.d for i in insts)
     assert all(x["status"] == "QP_OK" and x["rel_residual"] <= 1e-10 for x in infos)
-    for inst, A in zip(insts, As):
+    for inst, A, g in zip(insts, As, gold):
+        assert g["name"] == inst.name
+        ref = np.array(g["astar_re"])
+        assert np.abs(A - ref).max() <= 1e-10 * np.abs(ref).max(), (inst.name, A - ref)
         a = W.sample_on_grid(inst.N, inst.coeff.taps_k, inst.coeff.taps_val)[0]
         if inst.d == 1:
-            ref = 1.0 / np.mean(1.0 / a)                       # P1: exact discrete identity in 1D
-            assert abs(A[0, 0] - ref) <= 1e-10 * ref, inst.name
+            p1 = 1.0 / np.mean(1.0 / a)                        # P1: exact discrete identity in 1D
+            assert abs(A[0, 0] - p1) <= 1e-10 * p1, inst.name
         else:
             assert abs(A[0, 1] - A[1, 0]) <= 1e-10 * np.abs(A).max()
             ev = np.linalg.eigvalsh(0.5 * (A + A.T))

@@ -163,7 +163,9 @@ def test_cfg2_full_size_refinement_against_golden(qp):
     inst = W.cfg2()
     plan = qp.plan_from_instance(inst)
     ref = np.array(gold["astar_re"])
+    ref_im = np.array(gold["astar_im"])   # Im A*_12 ~ -5.6e-8: the Nyquist content of the clamped coefficient
     for mode in (qp.QP_MODE_FP32_REFINE, qp.QP_MODE_FP64):
         A, infos = qp.qp_homogenized(plan, tol=1e-10, mode=mode)
         assert all(i["status"] == "QP_OK" and i["rel_residual"] <= 1e-10 for i in infos)
         assert np.abs(A.real - ref).max() <= 1e-10 * np.abs(ref).max(), (mode, A.real - ref)
+        assert np.abs(A.imag - ref_im).max() <= 1e-10 * np.abs(ref).max(), (mode, A.imag - ref_im)
