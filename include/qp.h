@@ -61,7 +61,7 @@ typedef struct qp_batch qp_batch;   /* opaque; a set of plans solved together */
 /* The coefficient A(theta): real, d x d symmetric, uniformly elliptic (Sec. 2.2).
  * kind: QP_COEF_SCALAR (A = a I, 1 component), QP_COEF_DIAG (d components a_11..a_dd),
  *       QP_COEF_SYM (d(d+1)/2 components: the upper triangle row by row, 11, 12, .., 1d, 22, .., dd).
- * repr: QP_REPR_TAPS - Fourier modes (taps): tap_k host int32 [ntaps x n], every |m_j| < N_j / 2;
+ * repr: QP_REPR_TAPS - Fourier modes (taps): tap_k host int32 [ntaps x n], every |m_j| < N_j / 2 and <= 127;
  *       tap_val host double [ntaps x ncomp x 2] (re, im) with A~_{-m} = conj(A~_m) (so A is real).
  *       Values are the Fourier coefficients of Sec. 3.1.1; a mode listed twice is summed.
  *       QP_REPR_GRID - samples A(y_j) at y_j = 2 pi j / N: grid is DEVICE double [ncomp x D], C order, 8-byte
@@ -131,8 +131,8 @@ typedef struct {
 qp_status qp_plan_create(int d, int n, const double* P, const int* N, const qp_coeff* coeff,
                          const qp_options* opt, void* stream, qp_plan** out);
 /* Waits for all work on the device (no stream may still use the plan), then returns the plan's device memory to
- * the library's pool (blocks are kept cached for the next plans; beyond an eighth of the device's memory, at
- * least 1 GiB, they go back to the device). */
+ * the library's pool (blocks are kept cached for the next plans up to the cache size of qp_set_memory_cache, by
+ * default an eighth of the device's memory and at least 1 GiB; the rest goes back to the device). */
 qp_status qp_plan_destroy(qp_plan* plan);
 qp_status qp_plan_query(const qp_plan* plan, qp_plan_info* info);
 
@@ -189,7 +189,9 @@ qp_status qp_batch_destroy(qp_batch* batch);
  * library routine. Arguments as qp_plan_create (d, n, P, N, coeff; taps only) and qp_pcg_solve (nrhs, F, U
  * with U as the initial guess, opts with mode QP_MODE_FP64, info). Needs about (24 + 48 nrhs) D bytes plus
  * the tap tables; larger problems return QP_ERR_INVALID_ARG ("too large for the static scratch") before any
- * device work. The first call on a device looks up the array's device address (cudaGetSymbolAddress), so
+ * device work. It checks its inputs as qp_plan_create does (QP_ERR_NOT_ELLIPTIC for a mean tap that is not positive
+ * definite) and, like qp_pcg_solve, solves again from the current U (at most twice) a right-hand side whose true
+ * residual misses the tolerance after its recursive residual met it. The first call on a device looks up the array's device address (cudaGetSymbolAddress), so
  * make that first call before any stream capture. All calls share the one array: calls whose GPU work
  * overlaps (other streams or threads) race and give wrong results; serialise them. Each call clears what
  * must start at zero, so a call never depends on what the previous call left there. Synchronises stream. */
@@ -212,6 +214,36 @@ qp_status qp_plan_diagonal(qp_plan* plan, int precond, double* out, void* stream
  * K_N^n (truncation) add the sum of their |coefficient|^2 to out[r]^2; the caller adds that part. Deterministic
  * FP64 reduction; synchronises stream. */
 qp_status qp_l2qp_error(qp_plan* plan, int nrhs, const void* U, const void* Uref, double* out, void* stream);
+
+/* The library's device-memory pool on the current device (plans, solvers and batches take their buffers from it):
+ * reserved_bytes = memory the pool holds from the device, used_bytes = memory in live buffers, allocations = pool
+ * allocations served so far in this process (all devices). Any output may be NULL. */
+qp_status qp_memory_pool_stats(int64_t* reserved_bytes, int64_t* used_bytes, uint64_t* allocations);
+
+/* Freed pool memory kept cached for later plans when a plan or batch is destroyed (process-wide): bytes >= 0 keeps
+ * at most that much (0 returns every freed block to the device at once); bytes < 0 restores the default, an eighth
+ * of the device's memory and at least 1 GiB. The pool is trimmed to the new size at once. */
+qp_status qp_set_memory_cache(int64_t bytes);
+
+/* Phase timing of solves, for profiling (not in the paper). While it is enabled, qp_pcg_solve, qp_homogenized and
+ * qp_batch_homogenized run in the host-driven form (the kernels of the graph form, launched one PCG iteration at a
+ * time and with no launch after convergence; the iterates are bitwise the same) with CUDA events on the solve's
+ * stream around each group of kernels, and add each group's duration to its phase:
+ *   QP_PHASE_APPLY32 / APPLY64: the stiffness apply of a PCG iteration (FP32 inner level / FP64 level) with its
+ *     (h, Q h) reduction (FFT-backend plans: the FFT passes and the reduction);
+ *   QP_PHASE_UPDATE32 / UPDATE64: the alpha step and the reductions for beta (r -= alpha Q h, ...);
+ *   QP_PHASE_HUPDATE32 / HUPDATE64: the new search direction h = M r + beta h (and the U update);
+ *   QP_PHASE_INIT32 / INIT64: the PCG initialisation of a (inner) solve;
+ *   QP_PHASE_RESIDUAL64: FP64 applies of U (true residuals, warm starts);
+ *   QP_PHASE_REFINE: the refinement steps (scaled FP32 right-hand side, U += c / scale);
+ *   QP_PHASE_OTHER: zeroing and state resets.
+ * qp_set_phase_timing(enabled) also clears the totals. qp_phase_times: for phases 0 .. count - 1 the summed
+ * milliseconds (ms) and the number of timed groups (launches); either output may be NULL. Process-wide. */
+enum { QP_PHASE_APPLY32 = 0, QP_PHASE_UPDATE32 = 1, QP_PHASE_HUPDATE32 = 2, QP_PHASE_INIT32 = 3,
+       QP_PHASE_REFINE = 4, QP_PHASE_APPLY64 = 5, QP_PHASE_UPDATE64 = 6, QP_PHASE_HUPDATE64 = 7,
+       QP_PHASE_INIT64 = 8, QP_PHASE_RESIDUAL64 = 9, QP_PHASE_OTHER = 10, QP_NPHASE = 11 };
+qp_status qp_set_phase_timing(int enabled);
+qp_status qp_phase_times(double* ms, int64_t* launches, int count);
 
 /* Description of the last error on this host thread ("" if none). The string stays valid until the next call. */
 const char* qp_last_error(void);

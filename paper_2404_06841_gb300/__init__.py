@@ -28,6 +28,9 @@ QP_FP64, QP_FP32 = 0, 1
 QP_PRECOND_JACOBI, QP_PRECOND_FROBENIUS = 0, 1
 QP_MODE_FP64, QP_MODE_FP32_REFINE = 0, 1
 QP_EXEC_AUTO, QP_EXEC_DIRECT, QP_EXEC_GRAPH, QP_EXEC_PERSISTENT = 0, 1, 2, 3
+QP_PHASE_APPLY32, QP_PHASE_UPDATE32, QP_PHASE_HUPDATE32, QP_PHASE_INIT32, QP_PHASE_REFINE = 0, 1, 2, 3, 4
+QP_PHASE_APPLY64, QP_PHASE_UPDATE64, QP_PHASE_HUPDATE64, QP_PHASE_INIT64, QP_PHASE_RESIDUAL64 = 5, 6, 7, 8, 9
+QP_PHASE_OTHER, QP_NPHASE = 10, 11
 KIND_CODES = {"scalar": QP_COEF_SCALAR, "diag": QP_COEF_DIAG, "sym": QP_COEF_SYM}
 
 # Every symbol include/qp.h declares (checked by the test suite).
@@ -35,7 +38,10 @@ EXPORTS = ("qp_plan_create", "qp_plan_destroy", "qp_plan_query", "qp_apply_stiff
            "qp_pcg_solve", "qp_homogenized_reduce", "qp_homogenized", "qp_fft", "qp_batch_create",
            "qp_batch_homogenized", "qp_batch_destroy", "qp_last_error", "qp_launch_count",
            "qp_pcg_solve_taps_static", "qp_set_barrier_timeout", "qp_l2qp_error", "qp_plan_diagonal",
-           "qp_set_fft_autotune", "qp_fft_schedule", "qp_fft_set_schedule")
+           "qp_set_fft_autotune", "qp_fft_schedule", "qp_fft_set_schedule", "qp_memory_pool_stats",
+           "qp_set_memory_cache", "qp_set_phase_timing", "qp_phase_times")
+PHASES = ("apply32", "update32", "hupdate32", "init32", "refine", "apply64", "update64", "hupdate64", "init64",
+          "residual64", "other")
 
 
 class qp_coeff(C.Structure):
@@ -100,6 +106,10 @@ def load_library(path: str = LIB_PATH):
         "qp_set_fft_autotune": [i],
         "qp_fft_schedule": [vp, i, ip, ip, dp, C.c_char_p, i],
         "qp_fft_set_schedule": [vp, i, i],
+        "qp_memory_pool_stats": [C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_uint64)],
+        "qp_set_memory_cache": [C.c_int64],
+        "qp_set_phase_timing": [i],
+        "qp_phase_times": [dp, C.POINTER(C.c_int64), i],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -379,6 +389,32 @@ def qp_fft_schedule(plan: Plan, precision=QP_FP32) -> dict:
 
 def qp_fft_set_schedule(plan: Plan, precision, index: int) -> None:
     _check(_lib.qp_fft_set_schedule(plan.handle, int(precision), int(index)))
+
+
+def qp_memory_pool_stats() -> dict:
+    """The library's device-memory pool on the current device: reserved and used bytes, allocations served."""
+    res, use, n = C.c_int64(0), C.c_int64(0), C.c_uint64(0)
+    _check(_lib.qp_memory_pool_stats(C.byref(res), C.byref(use), C.byref(n)))
+    return {"reserved_bytes": res.value, "used_bytes": use.value, "allocations": n.value}
+
+
+def qp_set_memory_cache(nbytes: int) -> None:
+    """Freed pool memory kept cached after a destroy (bytes; 0 returns all of it; < 0 restores the default)."""
+    _check(_lib.qp_set_memory_cache(int(nbytes)))
+
+
+def qp_set_phase_timing(enabled: bool) -> None:
+    """Per-phase CUDA-event timing of solves (host-driven form while on); also clears the totals."""
+    _check(_lib.qp_set_phase_timing(1 if enabled else 0))
+
+
+def qp_phase_times() -> dict:
+    """{phase name: (milliseconds, timed launches)} accumulated since qp_set_phase_timing."""
+    n = len(PHASES)
+    ms = (C.c_double * n)()
+    cnt = (C.c_int64 * n)()
+    _check(_lib.qp_phase_times(ms, cnt, n))
+    return {name: (ms[i], cnt[i]) for i, name in enumerate(PHASES)}
 
 
 def qp_set_barrier_timeout(seconds: float) -> None:

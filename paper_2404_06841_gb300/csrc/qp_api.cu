@@ -225,23 +225,6 @@ bool is_23(int N) {
   return N == 1;
 }
 
-// Cholesky test of the real symmetric d x d matrix M (positive definite?).
-bool spd(const double M[MAXD][MAXD], int d) {
-  double L[MAXD][MAXD] = {};
-  for (int i = 0; i < d; ++i)
-    for (int j = 0; j <= i; ++j) {
-      double s = M[i][j];
-      for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
-      if (i == j) {
-        if (!(s > 0.0)) return false;
-        L[i][i] = std::sqrt(s);
-      } else {
-        L[i][j] = s / L[j][j];
-      }
-    }
-  return true;
-}
-
 // ------------------------------------------------------------------------------------------------ plan set-up
 
 void build_geometry(qp_plan* p, int d, int n, const double* P, const int* N) {
@@ -302,6 +285,7 @@ void build_taps(qp_plan* p, const qp_coeff* c) {
     for (int j = 0; j < n; ++j) {
       m[j] = c->tap_k[t * n + j];
       if (2 * std::abs(m[j]) >= p->N[j]) raise(QP_ERR_INVALID_ARG, "tap mode component |m_j| must be < N_j/2");
+      if (std::abs(m[j]) > 127) raise(QP_ERR_INVALID_ARG, "tap mode component |m_j| must be <= 127");
     }
     for (int q = 0; q < 2 * nc; ++q)
       if (!std::isfinite(c->tap_val[t * 2 * nc + q])) raise(QP_ERR_INVALID_ARG, "tap value is not finite");
@@ -342,21 +326,8 @@ void build_taps(qp_plan* p, const qp_coeff* c) {
     }
   }
   if (mean < 0) raise(QP_ERR_NOT_ELLIPTIC, "the coefficient has no mean (m = 0) tap");
-  {
-    double M0[MAXD][MAXD] = {};
-    for (int a = 0; a < d; ++a)
-      for (int b = 0; b < d; ++b) {
-        int comp = -1;
-        if (p->kind == QP_COEF_SCALAR) comp = (a == b) ? 0 : -1;
-        else if (p->kind == QP_COEF_DIAG) comp = (a == b) ? a : -1;
-        else {
-          const int lo = std::min(a, b), hi = std::max(a, b);
-          comp = lo * d - lo * (lo - 1) / 2 + (hi - lo);
-        }
-        M0[a][b] = comp >= 0 ? vals[mean][2 * comp] : 0.0;
-      }
-    if (!spd(M0, d)) raise(QP_ERR_NOT_ELLIPTIC, "the coefficient's mean A~_0 is not positive definite");
-  }
+  if (!mean_tap_spd(p->kind, d, vals[mean].data()))
+    raise(QP_ERR_NOT_ELLIPTIC, "the coefficient's mean A~_0 is not positive definite");
   // sorted order: mean, star taps by axis, multi-axis taps
   std::vector<int> order;
   order.push_back(mean);
@@ -574,10 +545,58 @@ void record_apply(const Units& us, const Entry& en, int level, int epi, int refi
   CK_LAUNCH();
 }
 
+// Phase timing (qp_set_phase_timing): while it is on, solves run in the host-driven form, one PCG iteration per
+// host check (no launch after convergence), with CUDA events on the solve's stream around each kernel group; the
+// durations are added up per phase once the solve's stream has been synchronised.
+std::atomic<int> g_phase_timing{0};
+std::mutex g_phase_mu;
+double g_phase_ms[QP_NPHASE] = {};
+int64_t g_phase_count[QP_NPHASE] = {};
+struct PendingPhase {
+  int phase;
+  cudaEvent_t a, b;
+};
+thread_local std::vector<PendingPhase> t_pending;
+
+template <typename Fn>
+void timed(int phase, cudaStream_t s, Fn fn) {
+  if (!g_phase_timing.load(std::memory_order_relaxed)) {
+    fn();
+    return;
+  }
+  PendingPhase pp{phase, nullptr, nullptr};
+  CK(cudaEventCreate(&pp.a));
+  CK(cudaEventCreate(&pp.b));
+  CK(cudaEventRecord(pp.a, s));
+  fn();
+  CK(cudaEventRecord(pp.b, s));
+  t_pending.push_back(pp);
+}
+
+// Adds the recorded phases of this thread's last solve (its stream synchronised) to the totals.
+void resolve_phases() {
+  if (t_pending.empty()) return;
+  std::lock_guard<std::mutex> lk(g_phase_mu);
+  for (auto& pp : t_pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, pp.a, pp.b) == cudaSuccess) {
+      g_phase_ms[pp.phase] += ms;
+      g_phase_count[pp.phase] += 1;
+    }
+    cudaEventDestroy(pp.a);
+    cudaEventDestroy(pp.b);
+  }
+  t_pending.clear();
+}
+
 void body_pcg(const Units& us, const Entry& en, int level, unsigned long long cond, cudaStream_t s) {
-  record_apply(us, en, level, EPI_DOT_HW, REFINE_NONE, cond, s);
-  launch_pcg_update(en.bd, us.max_rhs, level, cond, en.nblk, s);
-  launch_pcg_hupdate(en.bd, us.max_rhs, level, en.nblk, s);
+  const bool l32 = level == LEVEL_FP32;
+  timed(l32 ? QP_PHASE_APPLY32 : QP_PHASE_APPLY64, s,
+        [&] { record_apply(us, en, level, EPI_DOT_HW, REFINE_NONE, cond, s); });
+  timed(l32 ? QP_PHASE_UPDATE32 : QP_PHASE_UPDATE64, s,
+        [&] { launch_pcg_update(en.bd, us.max_rhs, level, cond, en.nblk, s); });
+  timed(l32 ? QP_PHASE_HUPDATE32 : QP_PHASE_HUPDATE64, s,
+        [&] { launch_pcg_hupdate(en.bd, us.max_rhs, level, en.nblk, s); });
   CK_LAUNCH();
 }
 
@@ -718,38 +737,47 @@ void run_direct(const Units& us, Entry& en, const Key& key, int nslots, cudaStre
     CK(cudaStreamSynchronize(s));
     return h;
   };
+  const bool timing = g_phase_timing.load(std::memory_order_relaxed) != 0;
   auto pcg_loop = [&](int level) {
-    int it = 0, chunk = 4;
+    int it = 0, chunk = timing ? 1 : 4;
     while (read_done(0) < nslots) {
       for (int i = 0; i < chunk; ++i) body_pcg(us, en, level, 0, s);
       it += chunk;
-      chunk = std::min(chunk * 2, 32);
+      if (!timing) chunk = std::min(chunk * 2, 32);
       if (it > key.maxit + 64) raise(QP_ERR_CUDA, "PCG loop exceeded its cap without the device flag");
     }
   };
   if (key.mode == QP_MODE_FP64) {
-    if (!key.warm) zero_solutions(us, s);
-    launch_level_reset(en.bd, 0, s);
-    if (key.warm) record_apply(us, en, LEVEL_FP64, EPI_NONE, REFINE_NONE, 0, s);
-    launch_pcg_init(en.bd, us.max_rhs, LEVEL_FP64, key.warm != 0, 0, en.nblk, s);
+    timed(QP_PHASE_OTHER, s, [&] {
+      if (!key.warm) zero_solutions(us, s);
+      launch_level_reset(en.bd, 0, s);
+    });
+    if (key.warm) timed(QP_PHASE_RESIDUAL64, s, [&] { record_apply(us, en, LEVEL_FP64, EPI_NONE, REFINE_NONE, 0, s); });
+    timed(QP_PHASE_INIT64, s, [&] { launch_pcg_init(en.bd, us.max_rhs, LEVEL_FP64, key.warm != 0, 0, en.nblk, s); });
     pcg_loop(LEVEL_FP64);
-    record_apply(us, en, LEVEL_FP64, EPI_RESIDUAL, REFINE_NONE, 0, s);
+    timed(QP_PHASE_RESIDUAL64, s, [&] { record_apply(us, en, LEVEL_FP64, EPI_RESIDUAL, REFINE_NONE, 0, s); });
   } else {
-    if (!key.warm) zero_solutions(us, s);
-    launch_level_reset(en.bd, 1, s);
-    record_apply(us, en, LEVEL_FP64, EPI_RESIDUAL, key.warm ? REFINE_ON : REFINE_ZERO_U, 0, s);
+    timed(QP_PHASE_OTHER, s, [&] {
+      if (!key.warm) zero_solutions(us, s);
+      launch_level_reset(en.bd, 1, s);
+    });
+    timed(QP_PHASE_RESIDUAL64, s, [&] {
+      record_apply(us, en, LEVEL_FP64, EPI_RESIDUAL, key.warm ? REFINE_ON : REFINE_ZERO_U, 0, s);
+    });
     for (int outer = 0; outer < 64; ++outer) {
       if (read_done(1) >= nslots) break;
-      launch_refine_prep(en.bd, en.nblk, s);
-      launch_level_reset(en.bd, 0, s);
-      launch_pcg_init(en.bd, us.max_rhs, LEVEL_FP32, false, 0, en.nblk, s);
+      timed(QP_PHASE_REFINE, s, [&] { launch_refine_prep(en.bd, en.nblk, s); });
+      timed(QP_PHASE_INIT32, s, [&] {
+        launch_level_reset(en.bd, 0, s);
+        launch_pcg_init(en.bd, us.max_rhs, LEVEL_FP32, false, 0, en.nblk, s);
+      });
       pcg_loop(LEVEL_FP32);
-      launch_refine_accum(en.bd, en.nblk, s);
-      record_apply(us, en, LEVEL_FP64, EPI_RESIDUAL, REFINE_ON, 0, s);
+      timed(QP_PHASE_REFINE, s, [&] { launch_refine_accum(en.bd, en.nblk, s); });
+      timed(QP_PHASE_RESIDUAL64, s, [&] { record_apply(us, en, LEVEL_FP64, EPI_RESIDUAL, REFINE_ON, 0, s); });
       CK_LAUNCH();
     }
   }
-  zero_mean_mode(us, s);
+  timed(QP_PHASE_OTHER, s, [&] { zero_mean_mode(us, s); });
 }
 
 // Builds (or finds) the entry for these units and key: device unit/chunk tables and the recorded graph.
@@ -880,7 +908,9 @@ void run_solve(Solver* sv, const Units& us, const Key& key, cudaStream_t s, Solv
   Entry& en = get_entry(sv, us, key, s);
   int nslots = 0;
   for (int r : us.nrhs) nslots += r;
-  if (en.pgrid > 0) {
+  if (g_phase_timing.load(std::memory_order_relaxed)) {
+    run_direct(us, en, key, nslots, s);   // the same kernels, one timed group at a time
+  } else if (en.pgrid > 0) {
     launch_persistent(en.bd, us.all_real, us.max_rhs, en.psk, en.psk ? &us.plans[0]->star_host : nullptr, key.mode,
                       key.warm != 0, sv->pbar, sv->perr, g_barrier_timeout.load(), en.pgrid, en.psmem, s);
     CK(cudaMemcpyAsync(sv->h_perr, sv->perr, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -892,7 +922,9 @@ void run_solve(Solver* sv, const Units& us, const Key& key, cudaStream_t s, Solv
   const size_t nu = us.plans.size();
   CK(cudaMemcpyAsync(sv->h_st, sv->st, nu * MAXR * sizeof(RhsSt), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  if (en.pgrid > 0 && *sv->h_perr != 0)
+  resolve_phases();
+  const bool ran_persistent = en.pgrid > 0 && !g_phase_timing.load(std::memory_order_relaxed);
+  if (ran_persistent && *sv->h_perr != 0)
     raise(QP_ERR_TIMEOUT, "persistent solve: a grid-barrier wait exceeded its limit");
   res = SolveResult();
   int max_it = 0, max_outer = 0, sum_inner_max = 0;
@@ -914,7 +946,7 @@ void run_solve(Solver* sv, const Units& us, const Key& key, cudaStream_t s, Solv
         max_outer = std::max(max_outer, x.outer);
       }
     }
-  if (en.exec) {
+  if (en.exec && !g_phase_timing.load(std::memory_order_relaxed)) {   // the graph ran: count its kernel nodes
     if (key.mode == QP_MODE_FP64) count_launch(en.fixed_nodes + en.body_nodes * std::max(1, max_it));
     else count_launch(en.fixed_nodes + en.outer_nodes * std::max(0, max_outer - 1) +
                       en.body_nodes * (sum_inner_max + max_outer));
@@ -1112,6 +1144,40 @@ qp_status qp_fft_set_schedule(qp_plan* p, int precision, int index) {
   if (p->backend != QP_BACKEND_FFT || !p->fft) raise(QP_ERR_UNSUPPORTED, "the plan has no FFT backend");
   if (precision != QP_FP64 && precision != QP_FP32) raise(QP_ERR_INVALID_ARG, "precision must be QP_FP64 or QP_FP32");
   fft_schedule_set(p->fft, precision == QP_FP64, index);
+  API_END
+}
+
+qp_status qp_set_phase_timing(int enabled) {
+  API_BEGIN
+  std::lock_guard<std::mutex> lk(g_phase_mu);
+  for (int i = 0; i < QP_NPHASE; ++i) {
+    g_phase_ms[i] = 0.0;
+    g_phase_count[i] = 0;
+  }
+  g_phase_timing.store(enabled ? 1 : 0);
+  API_END
+}
+
+qp_status qp_phase_times(double* ms, int64_t* launches, int count) {
+  API_BEGIN
+  if (count < 0) raise(QP_ERR_INVALID_ARG, "count must be >= 0");
+  std::lock_guard<std::mutex> lk(g_phase_mu);
+  for (int i = 0; i < count; ++i) {
+    if (ms) ms[i] = i < QP_NPHASE ? g_phase_ms[i] : 0.0;
+    if (launches) launches[i] = i < QP_NPHASE ? g_phase_count[i] : 0;
+  }
+  API_END
+}
+
+qp_status qp_memory_pool_stats(int64_t* reserved_bytes, int64_t* used_bytes, uint64_t* allocations) {
+  API_BEGIN
+  pool_stats(reserved_bytes, used_bytes, allocations);
+  API_END
+}
+
+qp_status qp_set_memory_cache(int64_t bytes) {
+  API_BEGIN
+  set_cache_bytes(bytes);
   API_END
 }
 

@@ -79,6 +79,37 @@ inline int64_t chunk_modes(int64_t D) {
   return std::max<int64_t>(2 * BLOCK, std::min<int64_t>(65536, (D / (SMS * 8) + BLOCK - 1) / BLOCK * BLOCK));
 }
 
+// Is the mean tap A~_0 of a coefficient positive definite? vals: its components as (re, im) pairs in the kind's
+// layout (scalar: a; diagonal: a_11..a_dd; symmetric: the upper triangle row by row); the real parts form the d x d
+// matrix, tested by a Cholesky factorisation.
+inline bool mean_tap_spd(int kind, int d, const double* vals) {
+  double M[MAXD][MAXD] = {};
+  for (int a = 0; a < d; ++a)
+    for (int b = 0; b < d; ++b) {
+      int comp = -1;
+      if (kind == QP_COEF_SCALAR) comp = (a == b) ? 0 : -1;
+      else if (kind == QP_COEF_DIAG) comp = (a == b) ? a : -1;
+      else {
+        const int lo = a < b ? a : b, hi = a < b ? b : a;
+        comp = lo * d - lo * (lo - 1) / 2 + (hi - lo);
+      }
+      M[a][b] = comp >= 0 ? vals[2 * comp] : 0.0;
+    }
+  double L[MAXD][MAXD] = {};
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j <= i; ++j) {
+      double s = M[i][j];
+      for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
+      if (i == j) {
+        if (!(s > 0.0)) return false;
+        L[i][i] = __builtin_sqrt(s);
+      } else {
+        L[i][j] = s / L[j][j];
+      }
+    }
+  return true;
+}
+
 inline FastDiv make_fastdiv(uint32_t d) {
   uint32_t L = 0;
   while ((1ull << L) < d) ++L;
@@ -263,6 +294,8 @@ void launch_refine_accum(const BatchDev& b, int nblk, cudaStream_t s);
 void* dev_alloc(size_t bytes, cudaStream_t s);
 void dev_free(void* p);
 void dev_trim();
+void set_cache_bytes(int64_t bytes);   // < 0: the default (an eighth of the device memory, at least 1 GiB)
+void pool_stats(int64_t* reserved, int64_t* used, uint64_t* allocs);
 void* pinned_alloc(size_t bytes);
 void pinned_free(void* p, size_t bytes);
 

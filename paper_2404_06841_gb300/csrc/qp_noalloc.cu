@@ -122,6 +122,7 @@ void build_host(int d, int n, const double* P, const int* N, const qp_coeff* c, 
     for (int j = 0; j < n; ++j) {
       m[j] = c->tap_k[t * n + j];
       if (2 * std::abs(m[j]) >= N[j]) raise(QP_ERR_INVALID_ARG, "tap mode component |m_j| must be < N_j/2");
+      if (std::abs(m[j]) > 127) raise(QP_ERR_INVALID_ARG, "tap mode component |m_j| must be <= 127");
     }
     int id = -1;
     for (int s = 0; s < G && id < 0; ++s) {
@@ -162,6 +163,8 @@ void build_host(int d, int n, const double* P, const int* N, const qp_coeff* c, 
     }
   }
   if (mean < 0) raise(QP_ERR_NOT_ELLIPTIC, "the coefficient has no mean (m = 0) tap");
+  if (!mean_tap_spd(c->kind, d, val[mean]))
+    raise(QP_ERR_NOT_ELLIPTIC, "the coefficient's mean A~_0 is not positive definite");
   int order[MAXT];
   int no = 0;
   order[no++] = mean;
@@ -300,38 +303,52 @@ extern "C" qp_status qp_pcg_solve_taps_static(int d, int n, const double* P, con
     bd.maxit = opts->maxit;
     bd.max_outer = 1;
 
-    // warm start from U: w = Q U, r = F - w, then Algorithm 2 with the host polling the done count
+    // warm start from U: w = Q U, r = F - w, then Algorithm 2 with the host polling the done count, then the
+    // FP64 true residual. Like qp_pcg_solve, a right-hand side whose recursive residual met the tolerance while
+    // its true residual did not (the two drift apart at tight tolerances) is solved again from its current U, at
+    // most twice; iterations add up over the attempts.
     const bool realc = ht.real;
     // FP64 applies of a single star-1 unit take the kernel-parameter form only with stored weights, which this
     // entry point has no room for: its kernels read the plan's star data from shared memory
     const StarParams* st1 = nullptr;
-    launch_level_reset(bd, 0, s);
-    launch_apply(bd, realc, G * nc, nrhs, LEVEL_FP64, EPI_NONE, false, 0, nchunks, st1, ht.pd.kind, s);
-    launch_pcg_init(bd, nrhs, LEVEL_FP64, true, 0, nchunks, s);
-    CK_LAUNCH();
-    int done = 0, launched = 0, burst = 4;
-    for (;;) {
-      CK(cudaMemcpyAsync(&done, ndone, sizeof(int), cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
-      if (done >= nrhs) break;
-      if (launched > opts->maxit + 64) raise(QP_ERR_CUDA, "PCG loop exceeded its cap without the device count");
-      for (int i = 0; i < burst; ++i) {
-        launch_apply(bd, realc, G * nc, nrhs, LEVEL_FP64, EPI_DOT_HW, false, 0, nchunks, st1, ht.pd.kind, s);
-        launch_pcg_update(bd, nrhs, LEVEL_FP64, 0, nchunks, s);
-        launch_pcg_hupdate(bd, nrhs, LEVEL_FP64, nchunks, s);
-      }
+    RhsSt hst[MAXR];
+    int iters_before[MAXR] = {0, 0, 0, 0};
+    for (int attempt = 0; attempt < 3; ++attempt) {
+      launch_level_reset(bd, 0, s);
+      launch_apply(bd, realc, G * nc, nrhs, LEVEL_FP64, EPI_NONE, false, 0, nchunks, st1, ht.pd.kind, s);
+      launch_pcg_init(bd, nrhs, LEVEL_FP64, true, 0, nchunks, s);
       CK_LAUNCH();
-      launched += burst;
-      burst = std::min(burst * 2, 32);
+      int done = 0, launched = 0, burst = 4;
+      for (;;) {
+        CK(cudaMemcpyAsync(&done, ndone, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (done >= nrhs) break;
+        if (launched > opts->maxit + 64) raise(QP_ERR_CUDA, "PCG loop exceeded its cap without the device count");
+        for (int i = 0; i < burst; ++i) {
+          launch_apply(bd, realc, G * nc, nrhs, LEVEL_FP64, EPI_DOT_HW, false, 0, nchunks, st1, ht.pd.kind, s);
+          launch_pcg_update(bd, nrhs, LEVEL_FP64, 0, nchunks, s);
+          launch_pcg_hupdate(bd, nrhs, LEVEL_FP64, nchunks, s);
+        }
+        CK_LAUNCH();
+        launched += burst;
+        burst = std::min(burst * 2, 32);
+      }
+      launch_apply(bd, realc, G * nc, nrhs, LEVEL_FP64, EPI_RESIDUAL, false, 0, nchunks, st1, ht.pd.kind, s);
+      CK_LAUNCH();
+      CK(cudaMemcpyAsync(hst, st, MAXR * sizeof(RhsSt), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      bool again = false;
+      for (int k = 0; k < nrhs; ++k) {
+        hst[k].iters += iters_before[k];
+        iters_before[k] = hst[k].iters;
+        const double rel = hst[k].of2 > 0.0 ? std::sqrt(hst[k].orr / hst[k].of2) : 0.0;
+        if (hst[k].status == QP_OK && rel > opts->tol) again = true;
+      }
+      if (!again) break;
     }
-    // FP64 true residual, then U(k = 0) = 0
-    launch_apply(bd, realc, G * nc, nrhs, LEVEL_FP64, EPI_RESIDUAL, false, 0, nchunks, st1, ht.pd.kind, s);
-    CK_LAUNCH();
+    // U(k = 0) = 0
     for (int k = 0; k < nrhs; ++k)
       CK(cudaMemsetAsync(static_cast<double2*>(U) + (size_t)k * D, 0, sizeof(double2), s));
-    RhsSt hst[MAXR];
-    CK(cudaMemcpyAsync(hst, st, MAXR * sizeof(RhsSt), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
     qp_status worst = QP_OK;
     for (int k = 0; k < nrhs; ++k) {
       const double rel = hst[k].of2 > 0.0 ? std::sqrt(hst[k].orr / hst[k].of2) : 0.0;

@@ -83,3 +83,34 @@ def test_sizes_beyond_the_limits_are_rejected(qp):
     with pytest.raises(qp.QPError) as ei:   # more right-hand sides than QP_MAX_RHS
         qp.qp_plan_create(1, 2, [[1.0, W.SQRT2]], [8, 8], c, max_rhs=5)
     assert ei.value.status == qp.QP_ERR_INVALID_ARG
+
+
+def test_tap_modes_beyond_127_rejected_by_both_entry_points(qp):
+    """Tap modes are held in 8 bits on the device: |m_j| = 130 on an axis of 512 modes (within |m_j| < N_j / 2)
+    is rejected with QP_ERR_INVALID_ARG by the plan and by the allocation-free solve, before any device work."""
+    k = np.array([[0, 0], [130, 0], [-130, 0]], np.int32)
+    v = np.array([[3.0], [0.25], [0.25]], complex)
+    c = W.Coefficient("scalar", k, v)
+    with pytest.raises(qp.QPError) as ei:
+        qp.qp_plan_create(1, 2, [[1.0, W.SQRT2]], [512, 4], c)
+    assert ei.value.status == qp.QP_ERR_INVALID_ARG and "127" in str(ei.value)
+    F = torch.zeros((1, 512 * 4), dtype=torch.complex128, device="cuda")
+    with pytest.raises(qp.QPError) as ei:
+        qp.qp_pcg_solve_taps_static(1, 2, [[1.0, W.SQRT2]], [512, 4], c, F, F.clone())
+    assert ei.value.status == qp.QP_ERR_INVALID_ARG and "127" in str(ei.value)
+
+
+def test_indefinite_mean_tap_rejected_by_both_entry_points(qp):
+    """A diagonal 2 x 2 coefficient whose mean tap has a negative entry (not elliptic): QP_ERR_NOT_ELLIPTIC from the
+    plan and from the allocation-free solve alike."""
+    k = np.array([[0, 0, 0, 0], [1, 0, 0, 0], [-1, 0, 0, 0]], np.int32)
+    v = np.array([[3.0, -1.0], [0.25, 0.25], [0.25, 0.25]], complex)
+    c = W.Coefficient("diag", k, v)
+    P = [[1.0, W.SQRT2, 0, 0], [0, 0, 1.0, W.SQRT3]]
+    with pytest.raises(qp.QPError) as ei:
+        qp.qp_plan_create(2, 4, P, [4, 4, 4, 4], c)
+    assert ei.value.status == qp.QP_ERR_NOT_ELLIPTIC
+    F = torch.zeros((2, 256), dtype=torch.complex128, device="cuda")
+    with pytest.raises(qp.QPError) as ei:
+        qp.qp_pcg_solve_taps_static(2, 4, P, [4, 4, 4, 4], c, F, F.clone())
+    assert ei.value.status == qp.QP_ERR_NOT_ELLIPTIC
