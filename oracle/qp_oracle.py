@@ -20,7 +20,9 @@ What it computes, each step written out from the paper, in double precision, slo
   eq. preconditioner (Sec. 4.3);
 * C-PCG, Algorithm 2;
 * the corrector right-hand side (Sec. 5.2 eq. corrector; App. D, f_1 = d alpha / d x_1) and the homogenized
-  coefficient of eq. homcoefficient, as a torus (grid) average.
+  coefficient of eq. homcoefficient, as a torus (grid) average;
+* the Nyquist-free variant of the scheme (not in the paper: the definition behind the library's half-spectrum
+  storage): the same Galerkin scheme restricted to the modes with no k_j = -N_j/2, a set closed under k -> -k.
 
 Readings of places where the paper is silent or garbled (each is also listed in the design notes):
 Nyquist modes k_j = -N/2 are kept with lambda = P k literally; k = 0 is excluded (U_0 = 0, row 0 of Q h is 0);
@@ -454,6 +456,52 @@ def homogenized(inst, tol: float | None = None, precond: str = "jacobi", maxit: 
     for j in range(inst.d):
         F = corrector_rhs(op.P, op.N, op.Ahat, j)
         U, info = pcg(op, F, M, tol, maxit)
+        Us.append(U)
+        infos.append(info)
+    Ac = homogenized_from_correctors(op.P, op.N, op.Ahat, Us)
+    return Ac.real.copy(), Us, infos, Ac
+
+
+# ------------------------------------------------------------------------------------ Nyquist-free variant
+
+def nyquist_free_mask(N) -> np.ndarray:
+    """True on the modes of K_N^n with no Nyquist component (k_j = -N_j/2 for an even N_j), shape (*N).
+
+    The remaining set K'_N = {k : |k_j| < N_j/2} is closed under k -> -k, which K_N^n is not for even N_j
+    (Sec. 2.3 gives K_N^n = {-N/2 <= k_j < N/2}). On K'_N the stiffness matrix of a real coefficient satisfies
+    Q(-k, -k') = conj(Q(k, k')) (lambda(-k) = -lambda(k), A~_{-m} = conj(A~_m)), so a real right-hand side has a
+    solution with U(-k) = conj(U(k)): the property a half-spectrum (real-arithmetic) storage relies on."""
+    N = tuple(int(x) for x in N)
+    kg = k_grids(N)
+    keep = np.ones(N, dtype=bool)
+    for j, Nj in enumerate(N):
+        if Nj % 2 == 0:
+            keep &= kg[j] != -(Nj // 2)
+    return keep
+
+
+def homogenized_nyquist_free(inst, tol: float | None = None, precond: str = "jacobi", maxit: int = 10000):
+    """The homogenization of `homogenized` on the Nyquist-free trial and test space: the Galerkin restriction
+    of the discrete scheme (Sec. 3.1.1, eq. n-discrete_equation; App. D) to the modes K'_N of nyquist_free_mask,
+    i.e. Q' = Q restricted to K'_N x K'_N (the same lambda = P k, the same coefficient modes, the convolution still
+    wrapping modulo N), F' = F on K'_N, then Algorithm 2 and eq. homcoefficient summed over K'_N. For odd N_j it is
+    `homogenized` itself. Returns (A* real d x d, [U_j], [info_j], Astar_complex)."""
+    op = Operator(inst)
+    if tol is None:
+        tol = inst.tol
+    keep = nyquist_free_mask(op.N)
+    if precond == "jacobi":
+        M = jacobi_inverse(op.P, op.N, op.Ahat) * keep
+    else:
+        raise ValueError(precond)
+
+    def restricted(h):
+        return keep * op(keep * h)
+
+    Us, infos = [], []
+    for j in range(inst.d):
+        F = keep * corrector_rhs(op.P, op.N, op.Ahat, j)
+        U, info = pcg(restricted, F, M, tol, maxit)
         Us.append(U)
         infos.append(info)
     Ac = homogenized_from_correctors(op.P, op.N, op.Ahat, Us)

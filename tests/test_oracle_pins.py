@@ -399,3 +399,64 @@ def test_pointwise_apply_matches_vectorised_convolution():
     pts = [tuple(int(rng.integers(0, Nj)) for Nj in inst.N) for _ in range(20)] + [(0, 0, 0), (5, 3, 7), (3, 2, 4)]
     wp = O.apply_taps_at(inst.P, inst.N, inst.coeff.taps_k, inst.coeff.taps_val, "sym", h, pts)
     assert np.abs(wp - np.array([w[p] for p in pts])).max() <= 1e-12 * np.abs(w).max()
+
+
+# ------------------------------------------------------------------------------ Nyquist-free variant
+
+@pytest.mark.parametrize("N", [(4, 6), (3, 4, 5), (2, 2, 3)])
+def test_nyquist_free_mask_is_the_symmetric_index_set(N):
+    keep = O.nyquist_free_mask(N)
+    assert keep.sum() == np.prod([Nj - (1 - Nj % 2) for Nj in N])
+    # closed under k -> -k: storage index i -> (-i) mod N on every axis
+    flip = np.roll(np.flip(keep, axis=tuple(range(len(N)))), 1, axis=tuple(range(len(N))))
+    assert np.array_equal(keep, flip)
+    kg = O.k_grids(N)
+    assert np.all(np.abs(kg[:, keep]) < np.asarray(N)[:, None] / 2.0)
+
+
+def test_nyquist_free_is_the_full_scheme_on_odd_grids():
+    inst = W.random_instance(2, 3, (5, 3, 7), "sym", "grid", seed=31, nonlinear=True)
+    A1, _, _, Ac1 = O.homogenized(inst, tol=1e-13)
+    A2, _, _, Ac2 = O.homogenized_nyquist_free(inst, tol=1e-13)
+    assert np.abs(Ac1 - Ac2).max() <= 1e-14 * np.abs(A1).max()
+
+
+@pytest.mark.parametrize("d,n,N,kind", [(1, 2, (6, 4), "scalar"), (2, 3, (4, 6, 4), "sym"), (2, 2, (6, 6), "diag")])
+def test_nyquist_free_solution_against_dense_restriction(d, n, N, kind):
+    """Q' = the principal submatrix of the dense Q (Alg. 1) on K'_N, solved directly, equals the oracle's
+    restricted PCG; the solution is conjugate-symmetric, U(-k) = conj(U(k)), and a* is real. The full scheme on
+    the same grid breaks both at the Nyquist modes (full-support grid coefficient), so the pin sees the
+    restriction."""
+    inst = W.random_instance(d, n, N, kind, "grid", seed=7 + d, nonlinear=True)
+    Ahat = O.coefficient_modes(inst)
+    Q = O.dense_Q(inst.P, N, Ahat)
+    keep = O.nyquist_free_mask(N).reshape(-1)
+    idx = np.nonzero(keep)[0][1:]                      # K'_N without k = 0
+    A, Us, infos, Ac = O.homogenized_nyquist_free(inst, tol=1e-14)
+    axes = tuple(range(len(N)))
+    for j in range(d):
+        F = O.corrector_rhs(inst.P, N, Ahat, j).reshape(-1)
+        U_direct = np.zeros(Q.shape[0], complex)
+        U_direct[idx] = np.linalg.solve(Q[np.ix_(idx, idx)], F[idx])
+        U = Us[j].reshape(-1)
+        assert np.abs(U - U_direct).max() <= 1e-11 * np.abs(U_direct).max()
+        Um = np.roll(np.flip(Us[j], axis=axes), 1, axis=axes)          # U(-k) at index k
+        assert np.abs(Um - np.conj(Us[j])).max() <= 1e-11 * np.abs(U_direct).max()
+    assert np.abs(Ac.imag).max() <= 1e-13 * np.abs(A).max()
+    _, Us_full, _, Ac_full = O.homogenized(inst, tol=1e-14)
+    Um = np.roll(np.flip(Us_full[0], axis=axes), 1, axis=axes)
+    assert np.abs(Um - np.conj(Us_full[0])).max() > 1e-8 * np.abs(Us_full[0]).max()
+
+
+@pytest.mark.parametrize("kind,seed", [("scalar", 2), ("sym", 4)])
+def test_nyquist_free_variational_bounds(kind, seed):
+    """The restricted trial space is a subspace of the full one, so the restricted a* (minimum energy over it)
+    lies between the full scheme's a* and the grid mean of A (the Voigt bound): A*_full <= A*' <= <A>."""
+    inst = W.random_instance(2, 3, (6, 4, 6), kind, "grid", seed=seed, nonlinear=True)
+    A_full, *_ = O.homogenized(inst, tol=1e-14)
+    A_nf, *_ = O.homogenized_nyquist_free(inst, tol=1e-14)
+    Agrid = O.coefficient_grid(inst)
+    voigt = np.moveaxis(Agrid.reshape(2, 2, -1), -1, 0).mean(axis=0)
+    assert np.linalg.eigvalsh(A_nf - A_full).min() >= -1e-12
+    assert np.linalg.eigvalsh(voigt - A_nf).min() >= -1e-12
+    assert np.abs(A_nf - A_full).max() > 1e-10          # the Nyquist modes carry energy here
