@@ -53,6 +53,7 @@ enum { QP_FP64 = 0, QP_FP32 = 1 };
 enum { QP_PRECOND_JACOBI = 0, QP_PRECOND_FROBENIUS = 1 };
 enum { QP_MODE_FP64 = 0, QP_MODE_FP32_REFINE = 1 };
 enum { QP_EXEC_AUTO = 0, QP_EXEC_DIRECT = 1, QP_EXEC_GRAPH = 2, QP_EXEC_PERSISTENT = 3 };
+enum { QP_SPECTRUM_FULL = 0, QP_SPECTRUM_HALF = 1 };
 enum { QP_MAX_N_AXES = 6, QP_MAX_D = 3, QP_MAX_RHS = 4, QP_MAX_TAPS = 256 };
 
 typedef struct qp_plan qp_plan;     /* opaque; owns every internal device buffer */
@@ -89,6 +90,19 @@ typedef struct {
                        convergence (for profilers and callers that cannot launch graphs); QP_EXEC_AUTO (0,
                        default): PERSISTENT where it applies and every chunk of modes gets its own resident block,
                        else GRAPH. A persistent solve whose barrier wait exceeds its limit returns QP_ERR_TIMEOUT. */
+  int spectrum;     /* QP_SPECTRUM_FULL (0, default): the scheme on K_N^n as written (Sec. 2.3, 3.1.1), complex vectors
+                       of D = N_1 .. N_n entries. QP_SPECTRUM_HALF (not in the paper; opt-in): the scheme restricted to
+                       the Nyquist-free modes K'_N = {k : |k_j| < N_j / 2} (for an even N_j the mode k_j = -N_j/2 is
+                       dropped; for odd N_j nothing is), a set closed under k -> -k on which the solution of a real
+                       problem satisfies U(-k) = conj(U(k)); vectors then store only the modes with k_n >= 0:
+                       D_h = N_1 .. N_{n-1} x ceil(N_n / 2) entries, the last axis holding k_n = 0 .. ceil(N_n/2) - 1
+                       at index k_n, the others in the usual storage order (index k_j mod N_j). A mode with k_n < 0
+                       is the conjugate of its mirror -k; entries at a dropped mode (some k_j = -N_j/2, j < n) are
+                       ignored on input and 0 on output; the k_n = 0 plane holds both k and -k, which a real
+                       problem keeps conjugate (inputs should). About half the bytes per PCG iteration; the discrete
+                       result differs from the full scheme's by the Nyquist modes' share (a* is larger or equal:
+                       a smaller trial space). Taps backend with a tap coefficient, Jacobi preconditioner;
+                       solves run as CUDA graphs (not persistent). qp_plan_query reports the stored length. */
 } qp_options;
 
 typedef struct {
@@ -120,6 +134,8 @@ typedef struct {
                             stencil of the taps backend) */
   int stored_weights;    /* 1: the plan stores the FP64 stiffness entries Q_ij per (tap, mode) (Sec. 4.2's
                             compressed format Q~), which single-plan FP64 applies read instead of forming */
+  int spectrum;          /* QP_SPECTRUM_FULL or QP_SPECTRUM_HALF */
+  int64_t stored;        /* entries of each vector the plan's calls take: D, or D_h for QP_SPECTRUM_HALF */
 } qp_plan_info;
 
 /* Creates a plan: validates d (1..3), n (d..6), P (host double d x n, row-major, Sec. 2.1 projection

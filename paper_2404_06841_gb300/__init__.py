@@ -28,6 +28,7 @@ QP_FP64, QP_FP32 = 0, 1
 QP_PRECOND_JACOBI, QP_PRECOND_FROBENIUS = 0, 1
 QP_MODE_FP64, QP_MODE_FP32_REFINE = 0, 1
 QP_EXEC_AUTO, QP_EXEC_DIRECT, QP_EXEC_GRAPH, QP_EXEC_PERSISTENT = 0, 1, 2, 3
+QP_SPECTRUM_FULL, QP_SPECTRUM_HALF = 0, 1
 QP_PHASE_APPLY32, QP_PHASE_UPDATE32, QP_PHASE_HUPDATE32, QP_PHASE_INIT32, QP_PHASE_REFINE = 0, 1, 2, 3, 4
 QP_PHASE_APPLY64, QP_PHASE_UPDATE64, QP_PHASE_HUPDATE64, QP_PHASE_INIT64, QP_PHASE_RESIDUAL64 = 5, 6, 7, 8, 9
 QP_PHASE_OTHER, QP_NPHASE = 10, 11
@@ -50,7 +51,8 @@ class qp_coeff(C.Structure):
 
 
 class qp_options(C.Structure):
-    _fields_ = [("backend", C.c_int), ("max_rhs", C.c_int), ("precisions", C.c_int), ("exec", C.c_int)]
+    _fields_ = [("backend", C.c_int), ("max_rhs", C.c_int), ("precisions", C.c_int), ("exec", C.c_int),
+                ("spectrum", C.c_int)]
 
 
 class qp_solve_opts(C.Structure):
@@ -70,7 +72,7 @@ class qp_solve_info(C.Structure):
 class qp_plan_info(C.Structure):
     _fields_ = [("D", C.c_int64), ("backend", C.c_int), ("ntaps", C.c_int), ("max_rhs", C.c_int),
                 ("min_abs_lambda", C.c_double), ("device_bytes", C.c_int64), ("star", C.c_int),
-                ("stored_weights", C.c_int)]
+                ("stored_weights", C.c_int), ("spectrum", C.c_int), ("stored", C.c_int64)]
 
 
 class QPError(RuntimeError):

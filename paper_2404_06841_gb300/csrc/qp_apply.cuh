@@ -202,11 +202,11 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 3) k_apply(BatchDe
 }
 
 // Batch apply of a single star-1 unit (even last axis): the stencil data as a kernel parameter. The FP32 star
-// stencil waits on L2 latency of its neighbour reads: four blocks per SM (64 registers) hide it best on GB300
-// (cfg4: 435 us at four blocks, 470 at three, 474 at five; the fixed-geometry variant, spill-free at three blocks,
-// took the cfg4 solve to 41.7 ms against 37.7 at four).
+// stencil waits on the L2 latency of its neighbour reads: the run-time-geometry kernels run four blocks per SM (64
+// registers); the fixed-geometry ones, whose packed stencil with the chunk loop and epilogue spilled at 64 registers,
+// two (up to 128 registers).
 template <typename T, int EPI, bool REALC, int NR, int SK, int NAX = 0, int DC = 0>
-__global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 4)
+__global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : (NAX != 0 ? 2 : 4))
     k_apply_star(BatchDev b, int level, int refine, unsigned long long cond, const __grid_constant__ StarParams st) {
   apply_units<T, EPI, REALC, NR, SK, NAX, DC>(b, level, refine, cond, st);
 }
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 3) k_apply_plain(c
 // Plain apply of a star-1 plan with an even last axis: the stencil data as a kernel parameter; one run of two
 // modes per thread.
 template <typename T, bool REALC, int NR, int SK, int NAX = 0, int DC = 0>
-__global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 4)
+__global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : (NAX != 0 ? 2 : 4))
     k_apply_plain_star(const __grid_constant__ StarParams st, int D, int nrhs, const cplx<T>* h, cplx<T>* w) {
   const int e0 = (blockIdx.x * BLOCK + threadIdx.x) * 2;
   if (e0 >= D) return;

@@ -138,6 +138,13 @@ struct alignas(16) StarParams {
   int wreal, pad_;              // 1: w64 holds real weights (8 bytes each; real tap values), else complex (16 bytes)
   const void* w64;              // the plan's stored FP64 weights (see star_slots), or null
   const void* pad_ptr_;
+  // FP32 form of the taps as Hermitian pairs (the tap -e_j of a real coefficient holds the conjugate of the tap
+  // +e_j): per axis j and component a < d of the lambda products, the tap +e_j's coefficient (a scalar coefficient
+  // repeats it for every a) and that coefficient times P_aj; the mean tap's (real) coefficient per a
+  float2 hc32[MAXN][MAXD];
+  float2 hcp32[MAXN][MAXD];
+  float c0r32[MAXD];
+  int pad2_;
 };
 static_assert(sizeof(StarParams) % 16 == 0, "StarParams is uploaded and passed as 16-byte words");
 
@@ -191,6 +198,15 @@ inline void make_star(PlanDev& pd, const double2* c64, const float2* c32, StarPa
     sp.c064[q] = c64[q];
     sp.c032[q] = c32[q];
   }
+  for (int a = 0; a < pd.d; ++a) {
+    const int q = pd.kind == QP_COEF_DIAG ? a : 0;
+    sp.c0r32[a] = (float)c64[q].x;
+    for (int j = 0; j < pd.n; ++j) {
+      const double2 c = sp.c64[j][0][q];
+      sp.hc32[j][a] = make_float2((float)c.x, (float)c.y);
+      sp.hcp32[j][a] = make_float2((float)(c.x * pd.P[a][j]), (float)(c.y * pd.P[a][j]));
+    }
+  }
   for (int j = 0; j < MAXN; ++j) {
     sp.N[j] = pd.N[j];
     sp.stride[j] = pd.stride[j];
@@ -236,7 +252,7 @@ struct RhsSt {
   double of2, orr, scale, prev_rel;       // refinement outer level (FP64 true residual)
   double inv_scale, pad0;                 // ||F - Q U|| of the last outer step (1 / scale)
   int iters, done, status, inner_total;
-  int outer, odone, ostatus, pad1;
+  int outer, odone, ostatus, upend;       // upend: converged in this iteration, its U += alpha h still to come
 };
 
 struct BatchDev {

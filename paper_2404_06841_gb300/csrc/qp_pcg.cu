@@ -2,14 +2,15 @@
 // iterative-refinement steps around it.
 //
 // Per iteration: the stiffness apply (qp_taps.cu or the FFT passes) writes w = Q h and reduces (h, w); then
-//   pcg_update:  alpha = (r, z) / (h, Q h), U += alpha h, r -= alpha Q h, reduce (r, z') with z' = M r and
-//                ||r||^2; beta = (r', z') / (r, z); convergence ||r|| <= tol ||F||;
-//   pcg_hupdate: h = M r + beta h.
+//   pcg_update:  alpha = (r, z) / (h, Q h), r -= alpha Q h, reduce (r, z') with z' = M r and ||r||^2;
+//                beta = (r', z') / (r, z); convergence ||r|| <= tol ||F||;
+//   pcg_hupdate: U += alpha h and h = M r + beta h in one pass over h (h is read once per iteration for both;
+//                a right-hand side that converged in this iteration still gets its last U update).
 // z = M r is recomputed where needed instead of stored (the preconditioner is diagonal). Dot products are
 // accumulated in FP64 above the warp level whatever the vector precision (FP32 vectors: products and the
 // 32-lane warp tree in FP32, every sum above it in FP64). The update kernel's last block sets the CUDA-graph
 // conditional that keeps the iteration loop running while some right-hand side is not done.
-#include "qp_device.cuh"
+#include "qp_vec.cuh"
 
 namespace qp {
 
@@ -81,29 +82,7 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_init(BatchDev b, int level, int w
 #pragma unroll
     for (int q = 0; q < 3 * NR; ++q) vt[q] = T(0);
     const int base = (c - un.chunk0) * un.chunk, end = min(base + un.chunk, D);
-    for (int e = base + threadIdx.x; e < end; e += BLOCK) {
-      const T m = M[e];
-#pragma unroll
-      for (int k = 0; k < NR; ++k) {
-        if (k < nrhs) {
-          const size_t o = (size_t)k * D + e;
-          cplx<T> f = F[o];
-          if (e == 0 || zero_rhs[k]) f = mk<T>(0, 0);
-          cplx<T> rv = f;
-          if (warm && e != 0) {
-            const cplx<T> wv = w[o];
-            rv = mk<T>(f.x - wv.x, f.y - wv.y);
-          }
-          r[o] = rv;
-          h[o] = mk<T>(m * rv.x, m * rv.y);
-          if (level == LEVEL_FP32) U[o] = mk<T>(0, 0);
-          const T rr = fma(rv.x, rv.x, rv.y * rv.y);
-          vt[3 * k] = fma(f.x, f.x, fma(f.y, f.y, vt[3 * k]));
-          vt[3 * k + 1] = fma(m, rr, vt[3 * k + 1]);
-          vt[3 * k + 2] += rr;
-        }
-      }
-    }
+    vec_init<T, NR>(base, end, D, nrhs, warm != 0, level == LEVEL_FP32, zero_rhs, F, U, r, h, w, M, vt);
     block_reduce_mixed<T, 3 * NR>(vt, v);
     if (!chunk_arrive<3 * NR>(b, c, u, v)) continue;
     unit_sums<3 * NR>(b, un, v);
@@ -117,6 +96,7 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_init(BatchDev b, int level, int w
         x.rr = rr;
         x.iters = 0;
         x.status = QP_OK;
+        x.upend = 0;
         x.done = (f2 == 0.0 || rr <= b.tol2 * f2) ? 1 : 0;
         if (!isfinite(rr)) {
           x.done = 1;
@@ -136,7 +116,8 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_init(BatchDev b, int level, int w
   }
 }
 
-// alpha step, residual update, and the reductions for beta and the convergence test.
+// alpha step on the residual, and the reductions for beta and the convergence test (U is updated by
+// k_pcg_hupdate, which reads h anyway).
 template <typename T, int NR>
 __global__ void __launch_bounds__(BLOCK) k_pcg_update(BatchDev b, int level, unsigned long long cond) {
   for (int c = blockIdx.x; c < b.nchunks; c += gridDim.x) {
@@ -154,9 +135,7 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_update(BatchDev b, int level, uns
       active |= !done[k];
     }
     if (!active) continue;
-    cplx<T>* U = vU<T>(un);
     cplx<T>* r = vR<T>(un);
-    const cplx<T>* h = vH<T>(un);
     const cplx<T>* w = vW<T>(un);
     const T* M = vM<T>(un);
     T vt[2 * NR];
@@ -164,27 +143,7 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_update(BatchDev b, int level, uns
 #pragma unroll
     for (int q = 0; q < 2 * NR; ++q) vt[q] = T(0);
     const int base = (c - un.chunk0) * un.chunk, end = min(base + un.chunk, D);
-    for (int e = base + threadIdx.x; e < end; e += BLOCK) {
-      const T m = M[e];
-#pragma unroll
-      for (int k = 0; k < NR; ++k) {
-        if (k < nrhs && !done[k]) {
-          const size_t o = (size_t)k * D + e;
-          const T al = alpha[k];
-          const cplx<T> hv = h[o], wv = w[o];
-          cplx<T> uv = U[o], rv = r[o];
-          uv.x = fma(al, hv.x, uv.x);
-          uv.y = fma(al, hv.y, uv.y);
-          rv.x = fma(-al, wv.x, rv.x);
-          rv.y = fma(-al, wv.y, rv.y);
-          U[o] = uv;
-          r[o] = rv;
-          const T rr = fma(rv.x, rv.x, rv.y * rv.y);
-          vt[2 * k] = fma(m, rr, vt[2 * k]);
-          vt[2 * k + 1] += rr;
-        }
-      }
-    }
+    vec_update<T, NR>(base, end, D, nrhs, done, alpha, r, w, M, vt);
     block_reduce_mixed<T, 2 * NR>(vt, v);
     if (!chunk_arrive<2 * NR>(b, c, u, v)) continue;
     unit_sums<2 * NR>(b, un, v);
@@ -208,7 +167,10 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_update(BatchDev b, int level, uns
         }
         x.beta = rz / x.rz;
         x.rz = rz;
-        if (dn) x.done = 1;
+        if (dn) {
+          x.done = 1;
+          x.upend = 1;   // its last U += alpha h comes in this iteration's k_pcg_hupdate
+        }
         nd += dn;
       }
       b.ucount[u] = 0;
@@ -217,6 +179,9 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_update(BatchDev b, int level, uns
   }
 }
 
+// U += alpha h for the right-hand sides active in this iteration (those that converged in it included), then
+// h = M r + beta h for those still running. The last block of a unit clears the pending U updates of its
+// converged right-hand sides.
 template <typename T, int NR>
 __global__ void __launch_bounds__(BLOCK) k_pcg_hupdate(BatchDev b, int level) {
   for (int c = blockIdx.x; c < b.nchunks; c += gridDim.x) {
@@ -224,33 +189,33 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_hupdate(BatchDev b, int level) {
     const UnitDev& un = unit_at(b, u);
     RhsSt* st = b.st + (size_t)u * MAXR;
     const int nrhs = un.nrhs, D = un.D;
-    int done[NR];
-    T beta[NR];
+    int upd[NR], hup[NR];
+    T alpha[NR], beta[NR];
     bool active = false;
 #pragma unroll
     for (int k = 0; k < NR; ++k) {
-      done[k] = k < nrhs ? ld_int(&st[k].done) : 1;
-      beta[k] = done[k] ? T(0) : (T)__ldcg(&st[k].beta);
-      active |= !done[k];
+      const int dn = k < nrhs ? ld_int(&st[k].done) : 1;
+      upd[k] = k < nrhs && (!dn || ld_int(&st[k].upend));
+      hup[k] = !dn;
+      alpha[k] = upd[k] ? (T)__ldcg(&st[k].alpha) : T(0);
+      beta[k] = hup[k] ? (T)__ldcg(&st[k].beta) : T(0);
+      active |= upd[k] != 0;
     }
     if (!active) continue;
     const cplx<T>* r = vR<T>(un);
     cplx<T>* h = vH<T>(un);
+    cplx<T>* U = vU<T>(un);
     const T* M = vM<T>(un);
     const int base = (c - un.chunk0) * un.chunk, end = min(base + un.chunk, D);
-    for (int e = base + threadIdx.x; e < end; e += BLOCK) {
-      const T m = M[e];
-#pragma unroll
-      for (int k = 0; k < NR; ++k) {
-        if (k < nrhs && !done[k]) {
-          const size_t o = (size_t)k * D + e;
-          const cplx<T> rv = r[o];
-          cplx<T> hv = h[o];
-          hv.x = fma(beta[k], hv.x, m * rv.x);
-          hv.y = fma(beta[k], hv.y, m * rv.y);
-          h[o] = hv;
-        }
-      }
+    vec_hupdate<T, NR>(base, end, D, nrhs, upd, alpha, hup, beta, r, h, U, M);
+    __shared__ int s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(&b.ucount[u], 1u) == (unsigned)un.nchunk - 1u);
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+      for (int k = 0; k < nrhs && k < NR; ++k)
+        if (ld_int(&st[k].done)) st[k].upend = 0;
+      b.ucount[u] = 0;
     }
   }
 }

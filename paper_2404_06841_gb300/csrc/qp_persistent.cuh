@@ -14,6 +14,7 @@
 // every block returns as soon as it sees the flag, and the host reports QP_ERR_TIMEOUT.
 #pragma once
 #include "qp_stencil.cuh"
+#include "qp_vec.cuh"
 
 namespace qp {
 
@@ -120,29 +121,7 @@ __device__ __forceinline__ void ph_init(const BatchDev& b, const UnitDev& un, in
   for (int q = 0; q < 3 * NR; ++q) vt[q] = T(0);
   int base, end;
   chunk_range(un, c, base, end);
-  for (int e = base + threadIdx.x; e < end; e += BLOCK) {
-    const T m = M[e];
-#pragma unroll
-    for (int k = 0; k < NR; ++k) {
-      if (k < nrhs) {
-        const size_t o = (size_t)k * D + e;
-        cplx<T> f = F[o];
-        if (e == 0 || zero_rhs[k]) f = mk<T>(0, 0);
-        cplx<T> rv = f;
-        if (warm && e != 0) {
-          const cplx<T> wv = w[o];
-          rv = mk<T>(f.x - wv.x, f.y - wv.y);
-        }
-        r[o] = rv;
-        h[o] = mk<T>(m * rv.x, m * rv.y);
-        if (zero_u) U[o] = mk<T>(0, 0);
-        const T rr = fma(rv.x, rv.x, rv.y * rv.y);
-        vt[3 * k] = fma(f.x, f.x, fma(f.y, f.y, vt[3 * k]));
-        vt[3 * k + 1] = fma(m, rr, vt[3 * k + 1]);
-        vt[3 * k + 2] += rr;
-      }
-    }
-  }
+  vec_init<T, NR>(base, end, D, nrhs, warm, zero_u, zero_rhs, F, U, r, h, w, M, vt);
   block_reduce_mixed<T, 3 * NR>(vt, v);
   store_partials<3 * NR>(b, c, S_INIT, v);
 }
@@ -222,11 +201,10 @@ __device__ __forceinline__ void ph_apply(const BatchDev& b, const UnitDev& un, i
   store_partials<NV>(b, c, EPI == EPI_RESIDUAL ? S_RES : S_HW, v);
 }
 
-// U += alpha h, r -= alpha w; reduces (r, M r) and ||r||^2.
+// r -= alpha w; reduces (r, M r) and ||r||^2 (U is updated in the h-update phase, as in the graph form).
 template <typename T, int NR>
 __device__ __forceinline__ void ph_update(const BatchDev& b, const UnitDev& un, int c, const int* done,
-                                          const T* alpha, cplx<T>* U, cplx<T>* r, const cplx<T>* h,
-                                          const cplx<T>* w, const T* M) {
+                                          const T* alpha, cplx<T>* r, const cplx<T>* w, const T* M) {
   const int D = un.D, nrhs = un.nrhs;
   T vt[2 * NR];
   double v[2 * NR];
@@ -234,52 +212,21 @@ __device__ __forceinline__ void ph_update(const BatchDev& b, const UnitDev& un, 
   for (int q = 0; q < 2 * NR; ++q) vt[q] = T(0);
   int base, end;
   chunk_range(un, c, base, end);
-  for (int e = base + threadIdx.x; e < end; e += BLOCK) {
-    const T m = M[e];
-#pragma unroll
-    for (int k = 0; k < NR; ++k) {
-      if (k < nrhs && !done[k]) {
-        const size_t o = (size_t)k * D + e;
-        const T al = alpha[k];
-        const cplx<T> hv = h[o], wv = w[o];
-        cplx<T> uv = U[o], rv = r[o];
-        uv.x = fma(al, hv.x, uv.x);
-        uv.y = fma(al, hv.y, uv.y);
-        rv.x = fma(-al, wv.x, rv.x);
-        rv.y = fma(-al, wv.y, rv.y);
-        U[o] = uv;
-        r[o] = rv;
-        const T rr = fma(rv.x, rv.x, rv.y * rv.y);
-        vt[2 * k] = fma(m, rr, vt[2 * k]);
-        vt[2 * k + 1] += rr;
-      }
-    }
-  }
+  vec_update<T, NR>(base, end, D, nrhs, done, alpha, r, w, M, vt);
   block_reduce_mixed<T, 2 * NR>(vt, v);
   store_partials<2 * NR>(b, c, S_UPD, v);
 }
 
-// h = M r + beta h.
+// U += alpha h for the right-hand sides active in this iteration (act), h = M r + beta h for those still running.
 template <typename T, int NR>
-__device__ __forceinline__ void ph_hupdate(const UnitDev& un, int c, const int* done, const T* beta,
-                                           const cplx<T>* r, cplx<T>* h, const T* M) {
-  const int D = un.D, nrhs = un.nrhs;
+__device__ __forceinline__ void ph_hupdate(const UnitDev& un, int c, const int* act, const T* alpha, const int* done,
+                                           const T* beta, const cplx<T>* r, cplx<T>* h, cplx<T>* U, const T* M) {
+  int hup[NR];
+#pragma unroll
+  for (int k = 0; k < NR; ++k) hup[k] = !done[k];
   int base, end;
   chunk_range(un, c, base, end);
-  for (int e = base + threadIdx.x; e < end; e += BLOCK) {
-    const T m = M[e];
-#pragma unroll
-    for (int k = 0; k < NR; ++k) {
-      if (k < nrhs && !done[k]) {
-        const size_t o = (size_t)k * D + e;
-        const cplx<T> rv = r[o];
-        cplx<T> hv = h[o];
-        hv.x = fma(beta[k], hv.x, m * rv.x);
-        hv.y = fma(beta[k], hv.y, m * rv.y);
-        h[o] = hv;
-      }
-    }
-  }
+  vec_hupdate<T, NR>(base, end, un.D, un.nrhs, act, alpha, hup, beta, r, h, U, M);
 }
 
 template <typename T> struct LevelVecs {
@@ -307,8 +254,8 @@ __device__ __forceinline__ bool pcg_solve_block(const PersistArgs& a, const Unit
   const BatchDev& b = a.b;
   const int nrhs = un.nrhs;
   const LevelVecs<T> L = level_vecs(un, T(0));
-  __shared__ int s_done[MAXR];
-  __shared__ T s_coef[MAXR];
+  __shared__ int s_done[MAXR], s_act[MAXR];
+  __shared__ T s_coef[MAXR], s_alpha[MAXR];
   if (warm) {
     for (int c = blockIdx.x; c < b.nchunks; c += gridDim.x)
       ph_apply<T, REALC, NR, EPI_NONE, SK, NAX, DC>(b, un, c, sp, scoef, a.star, L.U, L.w, L.F);
@@ -365,12 +312,13 @@ __device__ __forceinline__ bool pcg_solve_block(const PersistArgs& a, const Unit
       if (threadIdx.x < MAXR) {
         const int k = threadIdx.x;
         s_done[k] = k < nrhs ? ls[k].done : 1;
-        s_coef[k] = s_done[k] ? T(0) : (T)ls[k].alpha;
+        s_act[k] = !s_done[k];
+        s_alpha[k] = s_done[k] ? T(0) : (T)ls[k].alpha;
       }
       __syncthreads();
     }
     for (int c = blockIdx.x; c < b.nchunks; c += gridDim.x)
-      ph_update<T, NR>(b, un, c, s_done, s_coef, L.U, L.r, L.h, L.w, L.M);
+      ph_update<T, NR>(b, un, c, s_done, s_alpha, L.r, L.w, L.M);
     if (!grid_sync(a)) return false;
     {
       double v[2 * NR];
@@ -405,11 +353,13 @@ __device__ __forceinline__ bool pcg_solve_block(const PersistArgs& a, const Unit
       }
       __syncthreads();
     }
+    // U += alpha h for this iteration's right-hand sides, h = M r + beta h for those still running
+    for (int c = blockIdx.x; c < b.nchunks; c += gridDim.x)
+      ph_hupdate<T, NR>(un, c, s_act, s_alpha, s_done, s_coef, L.r, L.h, L.U, L.M);
+    if (!grid_sync(a)) return false;
     bool all2 = true;
     for (int k = 0; k < nrhs && k < NR; ++k) all2 = all2 && s_done[k];
     if (all2) break;
-    for (int c = blockIdx.x; c < b.nchunks; c += gridDim.x) ph_hupdate<T, NR>(un, c, s_done, s_coef, L.r, L.h, L.M);
-    if (!grid_sync(a)) return false;
   }
   return true;
 }
@@ -532,7 +482,9 @@ __global__ void __launch_bounds__(BLOCK, NR >= 3 ? 1 : 2) k_pcg_persistent(const
           }
         }
       }
-      // (the inner init reads F32 only at the modes this thread just wrote: no barrier needed before it)
+      // the inner init reads F32 in this block's chunks only, with its own mapping of modes to threads: a block
+      // barrier before it suffices
+      __syncthreads();
       if (!(ok = pcg_solve_block<float, REALC, NR, SK, NAX, DC>(a, un, sp, sc32, false, true, ls, s_zero, b.tol2, b.maxit)))
         break;
       // U64 += |r64| c32 for the right-hand sides still refining

@@ -114,14 +114,190 @@ __device__ __forceinline__ void wstore(void* out, int slot, int e0, int D, const
   }
 }
 
+// ---- FP32 star-1 run in packed form: the taps as Hermitian pairs, two FP32 lanes per instruction
+//
+// For a real coefficient the tap -e_j holds the conjugate of the tap +e_j (c_j,a), so the two weights of axis j at
+// mode k come from the same two complex sums
+//   A = sum_a c_j,a q_a(k),   B = sum_a (c_j,a P_aj) lambda_a(k)         (q_a = lambda_a^2; scalar: c_j,a = c_j)
+// as  w(+e_j) = A + dp B  and  w(-e_j) = conj(A + dm B)  (dp, dm: the mode steps of the two neighbours, -1 and +1
+// away from the frequency wrap). Each complex sum is formed as a (re, im) pair with packed FP32 multiply-adds
+// (__ffma2_rn: two independent round-to-nearest fused multiply-adds), the lambda and q factors broadcast to both
+// lanes. The products with the vectors accumulate per mode in two pairs, P = sum w.re (h.re, h.im) and
+// S = sum w.im (h.re, h.im), so that each loaded value enters as it is stored; Q h = (P.re - S.im, P.im + S.re).
+// Real tap values skip S. The mean tap is real.
+__device__ __forceinline__ float2 pk(float x, float y) { return make_float2(x, y); }
+__device__ __forceinline__ float2 pk_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 pk_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+
+template <bool REALC, int NR, bool RO, int NAX = 0, int DC = 0>
+__device__ __forceinline__ void apply_run_star_f32(const StarParams& sp, int e0, const float2* h, int D, int nrhs,
+                                                   float2 (&acc)[2][NR]) {
+  const int d = DC ? DC : sp.d, n = NAX ? NAX : sp.n, jl = n - 1, Nl = sp.N[jl];
+  if (NAX != 0) nrhs = NR;   // the compiled-in geometries run with d = NR right-hand sides
+  int ib[MAXN], k[MAXN];
+  {
+    uint32_t x = (uint32_t)e0;
+#pragma unroll
+    for (int j = MAXN - 1; j >= 0; --j) {
+      if (j < n) {
+        const uint32_t qd = fdiv(x, sp.div[j]);
+        ib[j] = (int)(x - qd * (uint32_t)sp.N[j]);
+        k[j] = (2 * ib[j] < sp.N[j]) ? ib[j] : ib[j] - sp.N[j];
+        x = qd;
+      } else {
+        ib[j] = 0;
+        k[j] = 0;
+      }
+    }
+  }
+  int ibl = 0, kl0 = 0;
+#pragma unroll
+  for (int j = 0; j < MAXN; ++j)
+    if (j == jl) {
+      ibl = ib[j];
+      kl0 = k[j];
+    }
+  const int kl1 = (2 * (ibl + 1) < Nl) ? ibl + 1 : ibl + 1 - Nl;
+  // broadcast pairs per mode s of the run: (q_a, q_a) and (lambda_a, lambda_a)
+  float2 QQ[2][MAXD], LL[2][MAXD];
+  {
+    float lr[MAXD];
+#pragma unroll
+    for (int a = 0; a < MAXD; ++a) {
+      lr[a] = 0.f;
+#pragma unroll
+      for (int j = 0; j < MAXN - 1; ++j)
+        if (a < d && j < jl) lr[a] = fmaf(sp.P32[a][j], (float)k[j], lr[a]);
+    }
+#pragma unroll
+    for (int a = 0; a < MAXD; ++a) {
+      const float pl = sp.P32[a][jl];
+      const float l0 = (a < d) ? fmaf(pl, (float)kl0, lr[a]) : 0.f;
+      const float l1 = (a < d) ? fmaf(pl, (float)kl1, lr[a]) : 0.f;
+      LL[0][a] = pk(l0, l0);
+      LL[1][a] = pk(l1, l1);
+      QQ[0][a] = pk(l0 * l0, l0 * l0);
+      QQ[1][a] = pk(l1 * l1, l1 * l1);
+    }
+  }
+  const float2* hr[NR];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) hr[r] = h + (size_t)r * D;
+  float2 Pa[2][NR], Sa[2][NR];
+  // mean tap (real): P = w0 h
+  {
+    float2 w0[2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      w0[s] = pk_mul(pk(sp.c0r32[0], sp.c0r32[0]), QQ[s][0]);
+#pragma unroll
+      for (int a = 1; a < MAXD; ++a)
+        if (a < d) w0[s] = pk_fma(pk(sp.c0r32[a], sp.c0r32[a]), QQ[s][a], w0[s]);
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      if (r < nrhs) {
+        float2 v[2];
+        ld_run<RO, float, 2>(hr[r] + e0, v);
+        Pa[0][r] = pk_mul(w0[0], v[0]);
+        Pa[1][r] = pk_mul(w0[1], v[1]);
+      } else {
+        Pa[0][r] = Pa[1][r] = pk(0.f, 0.f);
+      }
+      Sa[0][r] = Sa[1][r] = pk(0.f, 0.f);
+    }
+  }
+  // weights of axis j at mode s: wp (tap +e_j) and wmc, the conjugate of the tap -e_j's weight
+  auto weights = [&](int j, int s, float dp, float dm, float2& wp, float2& wmc) {
+    float2 A = pk_mul(sp.hc32[j][0], QQ[s][0]);
+    float2 B = pk_mul(sp.hcp32[j][0], LL[s][0]);
+#pragma unroll
+    for (int a = 1; a < MAXD; ++a) {
+      if (a < d) {
+        A = pk_fma(sp.hc32[j][a], QQ[s][a], A);
+        B = pk_fma(sp.hcp32[j][a], LL[s][a], B);
+      }
+    }
+    wp = pk_fma(pk(dp, dp), B, A);
+    wmc = pk_fma(pk(dm, dm), B, A);
+  };
+  // the product of weight w (conj: the conjugate of w) with the stored value v
+  auto mac = [&](float2& P, float2& S, float2 w, bool conj, float2 v) {
+    P = pk_fma(pk(w.x, w.x), v, P);
+    if (!REALC) {
+      const float wy = conj ? -w.y : w.y;
+      S = pk_fma(pk(wy, wy), v, S);
+    }
+  };
+  // the last axis: one neighbour each side of the run, the run's own values for the inner taps
+  if (NAX != 0 || sp.has[jl]) {
+    const int hl = sp.half[jl];
+    const float dp0 = (ibl == hl) ? (float)(Nl - 1) : -1.f, dp1 = (ibl + 1 == hl) ? (float)(Nl - 1) : -1.f;
+    const float dm0 = (ibl == hl - 1) ? (float)(1 - Nl) : 1.f, dm1 = (ibl + 1 == hl - 1) ? (float)(1 - Nl) : 1.f;
+    float2 wp0, wm0, wp1, wm1;
+    weights(jl, 0, dp0, dm0, wp0, wm0);
+    weights(jl, 1, dp1, dm1, wp1, wm1);
+    const int il = e0 + ((ibl == 0) ? Nl - 1 : -1);       // k - e_l of the run's first mode
+    const int ir = e0 + ((ibl + 2 == Nl) ? 2 - Nl : 2);   // k + e_l of its second mode
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      if (r < nrhs) {
+        float2 v[2];
+        ld_run<RO, float, 2>(hr[r] + e0, v);
+        mac(Pa[0][r], Sa[0][r], wm0, true, v[1]);
+        mac(Pa[1][r], Sa[1][r], wp1, false, v[0]);
+        mac(Pa[0][r], Sa[0][r], wp0, false, ldh<RO>(hr[r] + il));
+        mac(Pa[1][r], Sa[1][r], wm1, true, ldh<RO>(hr[r] + ir));
+      }
+    }
+  }
+  // the other axes: one neighbour offset and one mode step per tap for the whole run
+#pragma unroll
+  for (int j = 0; j < MAXN - 1; ++j) {
+    if (j < jl && (NAX != 0 || sp.has[j])) {
+      const int Nj = sp.N[j], ibj = ib[j], hj = sp.half[j];
+      const int ep = e0 + ((ibj == 0) ? sp.woff[j] : -sp.stride[j]);        // k - e_j (tap +e_j)
+      const int em = e0 + ((ibj == Nj - 1) ? -sp.woff[j] : sp.stride[j]);   // k + e_j (tap -e_j)
+      const float dp = (ibj == hj) ? (float)(Nj - 1) : -1.f;
+      const float dm = (ibj == hj - 1) ? (float)(1 - Nj) : 1.f;
+      float2 wp0, wm0, wp1, wm1;
+      weights(j, 0, dp, dm, wp0, wm0);
+      weights(j, 1, dp, dm, wp1, wm1);
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        if (r < nrhs) {
+          float2 u[2], v[2];
+          ld_run<RO, float, 2>(hr[r] + ep, u);
+          ld_run<RO, float, 2>(hr[r] + em, v);
+          mac(Pa[0][r], Sa[0][r], wp0, false, u[0]);
+          mac(Pa[1][r], Sa[1][r], wp1, false, u[1]);
+          mac(Pa[0][r], Sa[0][r], wm0, true, v[0]);
+          mac(Pa[1][r], Sa[1][r], wm1, true, v[1]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+      acc[s][r] = REALC ? Pa[s][r] : pk(Pa[s][r].x - Sa[s][r].y, Pa[s][r].y + Sa[s][r].x);
+}
+
 // WM: 0 the weights are formed here; 1 (T = double) they are read from sp.w64; 2 (T = double) they are formed and
 // written to wout (the same arithmetic as WM = 0, so stored and formed weights agree bit for bit) and nothing
 // else is done.
 // NAX, DC (0: from sp at run time): the number of axes, every one of them with taps, and d known at compile time,
 // so that the axis loop is straight-line code whose neighbour reads the compiler can issue early.
+// FP32 with formed weights (WM = 0) takes apply_run_star_f32 above.
 template <typename T, bool REALC, int NR, bool RO, bool DIAGK, int WM = 0, int NAX = 0, int DC = 0>
 __device__ __forceinline__ void apply_run_star(const StarParams& sp, int e0, const cplx<T>* h, int D, int nrhs,
                                                cplx<T> (&acc)[2][NR], void* wout = nullptr) {
+  if constexpr (sizeof(T) == 4 && WM == 0) {
+    apply_run_star_f32<REALC, NR, RO, NAX, DC>(sp, e0, reinterpret_cast<const float2*>(h), D, nrhs,
+                                               reinterpret_cast<float2(&)[2][NR]>(acc));
+    return;
+  } else {
   constexpr int NQ = DIAGK ? MAXD : 1;   // weight terms per mode: q_a (diagonal) or q (scalar)
   constexpr bool FORM = WM != 1;         // the weights are formed from lambda
   const int d = DC ? DC : sp.d, n = NAX ? NAX : sp.n, jl = n - 1, Nl = sp.N[jl];
@@ -326,6 +502,7 @@ __device__ __forceinline__ void apply_run_star(const StarParams& sp, int e0, con
         }
       }
     }
+  }
   }
 }
 
