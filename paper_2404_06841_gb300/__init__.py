@@ -154,6 +154,8 @@ class Plan:
         self.handle = handle
         self.d, self.n, self.N = d, n, tuple(N)
         self.D = int(np.prod(N))
+        self.shape = tuple(N)
+        self.spectrum = QP_SPECTRUM_FULL
         self._keep = keep
 
     def __del__(self):
@@ -192,18 +194,25 @@ def _coeff_struct(coeff, d, keep):
 
 
 def qp_plan_create(d, n, P, N, coeff, backend=QP_BACKEND_AUTO, max_rhs=0, precisions=0, exec_mode=QP_EXEC_AUTO,
-                   stream=None) -> Plan:
+                   spectrum=QP_SPECTRUM_FULL, stream=None) -> Plan:
+    """A plan; ``plan.D`` is the length of the vectors its calls take (the half-spectrum storage's D_h for
+    spectrum=QP_SPECTRUM_HALF), ``plan.shape`` their shape as an array (last axis ceil(N/2) long for that storage)."""
     P = np.ascontiguousarray(P, dtype=np.float64).reshape(-1)
     Narr = np.ascontiguousarray(N, dtype=np.int32).reshape(-1)
     if d >= 1 and n >= 1 and (P.size != d * n or Narr.size != n):
         raise ValueError("P must hold d*n entries and N n entries")
     keep = [P, Narr]
     c = _coeff_struct(coeff, d, keep)
-    opt = qp_options(int(backend), int(max_rhs), int(precisions), int(exec_mode))
+    opt = qp_options(int(backend), int(max_rhs), int(precisions), int(exec_mode), int(spectrum))
     out = C.c_void_p()
     _check(_lib.qp_plan_create(d, n, P.ctypes.data_as(C.POINTER(C.c_double)), Narr.ctypes.data_as(C.POINTER(C.c_int)),
                                C.byref(c), C.byref(opt), _stream(stream), C.byref(out)))
-    return Plan(out, d, n, [int(x) for x in Narr], keep=[])
+    plan = Plan(out, d, n, [int(x) for x in Narr], keep=[])
+    if spectrum == QP_SPECTRUM_HALF:
+        plan.spectrum = QP_SPECTRUM_HALF
+        plan.shape = plan.N[:-1] + ((plan.N[-1] + 1) // 2,)
+        plan.D = int(np.prod(plan.shape))
+    return plan
 
 
 def qp_plan_destroy(plan: Plan):
@@ -218,7 +227,8 @@ def qp_plan_query(plan: Plan) -> dict:
     _check(_lib.qp_plan_query(plan.handle, C.byref(info)))
     return {"D": info.D, "backend": {1: "taps", 2: "fft"}.get(info.backend, info.backend), "ntaps": info.ntaps,
             "max_rhs": info.max_rhs, "min_abs_lambda": info.min_abs_lambda, "device_bytes": info.device_bytes,
-            "star": bool(info.star), "stored_weights": bool(info.stored_weights)}
+            "star": bool(info.star), "stored_weights": bool(info.stored_weights), "spectrum": info.spectrum,
+            "stored": info.stored}
 
 
 def qp_apply_stiffness(plan: Plan, U, QU, precision=QP_FP64, nrhs=None, stream=None):
@@ -359,7 +369,7 @@ def qp_launch_count() -> int:
 def qp_plan_diagonal(plan: Plan, precond=QP_PRECOND_JACOBI, stream=None):
     """The preconditioner diagonal M (z = M r) as a device float64 tensor of the plan's grid shape."""
     import torch
-    out = torch.empty(plan.N, dtype=torch.float64, device="cuda")
+    out = torch.empty(plan.shape, dtype=torch.float64, device="cuda")
     _check(_lib.qp_plan_diagonal(plan.handle, int(precond), _ptr(out), _stream(stream)))
     return out
 

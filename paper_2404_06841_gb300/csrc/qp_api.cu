@@ -55,6 +55,8 @@ struct Solver;
 
 struct qp_plan {
   int d = 0, n = 0, kind = 0, ncomp = 0, backend = 0, max_rhs = 0, nblk = 0, precisions = 3, D = 0, exec = 0;
+  int64_t Dfull = 0;             // product of the N_j (D is the stored length: D_h for a half-spectrum plan)
+  int spectrum = QP_SPECTRUM_FULL;
   int N[MAXN] = {};
   double P[MAXD][MAXN] = {};
   double min_abs_lambda = 0.0;
@@ -227,34 +229,44 @@ bool is_23(int N) {
 
 // ------------------------------------------------------------------------------------------------ plan set-up
 
-void build_geometry(qp_plan* p, int d, int n, const double* P, const int* N) {
+// half: half-spectrum storage (QP_SPECTRUM_HALF): the last axis keeps k_{n-1} = 0 .. ceil(N/2) - 1 and vectors hold
+// D_h = N_1 .. N_{n-1} ceil(N_n / 2) entries (p->D); p->Dfull keeps the product of all N_j.
+void build_geometry(qp_plan* p, int d, int n, const double* P, const int* N, bool half) {
   if (d < 1 || d > MAXD) raise(QP_ERR_INVALID_ARG, "d must be 1..3");
   if (n < d || n > MAXN) raise(QP_ERR_INVALID_ARG, "n must satisfy d <= n <= 6");
   if (!P || !N) raise(QP_ERR_INVALID_ARG, "P and N must be non-null host arrays");
   p->d = d;
   p->n = n;
-  int64_t D = 1;
+  int64_t Dfull = 1;
   for (int j = 0; j < n; ++j) {
     if (N[j] < 2 || N[j] > 1024) raise(QP_ERR_INVALID_ARG, "every N_j must be in 2..1024");
-    D *= N[j];
+    Dfull *= N[j];
   }
-  if (D > (int64_t(1) << 30)) raise(QP_ERR_INVALID_ARG, "D = prod N_j must be <= 2^30");
-  p->D = (int)D;
+  if (Dfull > (int64_t(1) << 30)) raise(QP_ERR_INVALID_ARG, "D = prod N_j must be <= 2^30");
   PlanDev& pd = p->host_pd;
   std::memset(&pd, 0, sizeof(pd));
   pd.n = n;
   pd.d = d;
-  pd.D = (int)D;
+  pd.hspec = half ? 1 : 0;
+  pd.Hl = (N[n - 1] + 1) / 2;
   int st = 1;
   for (int j = n - 1; j >= 0; --j) {
     pd.N[j] = N[j];
     p->N[j] = N[j];
+    pd.Nst[j] = (half && j == n - 1) ? pd.Hl : N[j];
+    pd.nyq[j] = (half && j < n - 1 && N[j] % 2 == 0) ? N[j] / 2 : -1;
     pd.stride[j] = st;
-    pd.div[j] = make_fastdiv((uint32_t)N[j]);
-    st *= N[j];
+    pd.div[j] = make_fastdiv((uint32_t)pd.Nst[j]);
+    st *= pd.Nst[j];
   }
+  const int64_t D = st;
+  p->D = (int)D;
+  p->Dfull = Dfull;
+  pd.D = (int)D;
   for (int j = n; j < MAXN; ++j) {
     pd.N[j] = 1;
+    pd.Nst[j] = 1;
+    pd.nyq[j] = -1;
     pd.stride[j] = (int)D;
     pd.div[j] = make_fastdiv(1);
   }
@@ -389,7 +401,7 @@ void build_taps(qp_plan* p, const qp_coeff* c) {
 // FP64 vectors and the table takes at most a quarter of the free device memory.
 void build_star_weights(qp_plan* p, cudaStream_t s) {
   const PlanDev& pd = p->host_pd;
-  if (!pd.star1 || !(p->precisions & 1) || pd.N[pd.n - 1] % 2 != 0) return;
+  if (!pd.star1 || !(p->precisions & 1) || pd.Nst[pd.n - 1] % 2 != 0) return;
   const size_t bytes = (size_t)(1 + 2 * pd.n) * (size_t)p->D * (p->real_coef ? sizeof(double) : sizeof(double2));
   size_t fr = 0, tot = 0;
   CK(cudaMemGetInfo(&fr, &tot));
@@ -508,7 +520,7 @@ void alloc_workspace(qp_plan* p) {
 // Modes per thread step of the stencil kernels for this plan: runs of 2 along the last axis when its length is
 // even (the run then never crosses a row), else 1. (Longer runs cut index work further but need more registers
 // per thread; on GB300 the occupancy they cost outweighed it.)
-int last_axis_run(const qp_plan* p) { return (p->host_pd.N[p->host_pd.n - 1] % 2 == 0) ? 2 : 1; }
+int last_axis_run(const qp_plan* p) { return (p->host_pd.Nst[p->host_pd.n - 1] % 2 == 0) ? 2 : 1; }
 
 // Everything a solve needs about its units on the host side.
 struct Units {
@@ -809,6 +821,9 @@ Entry& get_entry(Solver* sv, const Units& us, const Key& key, cudaStream_t s) {
     x.chunk = (int)chunk;
     x.run = last_axis_run(p);
     x.fft = p->backend == QP_BACKEND_FFT ? 1 : 0;
+    x.hspec = p->host_pd.hspec;
+    x.Hl = p->host_pd.Hl;
+    x.hdiv = make_fastdiv((uint32_t)p->host_pd.Hl);
     x.chunk0 = (int)chunk_unit.size();
     x.nchunk = (int)((p->D + chunk - 1) / chunk);
     for (int c = 0; c < x.nchunk; ++c) chunk_unit.push_back(u);
@@ -991,7 +1006,7 @@ Units single_units(qp_plan* p, int nrhs) {
   us.max_coef = std::max(1, p->coef_count);
   us.max_rhs = nrhs;
   us.direct = p->exec == QP_EXEC_DIRECT;
-  us.exec = p->backend == QP_BACKEND_TAPS ? p->exec : QP_EXEC_GRAPH;
+  us.exec = (p->backend == QP_BACKEND_TAPS && p->spectrum == QP_SPECTRUM_FULL) ? p->exec : QP_EXEC_GRAPH;
   us.run = last_axis_run(p);
   return us;
 }
@@ -1012,6 +1027,8 @@ void check_opts(const qp_solve_opts* o, const qp_plan* p) {
 // diagonal, on first request).
 void prepare_precond(qp_plan* p, int precond, cudaStream_t s) {
   if (precond != QP_PRECOND_FROBENIUS || p->frob_ready) return;
+  if (p->spectrum == QP_SPECTRUM_HALF)
+    raise(QP_ERR_UNSUPPORTED, "the Frobenius-optimal diagonal is not built for half-spectrum plans (Jacobi is)");
   if (p->backend == QP_BACKEND_TAPS) {
     launch_diag(p->pd, p->coef_count, p->D, p->jac64, p->frob64, p->jac32, p->frob32, p->scratch, p->counter,
                 p->small, p->nblk, true, s);
@@ -1104,7 +1121,8 @@ qp_status qp_l2qp_error(qp_plan* p, int nrhs, const void* U, const void* Uref, d
   if (nrhs < 1 || nrhs > MAXR) raise(QP_ERR_INVALID_ARG, "nrhs must be 1..QP_MAX_RHS");
   if (((uintptr_t)U | (uintptr_t)Uref) & 15u) raise(QP_ERR_INVALID_ARG, "U and Uref must be 16-byte aligned");
   cudaStream_t s = S(stream);
-  launch_l2_norms(p->D, nrhs, (const double2*)U, (const double2*)Uref, p->scratch, p->nblk, p->small, s);
+  launch_l2_norms(p->D, nrhs, (const double2*)U, (const double2*)Uref, p->scratch, p->nblk, p->small,
+                  p->host_pd.hspec ? p->host_pd.Hl : 0, s);
   CK_LAUNCH();
   CK(cudaMemcpyAsync(p->h_small, p->small, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
@@ -1197,7 +1215,12 @@ qp_status qp_plan_create(int d, int n, const double* P, const int* N, const qp_c
   std::unique_ptr<qp_plan> p(new qp_plan());
   cudaStream_t s = S(stream);
   p->create_stream = s;
-  build_geometry(p.get(), d, n, P, N);
+  p->spectrum = opt ? opt->spectrum : QP_SPECTRUM_FULL;
+  if (p->spectrum != QP_SPECTRUM_FULL && p->spectrum != QP_SPECTRUM_HALF) raise(QP_ERR_INVALID_ARG, "unknown spectrum");
+  const bool half = p->spectrum == QP_SPECTRUM_HALF;
+  if (half && (coeff->repr != QP_REPR_TAPS || (opt && opt->backend == QP_BACKEND_FFT)))
+    raise(QP_ERR_UNSUPPORTED, "the half-spectrum storage needs a tap coefficient on the taps backend");
+  build_geometry(p.get(), d, n, P, N, half);
   if (coeff->kind < QP_COEF_SCALAR || coeff->kind > QP_COEF_SYM) raise(QP_ERR_INVALID_ARG, "unknown coefficient kind");
   p->kind = coeff->kind;
   p->ncomp = ncomp_of(coeff->kind, d);
@@ -1229,7 +1252,7 @@ qp_status qp_plan_create(int d, int n, const double* P, const int* N, const qp_c
   bool fft_ok = true;
   for (int j = 0; j < n; ++j) fft_ok = fft_ok && fft_supported(N[j]);
   // (only dense tap lists on grids large enough to time reliably: below that the stencil is taken outright)
-  if (p->backend == QP_BACKEND_TAPS && backend_req == QP_BACKEND_AUTO && fft_ok && (p->precisions & 2) &&
+  if (p->backend == QP_BACKEND_TAPS && backend_req == QP_BACKEND_AUTO && fft_ok && (p->precisions & 2) && !half &&
       fft_autotune_on() && p->host_pd.ntaps >= 64 && p->D >= 65536) {
     CK(cudaMemcpyAsync(p->pd, &p->host_pd, sizeof(PlanDev), cudaMemcpyHostToDevice, s));
     p->backend = tune_backend(p.get(), s);
@@ -1281,7 +1304,9 @@ qp_status qp_plan_destroy(qp_plan* plan) {
 qp_status qp_plan_query(const qp_plan* p, qp_plan_info* info) {
   API_BEGIN
   if (!p || !info) raise(QP_ERR_INVALID_ARG, "plan and info must be non-null");
-  info->D = p->D;
+  info->D = p->Dfull;
+  info->stored = p->D;
+  info->spectrum = p->spectrum;
   info->backend = p->backend;
   info->ntaps = p->host_pd.ntaps;
   info->max_rhs = p->max_rhs;

@@ -46,9 +46,11 @@ __device__ __forceinline__ void apply_chunk(const PlanDev& sp, const cplx<T>* sc
             *reinterpret_cast<float4*>(dst + o) = make_float4((float)acc[0][r].x, (float)acc[0][r].y,
                                                               (float)acc[1][r].x, (float)acc[1][r].y);
             if (EPI == EPI_DOT_HW) {
+              // half-spectrum units weigh each mode 1 or 2 (mode_weight; exact scaling, 1 elsewhere)
+              const T w0 = (T)mode_weight(un, e0), w1 = (T)mode_weight(un, e0 + 1);
               const float4 hv = __ldg(reinterpret_cast<const float4*>(src + o));
-              vt[r] = fma((T)hv.x, acc[0][r].x, fma((T)hv.y, acc[0][r].y, vt[r]));
-              vt[r] = fma((T)hv.z, acc[1][r].x, fma((T)hv.w, acc[1][r].y, vt[r]));
+              vt[r] = fma(w0 * (T)hv.x, acc[0][r].x, fma(w0 * (T)hv.y, acc[0][r].y, vt[r]));
+              vt[r] = fma(w1 * (T)hv.z, acc[1][r].x, fma(w1 * (T)hv.w, acc[1][r].y, vt[r]));
             }
           }
         }
@@ -58,6 +60,7 @@ __device__ __forceinline__ void apply_chunk(const PlanDev& sp, const cplx<T>* sc
 #pragma unroll
     for (int s = 0; s < RUN; ++s) {
       const int e = e0 + s;
+      const T we = (EPI == EPI_NONE) ? T(1) : (T)mode_weight(un, e);
 #pragma unroll
       for (int r = 0; r < NR; ++r) {
         if (r < nrhs) {
@@ -65,13 +68,13 @@ __device__ __forceinline__ void apply_chunk(const PlanDev& sp, const cplx<T>* sc
           if (EPI == EPI_DOT_HW) {
             if (!fft_unit) dst[o] = acc[s][r];
             const cplx<T> hv = src[o];
-            vt[r] = fma(hv.x, acc[s][r].x, fma(hv.y, acc[s][r].y, vt[r]));
+            vt[r] = fma(we * hv.x, acc[s][r].x, fma(we * hv.y, acc[s][r].y, vt[r]));
           } else if (EPI == EPI_RESIDUAL) {
             const cplx<T> f = F[o];
             const cplx<T> res = (e == 0) ? mk<T>(0, 0) : mk<T>(f.x - acc[s][r].x, f.y - acc[s][r].y);
             dst[o] = res;
-            vt[2 * r] = fma(res.x, res.x, fma(res.y, res.y, vt[2 * r]));
-            if (e != 0) vt[2 * r + 1] = fma(f.x, f.x, fma(f.y, f.y, vt[2 * r + 1]));
+            vt[2 * r] = fma(we * res.x, res.x, fma(we * res.y, res.y, vt[2 * r]));
+            if (e != 0) vt[2 * r + 1] = fma(we * f.x, f.x, fma(we * f.y, f.y, vt[2 * r + 1]));
           } else {
             if (!fft_unit) dst[o] = acc[s][r];
           }

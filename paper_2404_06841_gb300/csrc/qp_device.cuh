@@ -84,14 +84,15 @@ __device__ __forceinline__ uint32_t fdiv(uint32_t x, const FastDiv& f) {
   return (uint32_t)(((uint64_t)x * f.m) >> f.p);
 }
 
-// Storage digits ibar_j of linear index e (last axis fastest) and the signed modes k_j.
+// Storage digits ibar_j of linear index e (last axis fastest) and the signed modes k_j. (A half-spectrum plan's
+// last-axis digit is k_{n-1} itself: 0 <= ibar < ceil(N/2), so the signed rule returns it unchanged.)
 __device__ __forceinline__ void mode_digits(const PlanDev& p, int e, int (&ib)[MAXN], int (&k)[MAXN]) {
   uint32_t x = (uint32_t)e;
 #pragma unroll
   for (int j = MAXN - 1; j >= 0; --j) {
     if (j < p.n) {
       const uint32_t q = fdiv(x, p.div[j]);
-      ib[j] = (int)(x - q * (uint32_t)p.N[j]);
+      ib[j] = (int)(x - q * (uint32_t)p.Nst[j]);
       k[j] = (2 * ib[j] < p.N[j]) ? ib[j] : ib[j] - p.N[j];
       x = q;
     } else {
@@ -226,5 +227,12 @@ __device__ __forceinline__ void count_done(const BatchDev& b, int which, int n, 
 }
 
 __device__ __forceinline__ int ld_int(const int* p) { return *((volatile const int*)p); }
+
+// Weight of storage index e in the inner products of a half-spectrum unit (1 on the self-conjugate plane
+// k_{n-1} = 0, 2 elsewhere: the entry stands for the mode and its mirror); 1 for full-spectrum units.
+__device__ __forceinline__ int mode_weight(const UnitDev& un, int e) {
+  if (!un.hspec) return 1;
+  return (e - (int)fdiv((uint32_t)e, un.hdiv) * un.Hl) == 0 ? 1 : 2;
+}
 
 }  // namespace qp

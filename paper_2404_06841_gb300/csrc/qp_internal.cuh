@@ -145,6 +145,10 @@ struct alignas(16) StarParams {
   float2 hcp32[MAXN][MAXD];
   float c0r32[MAXD];
   int pad2_;
+  // storage (PlanDev.Nst, nyq, hspec, Hl)
+  int Nst[MAXN];
+  int nyq[MAXN];
+  int hspec, Hl, pad3_, pad4_;
 };
 static_assert(sizeof(StarParams) % 16 == 0, "StarParams is uploaded and passed as 16-byte words");
 
@@ -166,6 +170,12 @@ struct alignas(16) PlanDev {
   int star1, pad_star;
   const StarParams* star;
   signed char m[MAXT][MAXN];  // sorted tap modes
+  // storage: Nst[j] entries along axis j (N[j], except ceil(N_{n-1} / 2) for the last axis of a half-spectrum plan,
+  // which stores k_{n-1} = 0 .. Hl - 1 at index k_{n-1}); nyq[j]: the storage index of the dropped Nyquist mode
+  // k_j = -N_j/2 of a half-spectrum plan (N_j even, j < n - 1), else -1
+  int Nst[MAXN];
+  int nyq[MAXN];
+  int hspec, Hl, pad_h0, pad_h1;   // hspec: half-spectrum storage (QP_SPECTRUM_HALF); Hl = ceil(N_{n-1} / 2)
 };
 static_assert(sizeof(PlanDev) % 16 == 0, "PlanDev is copied to shared memory in 16-byte words");
 
@@ -220,6 +230,12 @@ inline void make_star(PlanDev& pd, const double2* c64, const float2* c32, StarPa
   }
   sp.n = pd.n;
   sp.d = pd.d;
+  for (int j = 0; j < MAXN; ++j) {
+    sp.Nst[j] = pd.Nst[j];
+    sp.nyq[j] = pd.nyq[j];
+  }
+  sp.hspec = pd.hspec;
+  sp.Hl = pd.Hl;
   pd.star1 = 1;
 }
 
@@ -231,7 +247,10 @@ struct UnitDev {
   int run;             // stencil run along the last axis: 2 when its length is even, else 1
   int fft;             // 1: FFT-backend unit (its applies write w in FFT passes; the batch kernels add only the
                        // epilogue and need no plan in shared memory)
-  int pad_;
+  int hspec;           // 1: half-spectrum storage; a mode with k_{n-1} > 0 stands for itself and its mirror, so
+                       // it weighs 2 in every inner product (its storage index e has e mod Hl != 0)
+  int Hl, pad_u0;
+  FastDiv hdiv;        // division by Hl
   const double2* F;   // right-hand side (FP64)
   double2* U;         // solution (FP64)
   double2* r;         // FP64 PCG residual
@@ -317,7 +336,7 @@ void pinned_free(void* p, size_t bytes);
 
 // ||U_r - Uref_r||_2 over the Fourier coefficients (qp_norms.cu)
 void launch_l2_norms(int D, int nrhs, const double2* U, const double2* Uref, double* part, int nblk, double* out,
-                     cudaStream_t s);
+                     int hl, cudaStream_t s);
 
 // persistent solve of one taps unit (qp_persistent.cu): the kernel's argument
 struct PersistArgs {

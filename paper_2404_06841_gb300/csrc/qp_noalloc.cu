@@ -97,12 +97,18 @@ void build_host(int d, int n, const double* P, const int* N, const qp_coeff* c, 
   int st = 1;
   for (int j = n - 1; j >= 0; --j) {
     pd.N[j] = N[j];
+    pd.Nst[j] = N[j];
+    pd.nyq[j] = -1;
     pd.stride[j] = st;
     pd.div[j] = make_fastdiv((uint32_t)N[j]);
     st *= N[j];
   }
+  pd.hspec = 0;
+  pd.Hl = (N[n - 1] + 1) / 2;
   for (int j = n; j < MAXN; ++j) {
     pd.N[j] = 1;
+    pd.Nst[j] = 1;
+    pd.nyq[j] = -1;
     pd.stride[j] = (int)D;
     pd.div[j] = make_fastdiv(1);
   }

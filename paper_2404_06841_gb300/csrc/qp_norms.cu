@@ -6,9 +6,11 @@
 
 namespace qp {
 
-// part[r * gridDim.x + block] = sum over the block's modes of |U_r - Uref_r|^2 (Uref may be null: |U_r|^2)
+// part[r * gridDim.x + block] = sum over the block's modes of |U_r - Uref_r|^2 (Uref may be null: |U_r|^2).
+// hl > 0: half-spectrum storage with hl entries along the last axis; an entry off the plane k_{n-1} = 0 also
+// stands for its mirror and counts twice.
 __global__ void __launch_bounds__(BLOCK) k_sqdiff(int D, int nrhs, const double2* __restrict__ U,
-                                                   const double2* __restrict__ Uref, double* part) {
+                                                   const double2* __restrict__ Uref, double* part, int hl) {
   double v[MAXR];
 #pragma unroll
   for (int r = 0; r < MAXR; ++r) v[r] = 0.0;
@@ -22,7 +24,8 @@ __global__ void __launch_bounds__(BLOCK) k_sqdiff(int D, int nrhs, const double2
           u.x -= q.x;
           u.y -= q.y;
         }
-        v[r] = fma(u.x, u.x, fma(u.y, u.y, v[r]));
+        const double we = (hl > 0 && e % hl != 0) ? 2.0 : 1.0;
+        v[r] = fma(we * u.x, u.x, fma(we * u.y, u.y, v[r]));
       }
     }
   }
@@ -45,10 +48,10 @@ __global__ void __launch_bounds__(BLOCK) k_sqdiff_final(int nb, int nrhs, const 
     for (int r = 0; r < nrhs; ++r) out[r] = sqrt(v[r]);
 }
 
-// part: device, at least MAXR * nblk doubles; out: device, nrhs doubles.
+// part: device, at least MAXR * nblk doubles; out: device, nrhs doubles; hl: as k_sqdiff (0: full spectrum).
 void launch_l2_norms(int D, int nrhs, const double2* U, const double2* Uref, double* part, int nblk, double* out,
-                     cudaStream_t s) {
-  k_sqdiff<<<nblk, BLOCK, 0, s>>>(D, nrhs, U, Uref, part);
+                     int hl, cudaStream_t s) {
+  k_sqdiff<<<nblk, BLOCK, 0, s>>>(D, nrhs, U, Uref, part, hl);
   count_launch();
   k_sqdiff_final<<<1, BLOCK, 0, s>>>(nblk, nrhs, part, out);
   count_launch();

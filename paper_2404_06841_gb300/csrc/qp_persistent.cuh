@@ -121,7 +121,7 @@ __device__ __forceinline__ void ph_init(const BatchDev& b, const UnitDev& un, in
   for (int q = 0; q < 3 * NR; ++q) vt[q] = T(0);
   int base, end;
   chunk_range(un, c, base, end);
-  vec_init<T, NR>(base, end, D, nrhs, warm, zero_u, zero_rhs, F, U, r, h, w, M, vt);
+  vec_init<T, NR>(un, base, end, D, nrhs, warm, zero_u, zero_rhs, F, U, r, h, w, M, vt);
   block_reduce_mixed<T, 3 * NR>(vt, v);
   store_partials<3 * NR>(b, c, S_INIT, v);
 }
@@ -212,7 +212,7 @@ __device__ __forceinline__ void ph_update(const BatchDev& b, const UnitDev& un, 
   for (int q = 0; q < 2 * NR; ++q) vt[q] = T(0);
   int base, end;
   chunk_range(un, c, base, end);
-  vec_update<T, NR>(base, end, D, nrhs, done, alpha, r, w, M, vt);
+  vec_update<T, NR>(un, base, end, D, nrhs, done, alpha, r, w, M, vt);
   block_reduce_mixed<T, 2 * NR>(vt, v);
   store_partials<2 * NR>(b, c, S_UPD, v);
 }

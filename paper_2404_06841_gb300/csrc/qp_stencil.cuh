@@ -129,6 +129,61 @@ __device__ __forceinline__ float2 pk(float x, float y) { return make_float2(x, y
 __device__ __forceinline__ float2 pk_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 pk_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
 
+// ---- half-spectrum storage (StarParams.hspec): the last axis holds k_l = 0 .. Hl - 1 only. Of a run's last-axis
+// neighbours, k - e_l of its first mode at k_l = 0 is the conjugate of the stored mirror entry (-k, k_l = 1), and
+// k + e_l of its second mode at k_l = Hl - 1 is the dropped Nyquist mode (even N_l: 0) or, across the frequency
+// wrap, the conjugate of the mirror entry (-k, k_l = Hl - 1) (odd N_l). A mode with a dropped Nyquist digit on
+// another axis is not an unknown: its output is 0 (and its stored input is 0, so it adds nothing elsewhere).
+struct HalfEdges {
+  int il, ir;          // storage indices of the run's left and right last-axis neighbours
+  bool cl, cr, zr;     // conjugate the left / right value; the right value is 0
+  bool nyq_row;        // the run's modes have a dropped Nyquist digit
+};
+
+__device__ __forceinline__ HalfEdges half_edges(const StarParams& sp, const int (&ib)[MAXN], int n, int e0, int ibl) {
+  HalfEdges he;
+  const int jl = n - 1, Nsl = sp.Nst[jl];
+  he.il = e0 + ((ibl == 0) ? Nsl - 1 : -1);
+  he.ir = e0 + ((ibl + 2 == Nsl) ? 2 - Nsl : 2);
+  he.cl = he.cr = he.zr = he.nyq_row = false;
+  if (sp.hspec) {
+    if (ibl == 0 || ibl + 2 == Nsl) {
+      int mr = 0;   // storage index of (-k_0, .., -k_{n-2}, 0)
+#pragma unroll
+      for (int j = 0; j < MAXN - 1; ++j)
+        if (j < jl) mr += (ib[j] == 0 ? 0 : sp.N[j] - ib[j]) * sp.stride[j];
+      if (ibl == 0) {
+        he.il = mr + 1;
+        he.cl = true;
+      }
+      if (ibl + 2 == Nsl) {
+        if (sp.N[jl] % 2 == 0) {
+          he.zr = true;
+          he.ir = e0;
+        } else {
+          he.ir = mr + Nsl - 1;
+          he.cr = true;
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < MAXN - 1; ++j)
+      if (j < jl) he.nyq_row |= ib[j] == sp.nyq[j];
+  }
+  return he;
+}
+
+template <bool RO, typename V>
+__device__ __forceinline__ V ld_edge(const V* p, bool conj, bool zero) {
+  V v = ldh<RO>(p);
+  if (conj) v.y = -v.y;
+  if (zero) {
+    v.x = 0;
+    v.y = 0;
+  }
+  return v;
+}
+
 template <bool REALC, int NR, bool RO, int NAX = 0, int DC = 0>
 __device__ __forceinline__ void apply_run_star_f32(const StarParams& sp, int e0, const float2* h, int D, int nrhs,
                                                    float2 (&acc)[2][NR]) {
@@ -141,7 +196,7 @@ __device__ __forceinline__ void apply_run_star_f32(const StarParams& sp, int e0,
     for (int j = MAXN - 1; j >= 0; --j) {
       if (j < n) {
         const uint32_t qd = fdiv(x, sp.div[j]);
-        ib[j] = (int)(x - qd * (uint32_t)sp.N[j]);
+        ib[j] = (int)(x - qd * (uint32_t)sp.Nst[j]);
         k[j] = (2 * ib[j] < sp.N[j]) ? ib[j] : ib[j] - sp.N[j];
         x = qd;
       } else {
@@ -158,6 +213,7 @@ __device__ __forceinline__ void apply_run_star_f32(const StarParams& sp, int e0,
       kl0 = k[j];
     }
   const int kl1 = (2 * (ibl + 1) < Nl) ? ibl + 1 : ibl + 1 - Nl;
+  const HalfEdges he = half_edges(sp, ib, n, e0, ibl);   // k - e_l of the run's first mode, k + e_l of its second
   // broadcast pairs per mode s of the run: (q_a, q_a) and (lambda_a, lambda_a)
   float2 QQ[2][MAXD], LL[2][MAXD];
   {
@@ -237,8 +293,6 @@ __device__ __forceinline__ void apply_run_star_f32(const StarParams& sp, int e0,
     float2 wp0, wm0, wp1, wm1;
     weights(jl, 0, dp0, dm0, wp0, wm0);
     weights(jl, 1, dp1, dm1, wp1, wm1);
-    const int il = e0 + ((ibl == 0) ? Nl - 1 : -1);       // k - e_l of the run's first mode
-    const int ir = e0 + ((ibl + 2 == Nl) ? 2 - Nl : 2);   // k + e_l of its second mode
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
       if (r < nrhs) {
@@ -246,8 +300,8 @@ __device__ __forceinline__ void apply_run_star_f32(const StarParams& sp, int e0,
         ld_run<RO, float, 2>(hr[r] + e0, v);
         mac(Pa[0][r], Sa[0][r], wm0, true, v[1]);
         mac(Pa[1][r], Sa[1][r], wp1, false, v[0]);
-        mac(Pa[0][r], Sa[0][r], wp0, false, ldh<RO>(hr[r] + il));
-        mac(Pa[1][r], Sa[1][r], wm1, true, ldh<RO>(hr[r] + ir));
+        mac(Pa[0][r], Sa[0][r], wp0, false, ld_edge<RO>(hr[r] + he.il, he.cl, false));
+        mac(Pa[1][r], Sa[1][r], wm1, true, ld_edge<RO>(hr[r] + he.ir, he.cr, he.zr));
       }
     }
   }
@@ -281,7 +335,8 @@ __device__ __forceinline__ void apply_run_star_f32(const StarParams& sp, int e0,
   for (int s = 0; s < 2; ++s)
 #pragma unroll
     for (int r = 0; r < NR; ++r)
-      acc[s][r] = REALC ? Pa[s][r] : pk(Pa[s][r].x - Sa[s][r].y, Pa[s][r].y + Sa[s][r].x);
+      acc[s][r] = he.nyq_row ? pk(0.f, 0.f)
+                             : (REALC ? Pa[s][r] : pk(Pa[s][r].x - Sa[s][r].y, Pa[s][r].y + Sa[s][r].x));
 }
 
 // WM: 0 the weights are formed here; 1 (T = double) they are read from sp.w64; 2 (T = double) they are formed and
@@ -309,7 +364,7 @@ __device__ __forceinline__ void apply_run_star(const StarParams& sp, int e0, con
     for (int j = MAXN - 1; j >= 0; --j) {
       if (j < n) {
         const uint32_t qd = fdiv(x, sp.div[j]);
-        ib[j] = (int)(x - qd * (uint32_t)sp.N[j]);
+        ib[j] = (int)(x - qd * (uint32_t)sp.Nst[j]);
         k[j] = (2 * ib[j] < sp.N[j]) ? ib[j] : ib[j] - sp.N[j];
         x = qd;
       } else {
@@ -325,6 +380,7 @@ __device__ __forceinline__ void apply_run_star(const StarParams& sp, int e0, con
       ibl = ib[j];
       kl0 = k[j];
     }
+  const HalfEdges he = half_edges(sp, ib, n, e0, ibl);   // k - e_l of the run's first mode, k + e_l of its second
   const cplx<T>* hr[NR];
 #pragma unroll
   for (int r = 0; r < NR; ++r) hr[r] = h + (size_t)r * D;
@@ -442,14 +498,11 @@ __device__ __forceinline__ void apply_run_star(const StarParams& sp, int e0, con
     }
     const bool has = NAX != 0 || sp.has[jl] != 0;
     cplx<T> wp[2], wm[2];
-    int il = e0, ir = e0;
     if (has) {
       const int hl = sp.half[jl];
       const T dp[2] = {(ibl == hl) ? T(Nl - 1) : T(-1), (ibl + 1 == hl) ? T(Nl - 1) : T(-1)};
       const T dm[2] = {(ibl == hl - 1) ? T(1 - Nl) : T(1), (ibl + 1 == hl - 1) ? T(1 - Nl) : T(1)};
       pair_weights(jl, dp, dm, wp, wm);
-      il = e0 + ((ibl == 0) ? Nl - 1 : -1);       // k - e_l of the run's first mode
-      ir = e0 + ((ibl + 2 == Nl) ? 2 - Nl : 2);   // k + e_l of its second mode
     }
     if constexpr (WM != 2) {
 #pragma unroll
@@ -463,8 +516,8 @@ __device__ __forceinline__ void apply_run_star(const StarParams& sp, int e0, con
           if (has) {
             mac<T, REALC>(a0, wm[0], hv[1]);
             mac<T, REALC>(a1, wp[1], hv[0]);
-            mac<T, REALC>(a0, wp[0], ldh<RO>(hr[r] + il));
-            mac<T, REALC>(a1, wm[1], ldh<RO>(hr[r] + ir));
+            mac<T, REALC>(a0, wp[0], ld_edge<RO>(hr[r] + he.il, he.cl, false));
+            mac<T, REALC>(a1, wm[1], ld_edge<RO>(hr[r] + he.ir, he.cr, he.zr));
           }
           acc[0][r] = a0;
           acc[1][r] = a1;
@@ -503,6 +556,14 @@ __device__ __forceinline__ void apply_run_star(const StarParams& sp, int e0, con
       }
     }
   }
+  if constexpr (WM != 2) {
+    if (he.nyq_row) {
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int r = 0; r < NR; ++r) acc[q][r] = mk<T>(0, 0);
+    }
+  }
   }
 }
 
@@ -538,6 +599,72 @@ __device__ __noinline__ void star_run_call(const StarParams* st, bool diag, int 
 // run: the digits of e0, lambda over the other axes, and for every tap along another axis its wrapped offset and
 // its mode step dk; that tap then reads RUN consecutive entries of h. The weights are formed per mode:
 //   scalar:  c_t (|lambda|^2 + dk lambda.P_j),   otherwise  lambda^T C_t (lambda + dk P_j)   (star tap on axis j).
+// (Q h)(e0 + s), s < RUN, of a half-spectrum plan with any taps, one mode and one tap at a time (kernels call it
+// as a function of its own, so that its registers do not add to the full-spectrum stencil's). For tap t the
+// neighbour k' = k - m_t is wrapped into [-N_j/2, N_j/2) per axis; a dropped Nyquist component makes it 0; a
+// negative last component makes it the conjugate of the stored mirror entry -k'. The weight is
+// lambda(k)^T C_t lambda(k') with the unmirrored k'. out[s * NR + r].
+template <typename T, bool REALC, int NR, int RUN, bool RO>
+__device__ __noinline__ void apply_run_half(const PlanDev& p, const cplx<T>* sc, int e0, const cplx<T>* h, int D,
+                                            int nrhs, cplx<T>* out) {
+  const int d = p.d, n = p.n, nc = p.ncomp, jl = n - 1;
+  for (int s = 0; s < RUN; ++s) {
+    int ib[MAXN], k[MAXN];
+    mode_digits(p, e0 + s, ib, k);
+    bool nyq_row = false;
+    for (int j = 0; j < jl; ++j) nyq_row |= ib[j] == p.nyq[j];
+    cplx<T> acc[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) acc[r] = mk<T>(0, 0);
+    if (!nyq_row) {
+      T lk[MAXD];
+#pragma unroll
+      for (int a = 0; a < MAXD; ++a) {
+        lk[a] = T(0);
+        for (int j = 0; j < n; ++j)
+          if (a < d) lk[a] = fma(pcoef<T>(p, a, j), (T)k[j], lk[a]);
+      }
+      for (int t = 0; t < p.ntaps; ++t) {
+        int kk[MAXN];
+        bool zero = false, neg = false;
+        for (int j = 0; j < n; ++j) {
+          const int Nj = p.N[j];
+          int x = k[j] - (int)p.m[t][j];
+          x = ((x % Nj) + Nj) % Nj;                 // storage index of k_j - m_j
+          x = (2 * x < Nj) ? x : x - Nj;            // signed, in [-N_j/2, N_j/2)
+          zero |= (Nj % 2 == 0) && (2 * x == -Nj);  // the dropped Nyquist mode
+          kk[j] = x;
+        }
+        if (zero) continue;
+        neg = kk[jl] < 0;
+        T l2[MAXD];
+#pragma unroll
+        for (int a = 0; a < MAXD; ++a) {
+          l2[a] = T(0);
+          for (int j = 0; j < n; ++j)
+            if (a < d) l2[a] = fma(pcoef<T>(p, a, j), (T)kk[j], l2[a]);
+        }
+        int idx = 0;
+        for (int j = 0; j < n; ++j) {
+          const int x = neg ? -kk[j] : kk[j];
+          idx += (j == jl ? x : (x < 0 ? x + p.N[j] : x)) * p.stride[j];
+        }
+        const cplx<T> c = weight_general<T>(p.kind, d, sc + t * nc, lk, l2);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          if (r < nrhs) {
+            cplx<T> v = ldh<RO>(h + (size_t)r * D + idx);
+            if (neg) v.y = -v.y;
+            mac<T, REALC>(acc[r], c, v);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) out[s * NR + r] = acc[r];
+  }
+}
+
 template <typename T, bool REALC, int NR, int RUN, bool RO = true, bool STAR = true>
 __device__ __forceinline__ void apply_run(const PlanDev& p, const cplx<T>* __restrict__ sc, int e0,
                                           const cplx<T>* h, int D, int nrhs, cplx<T> (&acc)[RUN][NR]) {
@@ -546,6 +673,10 @@ __device__ __forceinline__ void apply_run(const PlanDev& p, const cplx<T>* __res
       star_run_call<T, REALC, NR, RO>(p.star, p.kind == QP_COEF_DIAG, e0, h, D, nrhs, &acc[0][0]);
       return;
     }
+  }
+  if (p.hspec) {
+    apply_run_half<T, REALC, NR, RUN, RO>(p, sc, e0, h, D, nrhs, &acc[0][0]);
+    return;
   }
   int ib[MAXN], k[MAXN];
   mode_digits(p, e0, ib, k);

@@ -94,7 +94,9 @@ __global__ void __launch_bounds__(BLOCK) k_diag(const PlanDev* plan, int D, doub
       cn += c.x * c.x + c.y * c.y;
     }
     double mj = 0.0, mf = 0.0;
-    if (e != 0) {
+    bool nyq_row = false;   // a dropped Nyquist mode of a half-spectrum plan: not an unknown
+    for (int j = 0; j < sp.n; ++j) nyq_row |= ib[j] == sp.nyq[j];
+    if (e != 0 && !nyq_row) {
       mj = q != 0.0 ? 1.0 / q : 0.0;
       mf = cn > 0.0 ? q / cn : 0.0;
       red[0] = fmin(red[0], l2sum);
@@ -145,6 +147,8 @@ __global__ void __launch_bounds__(BLOCK) k_rhs_taps(const PlanDev* plan, int j0,
   for (int idx = threadIdx.x; idx < p.ntaps * nrhs; idx += BLOCK) {
     const int t = idx % p.ntaps, jj = idx / p.ntaps, j = j0 + jj;
     if (t == 0) continue;                      // the mean mode: F(0) = 0
+    // (a half-spectrum plan stores the modes with m_{n-1} >= 0; the others are the conjugates of their mirrors)
+    if (p.hspec && p.m[t][p.n - 1] < 0) continue;
     int e = 0;
     double lm[MAXD] = {0, 0, 0};
     for (int ax = 0; ax < p.n; ++ax) {
@@ -194,9 +198,12 @@ __global__ void __launch_bounds__(BLOCK) k_astar_taps(const PlanDev* plan, int D
   for (int t = 1 + threadIdx.x; t < p.ntaps; t += BLOCK) {
     int e = 0;
     double lneg[MAXD] = {0, 0, 0};   // lambda(-m_t)
+    // U(-m_t): stored at -m_t, or (half-spectrum plan, last component of -m_t negative) the conjugate of U(m_t)
+    const bool mirror = p.hspec && p.m[t][p.n - 1] > 0;
     for (int ax = 0; ax < p.n; ++ax) {
       const int mj = -(int)p.m[t][ax];
-      e += (mj < 0 ? mj + p.N[ax] : mj) * p.stride[ax];
+      const int sj = mirror ? -mj : mj;
+      e += (sj < 0 ? sj + p.N[ax] : sj) * p.stride[ax];
       for (int a = 0; a < d; ++a) lneg[a] = fma(p.P[a][ax], (double)mj, lneg[a]);
     }
 #pragma unroll
@@ -210,7 +217,8 @@ __global__ void __launch_bounds__(BLOCK) k_astar_taps(const PlanDev* plan, int D
             sm.x += c.x * lneg[b];
             sm.y += c.y * lneg[b];
           }
-          const double2 u = U[(size_t)j * D + e];
+          double2 u = U[(size_t)j * D + e];
+          if (mirror) u.y = -u.y;
           const double pr = sm.x * u.x - sm.y * u.y, pim = sm.x * u.y + sm.y * u.x;
           v[2 * (i * MAXD + j)] += -pim;   // i * (s u)
           v[2 * (i * MAXD + j) + 1] += pr;

@@ -63,9 +63,10 @@ __device__ __forceinline__ void vld_real(const T* p, int n, T (&v)[W]) {
 }
 
 // r = F - w (warm: w = Q U) or r = F, with r(0) = 0 and F = 0 for the right-hand sides in zero_rhs; h = M r;
-// U = 0 where zero_u. Per-thread partials vt: ||F||^2, (r, M r), ||r||^2 per right-hand side.
+// U = 0 where zero_u. Per-thread partials vt: ||F||^2, (r, M r), ||r||^2 per right-hand side (each mode weighted
+// by mode_weight: a half-spectrum entry off the plane k_{n-1} = 0 counts for its mirror too).
 template <typename T, int NR>
-__device__ __forceinline__ void vec_init(int base, int end, int D, int nrhs, bool warm, bool zero_u,
+__device__ __forceinline__ void vec_init(const UnitDev& un, int base, int end, int D, int nrhs, bool warm, bool zero_u,
                                          const int* zero_rhs, const cplx<T>* __restrict__ F, cplx<T>* __restrict__ U,
                                          cplx<T>* __restrict__ r, cplx<T>* __restrict__ h,
                                          const cplx<T>* __restrict__ w, const T* __restrict__ M, T (&vt)[3 * NR]) {
@@ -75,6 +76,9 @@ __device__ __forceinline__ void vec_init(int base, int end, int D, int nrhs, boo
     const int n = min(W, end - e);
     T m[W];
     vld_real<T, W>(M + e, n, m);
+    T wts[W];   // inner-product weights (half-spectrum units: 1 or 2; else 1)
+#pragma unroll
+    for (int s = 0; s < W; ++s) wts[s] = (T)mode_weight(un, e + s);
     cplx<T> fv[NR][W], wv[NR][W];
 #pragma unroll
     for (int k = 0; k < NR; ++k) {
@@ -96,8 +100,9 @@ __device__ __forceinline__ void vec_init(int base, int end, int D, int nrhs, boo
           if (warm && e + s != 0) x = mk<T>(f.x - wv[k][s].x, f.y - wv[k][s].y);
           rv[s] = x;
           hv[s] = mk<T>(m[s] * x.x, m[s] * x.y);
-          const T rr = fma(x.x, x.x, x.y * x.y);
-          vt[3 * k] = fma(f.x, f.x, fma(f.y, f.y, vt[3 * k]));
+          const T we = wts[s];
+          const T rr = we * fma(x.x, x.x, x.y * x.y);
+          vt[3 * k] = fma(we * f.x, f.x, fma(we * f.y, f.y, vt[3 * k]));
           vt[3 * k + 1] = fma(m[s], rr, vt[3 * k + 1]);
           vt[3 * k + 2] += rr;
         }
@@ -116,7 +121,8 @@ __device__ __forceinline__ void vec_init(int base, int end, int D, int nrhs, boo
 
 // r -= alpha w for the right-hand sides not done; partials vt: (r, M r), ||r||^2 per right-hand side.
 template <typename T, int NR>
-__device__ __forceinline__ void vec_update(int base, int end, int D, int nrhs, const int* done, const T* alpha,
+__device__ __forceinline__ void vec_update(const UnitDev& un, int base, int end, int D, int nrhs, const int* done,
+                                           const T* alpha,
                                            cplx<T>* __restrict__ r, const cplx<T>* __restrict__ w,
                                            const T* __restrict__ M, T (&vt)[2 * NR]) {
   constexpr int W = vec_width<T>();
@@ -125,6 +131,9 @@ __device__ __forceinline__ void vec_update(int base, int end, int D, int nrhs, c
     const int n = min(W, end - e);
     T m[W];
     vld_real<T, W>(M + e, n, m);
+    T wts[W];
+#pragma unroll
+    for (int s = 0; s < W; ++s) wts[s] = (T)mode_weight(un, e + s);
     cplx<T> rv[NR][W], wv[NR][W];
 #pragma unroll
     for (int k = 0; k < NR; ++k) {
@@ -142,7 +151,7 @@ __device__ __forceinline__ void vec_update(int base, int end, int D, int nrhs, c
           cplx<T>& x = rv[k][s];
           x.x = fma(-al, wv[k][s].x, x.x);
           x.y = fma(-al, wv[k][s].y, x.y);
-          const T rr = fma(x.x, x.x, x.y * x.y);
+          const T rr = wts[s] * fma(x.x, x.x, x.y * x.y);
           vt[2 * k] = fma(m[s], rr, vt[2 * k]);
           vt[2 * k + 1] += rr;
         }
