@@ -622,6 +622,10 @@ def run_ours(args, rank, world, local_rank):
                                  "jacobi_iterations": [(i["iterations"], i["outer_iterations"]) for i in infos],
                                  "max_abs_astar_diff_vs_main": float(np.abs(A3 - A).max())}
 
+    # ---- the half-spectrum storage (the scheme on the Nyquist-free modes, vectors of the modes with k_{n-1} >= 0)
+    if not args.no_variants and name == "cfg4" and world == 1:
+        variants["half_spectrum"] = half_variant(qp, inst, mode, tol, flush, stream, max(3, min(args.steps, 10)))
+
     # ---- the batched form: the 64 instances in one batched solve against the same instances one after another
     if not args.no_variants and name in ("cfg3", "cfg4") and world == 1:
         variants["batched"] = batched_variant(qp, flush, stream, max(3, min(args.steps, 10)))
@@ -713,6 +717,37 @@ def _oracle_workers(name, N):
     per = 60 * 16 * D + (200 << 20)
     cap = host_cores() if avail is None else max(1, int(0.4 * avail // per))
     return max(1, min(host_cores(), cap, 64))
+
+
+def half_variant(qp, inst, mode, tol, flush, stream, reps):
+    """Time-to-a* of the same workload on a half-spectrum plan (QP_SPECTRUM_HALF: the scheme on the Nyquist-free
+    modes, about half the stored modes), its DOF*iter/s over the stored modes, and its a* against the oracle's
+    Nyquist-free a* (tests/golden, written by the oracle only)."""
+    import torch
+    plan = qp.plan_from_instance(inst, spectrum=qp.QP_SPECTRUM_HALF)
+    for _ in range(2):
+        A, infs = qp.qp_homogenized(plan, tol=tol, mode=mode, maxit=2000)
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        A, infs = qp.qp_homogenized(plan, tol=tol, mode=mode, maxit=2000)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    t = statistics.median(ts)
+    di = sum(plan.D * (x["iterations"] + x["outer_iterations"]) for x in infs)
+    out = {"what": "QP_SPECTRUM_HALF plan: Nyquist-free modes, %d stored of %d" % (plan.D, inst.D),
+           "time_to_astar_ms": round(t, 4), "dof_iter_per_s_stored": di / (t / 1e3),
+           "iterations": [(x["iterations"], x["outer_iterations"]) for x in infs],
+           "max_rel_residual": max(x["rel_residual"] for x in infs), "astar": np.round(A.real, 14).tolist()}
+    g = golden("cfg4_half") if tuple(inst.N) == tuple(W.cfg4().N) else None
+    if g is not None:
+        ref = np.array(g["astar_re"])
+        out["astar_vs_oracle_nyquist_free"] = float(np.abs(A.real - ref).max() / np.abs(ref).max())
+    qp.qp_plan_destroy(plan)
+    return out
 
 
 def batched_variant(qp, flush, stream, reps):
