@@ -202,10 +202,13 @@ struct qp_batch {
   double* small = nullptr;     // device a* outputs (2 d^2 per plan)
   double* h_small = nullptr;
   size_t small_bytes = 0;
+  PlanJob* jobs = nullptr;     // device table of the taps plans' right-hand-side / a* jobs
+  int njobs = 0, jobs_mc = 1;  // their count and largest coefficient table (ntaps * ncomp)
   ~qp_batch() {
     cudaDeviceSynchronize();
     delete solver;
     dev_free(small);
+    dev_free(jobs);
     pinned_free(h_small, small_bytes);
     dev_trim();
   }
@@ -413,6 +416,26 @@ void build_star_weights(qp_plan* p, cudaStream_t s) {
   CK_LAUNCH();
   // the device copy of the StarParams (read by batches of several plans) points at the table too
   CK(cudaMemcpyAsync(p->star_dev, &p->star_host, sizeof(StarParams), cudaMemcpyHostToDevice, s));
+}
+
+// The same for a plan with general taps (not star-1): its FP64 entries Q_ij per (sorted tap, mode), [ntaps][D], formed
+// by the general stencil's own arithmetic, read by every FP64 apply of the plan (single or batched). Built when the plan
+// has FP64 vectors, stores the full spectrum and the table takes at most a quarter of the free device memory.
+int last_axis_run(const qp_plan* p);
+
+void build_gen_weights(qp_plan* p, cudaStream_t s) {
+  PlanDev& pd = p->host_pd;
+  if (pd.star1 || p->backend != QP_BACKEND_TAPS || !(p->precisions & 1) || pd.hspec) return;
+  const size_t bytes = (size_t)pd.ntaps * (size_t)p->D * (p->real_coef ? sizeof(double) : sizeof(double2));
+  size_t fr = 0, tot = 0;
+  CK(cudaMemGetInfo(&fr, &tot));
+  if (bytes > fr / 4) return;
+  void* w = p->dalloc(bytes);
+  launch_gen_weights(p->pd, p->real_coef, p->coef_count, p->D, last_axis_run(p), w, s);
+  CK_LAUNCH();
+  pd.wgen = w;
+  pd.wgen_real = p->real_coef ? 1 : 0;
+  CK(cudaMemcpyAsync(p->pd, &pd, sizeof(PlanDev), cudaMemcpyHostToDevice, s));
 }
 
 // QP_BACKEND_AUTO with a tap coefficient: the stencil and the FFT backend are both exact for it (the taps are a
@@ -1268,6 +1291,7 @@ qp_status qp_plan_create(int d, int n, const double* P, const int* N, const qp_c
                 p->small, p->nblk, false, s);
     CK_LAUNCH();
     build_star_weights(p.get(), s);
+    build_gen_weights(p.get(), s);
   } else {
     CK(cudaMemcpyAsync(p->pd, &p->host_pd, sizeof(PlanDev), cudaMemcpyHostToDevice, s));
     if (!p->fft) {   // (AUTO with taps that the FFT backend applies faster: made and transformed already)
@@ -1313,7 +1337,7 @@ qp_status qp_plan_query(const qp_plan* p, qp_plan_info* info) {
   info->min_abs_lambda = p->min_abs_lambda;
   info->device_bytes = p->bytes + (p->fft ? fft_plan_bytes(p->fft) : 0);
   info->star = p->host_pd.star1;
-  info->stored_weights = p->w64 ? 1 : 0;
+  info->stored_weights = (p->w64 != nullptr || p->host_pd.wgen != nullptr) ? 1 : 0;
   API_END
 }
 
@@ -1438,6 +1462,21 @@ qp_status qp_batch_create(int count, qp_plan* const* plans, qp_batch** out) {
   b->small = (double*)dev_alloc(tot * sizeof(double), nullptr);
   b->small_bytes = tot * sizeof(double);
   b->h_small = (double*)pinned_alloc(b->small_bytes);
+  // the taps plans' right-hand sides and a* reductions run as one launch each over all of them
+  std::vector<PlanJob> jobs;
+  int off = 0;
+  for (qp_plan* p : b->plans) {
+    if (p->backend == QP_BACKEND_TAPS) {
+      jobs.push_back(PlanJob{p->pd, p->D, p->d, p->v64.F, p->v64.X, b->small + off});
+      b->jobs_mc = std::max(b->jobs_mc, p->coef_count);
+    }
+    off += 2 * p->d * p->d;
+  }
+  b->njobs = (int)jobs.size();
+  if (b->njobs) {
+    b->jobs = (PlanJob*)dev_alloc(jobs.size() * sizeof(PlanJob), nullptr);
+    CK(cudaMemcpy(b->jobs, jobs.data(), jobs.size() * sizeof(PlanJob), cudaMemcpyHostToDevice));
+  }
   CK(cudaStreamSynchronize(nullptr));
   *out = b.release();
   API_END
@@ -1460,15 +1499,24 @@ qp_status qp_batch_homogenized(qp_batch* b, const qp_solve_opts* opts, double* A
     if (p->backend == QP_BACKEND_TAPS) {
       us.all_real = us.all_real && p->real_coef;
       us.max_coef = std::max(us.max_coef, p->coef_count);
+    } else {
+      corrector_rhs(p, 0, p->d, p->v64.F, s);
     }
-    corrector_rhs(p, 0, p->d, p->v64.F, s);
+  }
+  if (b->njobs) {
+    launch_rhs_taps_multi(b->jobs, b->njobs, b->jobs_mc, s);
+    CK_LAUNCH();
   }
   SolveResult r;
   solve_units(b->solver, us, *opts, false, s, r);
   int off = 0;
   for (qp_plan* p : b->plans) {
-    astar_launch(p, p->v64.X, b->small + off, s);
+    if (p->backend != QP_BACKEND_TAPS) astar_launch(p, p->v64.X, b->small + off, s);
     off += 2 * p->d * p->d;
+  }
+  if (b->njobs) {
+    launch_astar_taps_multi(b->jobs, b->njobs, b->jobs_mc, s);
+    CK_LAUNCH();
   }
   CK(cudaMemcpyAsync(b->h_small, b->small, off * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));

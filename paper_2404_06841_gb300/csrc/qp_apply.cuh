@@ -17,7 +17,7 @@ __device__ __forceinline__ void apply_chunk(const PlanDev& sp, const cplx<T>* sc
                                             const UnitDev& un, int cl, int D, int nrhs, int refine, bool fft_unit,
                                             const cplx<T>* src, cplx<T>* dst, const cplx<T>* F, T (&vt)[NV]) {
   int start, stride, limit;
-  chunk_runs(un, cl, RUN, start, stride, limit);
+  chunk_runs<T>(un, cl, RUN, start, stride, limit);
   for (int e0 = start; e0 < limit; e0 += stride) {
     cplx<T> acc[RUN][NR];
     if (EPI == EPI_RESIDUAL && refine == REFINE_ZERO_U) {

@@ -153,12 +153,15 @@ __device__ __forceinline__ cplx<T> weight_general(int kind, int d, const cplx<T>
   return r;
 }
 
-// Blocks of the FP32 star-1 apply resident at one time on GB300 (152 SMs x 4): the width of one sweep below.
-constexpr int SWEEP_CHUNKS = 152 * 4;
+// Width of one sweep below, in chunks: the FP32 applies of large units (the compiled-in-geometry star-1 kernel runs two
+// blocks per SM) sweep 152 x 2 chunks at a time: with 608 the batched FP32 apply at 14^6 read 359 MB from DRAM for
+// 181 MB of vectors, with 304 it reads 208 MB. The FP64 applies, bound by FP64 arithmetic, keep 608 (the cfg4 FP64
+// residual took 11.7 ms in three applies with 304 against 10.3 ms with 608).
+template <typename T> __host__ __device__ constexpr int sweep_chunks() { return sizeof(T) == 4 ? 152 * 2 : 152 * 4; }
 
 // The stencil runs (RUN modes, one per thread and step) of chunk cl of a unit, as e0 = start, start + stride, ...
 // below limit. A chunk of fewer than four segments (segment: RUN x BLOCK modes) is its contiguous range of modes.
-// Larger chunks go in waves of SWEEP_CHUNKS consecutive chunks (the blocks resident together); wave w takes a
+// Larger chunks go in waves of SWEEP_CHUNKS consecutive chunks (about the blocks resident together); wave w takes a
 // contiguous share of the unit's segments, in proportion to its chunks, and its chunk p the segments
 // s0 + p, s0 + p + rw, s0 + p + 2 rw, ... of that share (rw: the wave's chunks). The resident blocks then sweep
 // one contiguous window together and the stencil's reads along the outer axes hit L2 (contiguous chunks of 13,824
@@ -166,7 +169,9 @@ constexpr int SWEEP_CHUNKS = 152 * 4;
 // whole unit left each of the two waves at 14^6 sweeping every other segment of it: 277 MB read per batched FP32
 // apply, against 215 MB in waves and 208 MB for the plain apply). A unit of at most SWEEP_CHUNKS chunks is one
 // wave: segments cl, cl + nchunk, cl + 2 nchunk, ...
+template <typename T>
 __device__ __forceinline__ void chunk_runs(const UnitDev& un, int cl, int run, int& start, int& stride, int& limit) {
+  constexpr int SWEEP_CHUNKS = sweep_chunks<T>();
   const int seg = run * BLOCK;
   if (un.chunk >= 4 * seg) {
     const int nseg = (un.D + seg - 1) / seg;

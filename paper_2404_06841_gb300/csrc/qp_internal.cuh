@@ -176,6 +176,10 @@ struct alignas(16) PlanDev {
   int Nst[MAXN];
   int nyq[MAXN];
   int hspec, Hl, pad_h0, pad_h1;   // hspec: half-spectrum storage (QP_SPECTRUM_HALF); Hl = ceil(N_{n-1} / 2)
+  // the stored FP64 stiffness entries of a plan with general taps, [tap (sorted)][D] (real: double, else double2),
+  // which FP64 applies read instead of forming the weights; null if not stored
+  const void* wgen;
+  int wgen_real, pad_w0, pad_w1, pad_w2;
 };
 static_assert(sizeof(PlanDev) % 16 == 0, "PlanDev is copied to shared memory in 16-byte words");
 
@@ -307,6 +311,9 @@ void launch_apply(const BatchDev& b, bool realc, int mc, int maxr, int level, in
 template <typename T>
 void launch_apply_plain(const PlanDev* plan_dev, bool realc, int mc, int D, int nrhs, const cplx<T>* h, cplx<T>* w,
                         int run, const StarParams* st1, int kind, cudaStream_t s);
+// Writes a general-taps plan's FP64 weights per (sorted tap, mode) to out: [ntaps][D] complex (double when realc);
+// run: the plan's stencil run (2 for an even stored last axis, else 1).
+void launch_gen_weights(const PlanDev* plan_dev, bool realc, int mc, int D, int run, void* out, cudaStream_t s);
 // Writes a star-1 plan's FP64 weights per (tap slot, mode) to out: [1 + 2n][D] complex (double when realc).
 void launch_star_weights(const StarParams& st, bool realc, int kind, int D, void* out, cudaStream_t s);
 // with_frob: also the Frobenius-optimal diagonal (else frob / frob32 are not written).
@@ -314,6 +321,16 @@ void launch_diag(const PlanDev* plan_dev, int mc, int D, double* jac, double* fr
                  double* partials, unsigned* counter, double* out, int nblk, bool with_frob, cudaStream_t s);
 void launch_rhs_taps(const PlanDev* plan_dev, int mc, int j0, int nrhs, int D, double2* F, cudaStream_t s);
 void launch_astar_taps(const PlanDev* plan_dev, int mc, int D, const double2* U, double* out, cudaStream_t s);
+// One taps plan's part of a batch's corrector right-hand sides and a* reduction (one block each).
+struct PlanJob {
+  const PlanDev* plan;
+  int D, nrhs;
+  double2* F;          // its right-hand sides (zeroed beforehand)
+  const double2* U;    // its corrector solutions
+  double* out;         // its a*: 2 d^2 doubles
+};
+void launch_rhs_taps_multi(const PlanJob* jobs, int njobs, int mc, cudaStream_t s);
+void launch_astar_taps_multi(const PlanJob* jobs, int njobs, int mc, cudaStream_t s);
 
 // ---- PCG kernels (qp_pcg.cu)
 void launch_level_reset(const BatchDev& b, int which, cudaStream_t s);

@@ -142,7 +142,7 @@ __device__ __forceinline__ void ph_apply(const BatchDev& b, const UnitDev& un, i
   for (int q = 0; q < NV; ++q) vt[q] = T(0);
   constexpr int PRUN = prun<T>();
   int start, stride, limit;
-  chunk_runs(un, c - un.chunk0, PRUN, start, stride, limit);   // the graph form's runs of this chunk
+  chunk_runs<T>(un, c - un.chunk0, PRUN, start, stride, limit);   // the graph form's runs of this chunk
   for (int e0 = start; e0 < limit; e0 += stride) {
     cplx<T> acc[PRUN][NR];
     if (zero_src) {   // src = 0: Q src = 0

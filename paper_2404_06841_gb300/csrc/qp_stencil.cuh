@@ -665,10 +665,26 @@ __device__ __noinline__ void apply_run_half(const PlanDev& p, const cplx<T>* sc,
   }
 }
 
-template <typename T, bool REALC, int NR, int RUN, bool RO = true, bool STAR = true>
+// Stored FP64 entries of a general-taps plan (PlanDev.wgen): the weight of sorted tap t at mode e.
+template <bool REALC>
+__device__ __forceinline__ double2 wgen_load(const PlanDev& p, int t, int e, int D) {
+  if (REALC || p.wgen_real) return make_double2(__ldg(static_cast<const double*>(p.wgen) + (size_t)t * D + e), 0.0);
+  return __ldg(static_cast<const double2*>(p.wgen) + (size_t)t * D + e);
+}
+template <bool REALC>
+__device__ __forceinline__ void wgen_store(void* out, int t, int e, int D, double2 c) {
+  if (REALC) static_cast<double*>(out)[(size_t)t * D + e] = c.x;
+  else static_cast<double2*>(out)[(size_t)t * D + e] = c;
+}
+
+// WM (general taps; T = double): 0 the weights are formed; 1 they are read from p.wgen (chosen at run time when the
+// plan stores them); 2 they are formed and written to wout, nothing else is done (the stencil's own arithmetic, so
+// stored and formed weights agree bit for bit).
+template <typename T, bool REALC, int NR, int RUN, bool RO = true, bool STAR = true, int WM = 0>
 __device__ __forceinline__ void apply_run(const PlanDev& p, const cplx<T>* __restrict__ sc, int e0,
-                                          const cplx<T>* h, int D, int nrhs, cplx<T> (&acc)[RUN][NR]) {
-  if constexpr (RUN == 2 && STAR) {
+                                          const cplx<T>* h, int D, int nrhs, cplx<T> (&acc)[RUN][NR],
+                                          void* wout = nullptr) {
+  if constexpr (RUN == 2 && STAR && WM != 2) {
     if (p.star1) {   // the plan's StarParams read from global memory (L1-resident across the block)
       star_run_call<T, REALC, NR, RO>(p.star, p.kind == QP_COEF_DIAG, e0, h, D, nrhs, &acc[0][0]);
       return;
@@ -678,6 +694,22 @@ __device__ __forceinline__ void apply_run(const PlanDev& p, const cplx<T>* __res
     apply_run_half<T, REALC, NR, RUN, RO>(p, sc, e0, h, D, nrhs, &acc[0][0]);
     return;
   }
+  if constexpr (sizeof(T) == 8 && WM == 0) {
+    if (p.wgen) {
+      apply_run<T, REALC, NR, RUN, RO, STAR, 1>(p, sc, e0, h, D, nrhs, acc);
+      return;
+    }
+  }
+  // the weight of sorted tap t at mode e0 + s: read (WM 1), or the formed value, also stored (WM 2)
+  auto wsel = [&](int t, int s, const cplx<T>& formed) -> cplx<T> {
+    if constexpr (WM == 1) {
+      const double2 c = wgen_load<REALC>(p, t, e0 + s, D);
+      return mk<T>((T)c.x, (T)c.y);
+    } else {
+      if constexpr (WM == 2) wgen_store<REALC>(wout, t, e0 + s, D, make_double2((double)formed.x, (double)formed.y));
+      return formed;
+    }
+  };
   int ib[MAXN], k[MAXN];
   mode_digits(p, e0, ib, k);
   const int d = p.d, kind = p.kind, nc = p.ncomp, n = p.n;
@@ -726,16 +758,20 @@ __device__ __forceinline__ void apply_run(const PlanDev& p, const cplx<T>* __res
     cplx<T> c[RUN];
 #pragma unroll
     for (int s = 0; s < RUN; ++s) {
-      if (scalar) {
-        c[s].x = sc[0].x * lam2[s];
-        c[s].y = REALC ? T(0) : sc[0].y * lam2[s];
-      } else {
-        c[s] = weight_general<T>(kind, d, sc, lk[s], lk[s]);
+      cplx<T> f = mk<T>(0, 0);
+      if constexpr (WM != 1) {
+        if (scalar) {
+          f.x = sc[0].x * lam2[s];
+          f.y = REALC ? T(0) : sc[0].y * lam2[s];
+        } else {
+          f = weight_general<T>(kind, d, sc, lk[s], lk[s]);
+        }
       }
+      c[s] = wsel(0, s, f);
     }
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
-      if (r < nrhs) {
+      if (WM != 2 && r < nrhs) {
         cplx<T> hv[RUN];
         ld_run<RO, T, RUN>(hr[r] + e0, hv);
 #pragma unroll
@@ -770,20 +806,24 @@ __device__ __forceinline__ void apply_run(const PlanDev& p, const cplx<T>* __res
         cplx<T> c[RUN];
 #pragma unroll
         for (int s = 0; s < RUN; ++s) {
-          if (scalar) {
-            const T w = fma(dk, lp[s], lam2[s]);
-            c[s].x = ct[0].x * w;
-            c[s].y = REALC ? T(0) : ct[0].y * w;
-          } else {
-            T l2[MAXD];
+          cplx<T> f = mk<T>(0, 0);
+          if constexpr (WM != 1) {
+            if (scalar) {
+              const T w = fma(dk, lp[s], lam2[s]);
+              f.x = ct[0].x * w;
+              f.y = REALC ? T(0) : ct[0].y * w;
+            } else {
+              T l2[MAXD];
 #pragma unroll
-            for (int a = 0; a < MAXD; ++a) l2[a] = (a < d) ? fma(dk, pj[a], lk[s][a]) : T(0);
-            c[s] = weight_general<T>(kind, d, ct, lk[s], l2);
+              for (int a = 0; a < MAXD; ++a) l2[a] = (a < d) ? fma(dk, pj[a], lk[s][a]) : T(0);
+              f = weight_general<T>(kind, d, ct, lk[s], l2);
+            }
           }
+          c[s] = wsel(t, s, f);
         }
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
-          if (r < nrhs) {
+          if (WM != 2 && r < nrhs) {
             cplx<T> hv[RUN];
             ld_run<RO, T, RUN>(hr[r] + e2, hv);
 #pragma unroll
@@ -817,20 +857,23 @@ __device__ __forceinline__ void apply_run(const PlanDev& p, const cplx<T>* __res
         ib2 -= (ib2 >= Nl) ? Nl : 0;
         const int k2 = (2 * ib2 < Nl) ? ib2 : ib2 - Nl;
         const T dk = (T)(k2 - kl[s]);
-        cplx<T> c;
-        if (scalar) {
-          const T w = fma(dk, lp[s], lam2[s]);
-          c.x = ct[0].x * w;
-          c.y = REALC ? T(0) : ct[0].y * w;
-        } else {
-          T l2[MAXD];
+        cplx<T> f = mk<T>(0, 0);
+        if constexpr (WM != 1) {
+          if (scalar) {
+            const T w = fma(dk, lp[s], lam2[s]);
+            f.x = ct[0].x * w;
+            f.y = REALC ? T(0) : ct[0].y * w;
+          } else {
+            T l2[MAXD];
 #pragma unroll
-          for (int a = 0; a < MAXD; ++a) l2[a] = (a < d) ? fma(dk, pl[a], lk[s][a]) : T(0);
-          c = weight_general<T>(kind, d, ct, lk[s], l2);
+            for (int a = 0; a < MAXD; ++a) l2[a] = (a < d) ? fma(dk, pl[a], lk[s][a]) : T(0);
+            f = weight_general<T>(kind, d, ct, lk[s], l2);
+          }
         }
+        const cplx<T> c = wsel(t, s, f);
 #pragma unroll
         for (int r = 0; r < NR; ++r)
-          if (r < nrhs) mac<T, REALC>(acc[s][r], c, ldh<RO>(hr[r] + row0 + ib2));
+          if (WM != 2 && r < nrhs) mac<T, REALC>(acc[s][r], c, ldh<RO>(hr[r] + row0 + ib2));
       }
     }
   }
@@ -865,13 +908,17 @@ __device__ __forceinline__ void apply_run(const PlanDev& p, const cplx<T>* __res
       ib2 -= (ib2 >= Nl) ? Nl : 0;
       const int k2 = (2 * ib2 < Nl) ? ib2 : ib2 - Nl;
       const T dk = (T)(k2 - kl[s]);
-      T l2[MAXD];
+      cplx<T> f = mk<T>(0, 0);
+      if constexpr (WM != 1) {
+        T l2[MAXD];
 #pragma unroll
-      for (int a = 0; a < MAXD; ++a) l2[a] = (a < d) ? fma(dk, pcoef<T>(p, a, jl), lk[s][a] + lo[a]) : T(0);
-      const cplx<T> c = weight_general<T>(kind, d, ct, lk[s], l2);
+        for (int a = 0; a < MAXD; ++a) l2[a] = (a < d) ? fma(dk, pcoef<T>(p, a, jl), lk[s][a] + lo[a]) : T(0);
+        f = weight_general<T>(kind, d, ct, lk[s], l2);
+      }
+      const cplx<T> c = wsel(t, s, f);
 #pragma unroll
       for (int r = 0; r < NR; ++r)
-        if (r < nrhs) mac<T, REALC>(acc[s][r], c, ldh<RO>(hr[r] + eo + ib2));
+        if (WM != 2 && r < nrhs) mac<T, REALC>(acc[s][r], c, ldh<RO>(hr[r] + eo + ib2));
     }
   }
 }

@@ -42,6 +42,33 @@ void launch_apply(const BatchDev& b, bool realc, int mc, int maxr, int level, in
 
 // ------------------------------------------------------------------------------------------------ set-up kernels
 
+// The stored FP64 entries of a plan with general taps: every tap's weight at every mode ([tap][D], real or complex),
+// formed by the general stencil's own arithmetic (apply_run with WM = 2), one run of modes per thread.
+template <bool REALC, int RUN>
+__global__ void __launch_bounds__(BLOCK) k_gen_weights(const PlanDev* plan, int D, void* out) {
+  __shared__ __align__(16) PlanDev sp;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double2* scoef = reinterpret_cast<double2*>(smraw);
+  load_plan<double>(plan, sp, scoef);
+  const int e0 = (blockIdx.x * BLOCK + threadIdx.x) * RUN;
+  if (e0 >= D) return;
+  double2 acc[RUN][1];
+  apply_run<double, REALC, 1, RUN, true, false, 2>(sp, scoef, e0, nullptr, D, 0, acc, out);
+}
+
+void launch_gen_weights(const PlanDev* plan_dev, bool realc, int mc, int D, int run, void* out, cudaStream_t s) {
+  const size_t smem = (size_t)mc * sizeof(double2);
+  const int nblk = (D / run + BLOCK - 1) / BLOCK;
+  if (run == 2) {
+    if (realc) k_gen_weights<true, 2><<<nblk, BLOCK, smem, s>>>(plan_dev, D, out);
+    else k_gen_weights<false, 2><<<nblk, BLOCK, smem, s>>>(plan_dev, D, out);
+  } else {
+    if (realc) k_gen_weights<true, 1><<<nblk, BLOCK, smem, s>>>(plan_dev, D, out);
+    else k_gen_weights<false, 1><<<nblk, BLOCK, smem, s>>>(plan_dev, D, out);
+  }
+  count_launch();
+}
+
 // lambda(k + m) for the tap with mode m (any number of nonzero axes), from the digits of k.
 __device__ __forceinline__ void lambda_shift(const PlanDev& p, const int (&ib)[MAXN], const int (&k)[MAXN],
                                              const signed char* m, int sign, const double (&lk)[MAXD],
@@ -137,8 +164,8 @@ void launch_diag(const PlanDev* plan_dev, int mc, int D, double* jac, double* fr
 }
 
 // Corrector right-hand sides on the taps backend: F_j = 0 except at the tap modes m != 0, where
-// F_j(m) = i sum_a lambda_a(m) A~^{aj}_m (Sec. 5.2 eq. corrector; App. D). F is zeroed beforehand.
-__global__ void __launch_bounds__(BLOCK) k_rhs_taps(const PlanDev* plan, int j0, int nrhs, int D, double2* F) {
+// F_j(m) = i sum_a lambda_a(m) A~^{aj}_m (Sec. 5.2 eq. corrector; App. D). F is zeroed beforehand. One block.
+__device__ __forceinline__ void rhs_taps_block(const PlanDev* plan, int j0, int nrhs, int D, double2* F) {
   __shared__ __align__(16) PlanDev sp;
   extern __shared__ __align__(16) unsigned char smraw[];
   double2* scoef = reinterpret_cast<double2*>(smraw);
@@ -170,16 +197,40 @@ __global__ void __launch_bounds__(BLOCK) k_rhs_taps(const PlanDev* plan, int j0,
   }
 }
 
+__global__ void __launch_bounds__(BLOCK) k_rhs_taps(const PlanDev* plan, int j0, int nrhs, int D, double2* F) {
+  rhs_taps_block(plan, j0, nrhs, D, F);
+}
+
+// The right-hand sides of several plans, one block per plan (jobs: device table).
+__global__ void __launch_bounds__(BLOCK) k_rhs_taps_multi(const PlanJob* jobs) {
+  const PlanJob& j = jobs[blockIdx.x];
+  rhs_taps_block(j.plan, 0, j.nrhs, j.D, j.F);
+}
+
 void launch_rhs_taps(const PlanDev* plan_dev, int mc, int j0, int nrhs, int D, double2* F, cudaStream_t s) {
   k_rhs_taps<<<1, BLOCK, (size_t)mc * sizeof(double2), s>>>(plan_dev, j0, nrhs, D, F);
   count_launch();
 }
 
+// F = 0 over every job's nrhs x D right-hand sides (blockIdx.y: job).
+__global__ void __launch_bounds__(BLOCK) k_zero_rhs_multi(const PlanJob* jobs) {
+  const PlanJob& j = jobs[blockIdx.y];
+  const size_t n = (size_t)j.nrhs * j.D;
+  for (size_t i = (size_t)blockIdx.x * BLOCK + threadIdx.x; i < n; i += (size_t)gridDim.x * BLOCK)
+    j.F[i] = make_double2(0.0, 0.0);
+}
+
+void launch_rhs_taps_multi(const PlanJob* jobs, int njobs, int mc, cudaStream_t s) {
+  k_zero_rhs_multi<<<dim3(16, njobs), BLOCK, 0, s>>>(jobs);
+  k_rhs_taps_multi<<<njobs, BLOCK, (size_t)mc * sizeof(double2), s>>>(jobs);
+  count_launch(2);
+}
+
 // A*_ij = A~^{ij}_0 + i sum_k sum_b A~^{ib}_{-k} lambda_b(k) U_j(k): on the taps backend only k = -m_t
 // contribute. One thread per tap computes its d x d terms; a fixed-order block reduction sums them.
-// out: (re, im) per entry, row-major.
-__global__ void __launch_bounds__(BLOCK) k_astar_taps(const PlanDev* plan, int D, const double2* __restrict__ U,
-                                                      double* out) {
+// out: (re, im) per entry, row-major. One block.
+__device__ __forceinline__ void astar_taps_block(const PlanDev* plan, int D, const double2* __restrict__ U,
+                                                 double* out) {
   __shared__ __align__(16) PlanDev sp;
   extern __shared__ __align__(16) unsigned char smraw[];
   double2* scoef = reinterpret_cast<double2*>(smraw);
@@ -237,8 +288,24 @@ __global__ void __launch_bounds__(BLOCK) k_astar_taps(const PlanDev* plan, int D
   }
 }
 
+__global__ void __launch_bounds__(BLOCK) k_astar_taps(const PlanDev* plan, int D, const double2* __restrict__ U,
+                                                      double* out) {
+  astar_taps_block(plan, D, U, out);
+}
+
+// a* of several plans, one block per plan (jobs: device table).
+__global__ void __launch_bounds__(BLOCK) k_astar_taps_multi(const PlanJob* jobs) {
+  const PlanJob& j = jobs[blockIdx.x];
+  astar_taps_block(j.plan, j.D, j.U, j.out);
+}
+
 void launch_astar_taps(const PlanDev* plan_dev, int mc, int D, const double2* U, double* out, cudaStream_t s) {
   k_astar_taps<<<1, BLOCK, (size_t)mc * sizeof(double2), s>>>(plan_dev, D, U, out);
+  count_launch();
+}
+
+void launch_astar_taps_multi(const PlanJob* jobs, int njobs, int mc, cudaStream_t s) {
+  k_astar_taps_multi<<<njobs, BLOCK, (size_t)mc * sizeof(double2), s>>>(jobs);
   count_launch();
 }
 

@@ -157,11 +157,35 @@ def test_fixed_geometry_solves_are_the_general_ones(qp, d, n, N, kind, real):
 
 
 def test_general_taps_are_not_star(qp):
+    """General taps take the general stencil; with FP64 vectors the plan stores their FP64 entries per (tap, mode)
+    (read by its FP64 applies), without them it stores none."""
     inst = W.random_instance(2, 3, (6, 4, 8), "sym", "taps", seed=23)
     info = qp.qp_plan_query(qp.plan_from_instance(inst))
+    assert not info["star"] and info["stored_weights"]
+    info = qp.qp_plan_query(qp.plan_from_instance(inst, precisions=2))
     assert not info["star"] and not info["stored_weights"]
     inst = W.random_instance(2, 3, (6, 4, 8), "scalar", "taps", seed=24)   # taps off the axes (|m|_inf <= 1)
     assert not qp.qp_plan_query(qp.plan_from_instance(inst))["star"]
+
+
+@pytest.mark.parametrize("kind,seed", [("sym", 31), ("scalar", 32), ("diag", 33)])
+def test_general_taps_stored_fp64_entries_equal_formed(qp, kind, seed):
+    """The FP64 apply of a general-taps plan reads its stored entries; a plan without FP64 solve workspace forms
+    them (precisions = FP32 solve only still allows FP64 applies): bit for bit the same Q h, and the oracle's."""
+    inst = W.random_instance(2, 4, (6, 4, 6, 8), kind, "taps", seed=seed, radius=1)
+    p_stored = qp.plan_from_instance(inst)
+    p_formed = qp.plan_from_instance(inst, precisions=2)
+    assert qp.qp_plan_query(p_stored)["stored_weights"] and not qp.qp_plan_query(p_formed)["stored_weights"]
+    rng = np.random.default_rng(seed)
+    h = rng.standard_normal((2,) + inst.N) + 1j * rng.standard_normal((2,) + inst.N)
+    ht = torch.from_numpy(h).cuda()
+    w1, w2 = torch.empty_like(ht), torch.empty_like(ht)
+    qp.qp_apply_stiffness(p_stored, ht, w1, qp.QP_FP64)
+    qp.qp_apply_stiffness(p_formed, ht, w2, qp.QP_FP64)
+    assert torch.equal(w1, w2)
+    op = O.Operator(inst)
+    ref = np.stack([op(h[r]) for r in range(2)])
+    assert np.abs(w1.cpu().numpy() - ref).max() <= 1e-13 * np.abs(ref).max()
 
 
 def test_misaligned_vectors_are_rejected_before_any_launch(qp):
