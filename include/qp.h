@@ -219,7 +219,8 @@ qp_status qp_pcg_solve_taps_static(int d, int n, const double* P, const int* N, 
  * of Q; QP_PRECOND_FROBENIUS gives the Frobenius-optimal M(k) = q(k)/||Q e_k||^2 (eq. preconditioner): on the taps
  * backend from the O(gD) column sums, on the FFT backend from FFT cross-correlations of lambda_a lambda_a' with
  * A~^{ab} conj(A~^{a'b'}) (d^4 + d(d+1) FP64 n-dim DFTs plus ~(5 + d(d+1)/2) x 16 B x D of temporary device memory);
- * on either backend done once, on this call or the first Frobenius solve. M(0) = 0 (the excluded mode). out: device double[D].
+ * on either backend done once, on this call or the first Frobenius solve. M(0) = 0 (the excluded mode). out: device
+ * double[stored length] (D; D_h for a QP_SPECTRUM_HALF plan, which has the Jacobi diagonal only, 0 at dropped modes).
  * Synchronises stream. */
 qp_status qp_plan_diagonal(qp_plan* plan, int precond, double* out, void* stream);
 

@@ -12,12 +12,16 @@ namespace qp {
 // of RUN consecutive modes chunk_runs gives it.
 // SK: the stencil's data source: 0 the plan in shared memory (apply_run), 1 / 2 the star-1 stencil of a scalar /
 // diagonal coefficient from st (a kernel parameter).
-template <typename T, int EPI, bool REALC, int NR, int RUN, int NV, int SK = 0, int NAX = 0, int DC = 0>
+template <typename T, int EPI, bool REALC, int NR, int RUN, int NV, int SK = 0, int NAX = 0, int DC = 0,
+          bool HSP = false>
 __device__ __forceinline__ void apply_chunk(const PlanDev& sp, const cplx<T>* scoef, const StarParams& st,
                                             const UnitDev& un, int cl, int D, int nrhs, int refine, bool fft_unit,
                                             const cplx<T>* src, cplx<T>* dst, const cplx<T>* F, T (&vt)[NV]) {
   int start, stride, limit;
   chunk_runs<T>(un, cl, RUN, start, stride, limit);
+  // half-spectrum units weigh each mode 1 or 2 in the sums (mode_weight); the star-1 kernels are compiled per
+  // storage, so the full-spectrum ones carry no weights (an FP64 multiply per term is not free)
+  const bool hw = (SK == 0 || HSP) && un.hspec;
   for (int e0 = start; e0 < limit; e0 += stride) {
     cplx<T> acc[RUN][NR];
     if (EPI == EPI_RESIDUAL && refine == REFINE_ZERO_U) {
@@ -32,7 +36,7 @@ __device__ __forceinline__ void apply_chunk(const PlanDev& sp, const cplx<T>* sc
         for (int r = 0; r < NR; ++r) acc[s][r] = (r < nrhs) ? dst[(size_t)r * D + e0 + s] : mk<T>(0, 0);
     } else if constexpr (SK != 0 && RUN == 2) {
       // FP64: the plan's stored weights; FP32: formed
-      apply_run_star<T, REALC, NR, true, SK == 2, sizeof(T) == 8 ? 1 : 0, NAX, DC>(st, e0, src, D, nrhs, acc);
+      apply_run_star<T, REALC, NR, true, SK == 2, sizeof(T) == 8 ? 1 : 0, NAX, DC, HSP>(st, e0, src, D, nrhs, acc);
     } else {
       apply_run<T, REALC, NR, RUN>(sp, scoef, e0, src, D, nrhs, acc);
     }
@@ -46,8 +50,7 @@ __device__ __forceinline__ void apply_chunk(const PlanDev& sp, const cplx<T>* sc
             *reinterpret_cast<float4*>(dst + o) = make_float4((float)acc[0][r].x, (float)acc[0][r].y,
                                                               (float)acc[1][r].x, (float)acc[1][r].y);
             if (EPI == EPI_DOT_HW) {
-              // half-spectrum units weigh each mode 1 or 2 (mode_weight; exact scaling, 1 elsewhere)
-              const T w0 = (T)mode_weight(un, e0), w1 = (T)mode_weight(un, e0 + 1);
+              const T w0 = hw ? (T)mode_weight(un, e0) : T(1), w1 = hw ? (T)mode_weight(un, e0 + 1) : T(1);
               const float4 hv = __ldg(reinterpret_cast<const float4*>(src + o));
               vt[r] = fma(w0 * (T)hv.x, acc[0][r].x, fma(w0 * (T)hv.y, acc[0][r].y, vt[r]));
               vt[r] = fma(w1 * (T)hv.z, acc[1][r].x, fma(w1 * (T)hv.w, acc[1][r].y, vt[r]));
@@ -60,7 +63,7 @@ __device__ __forceinline__ void apply_chunk(const PlanDev& sp, const cplx<T>* sc
 #pragma unroll
     for (int s = 0; s < RUN; ++s) {
       const int e = e0 + s;
-      const T we = (EPI == EPI_NONE) ? T(1) : (T)mode_weight(un, e);
+      const T we = (EPI == EPI_NONE || !hw) ? T(1) : (T)mode_weight(un, e);
 #pragma unroll
       for (int r = 0; r < NR; ++r) {
         if (r < nrhs) {
@@ -84,7 +87,7 @@ __device__ __forceinline__ void apply_chunk(const PlanDev& sp, const cplx<T>* sc
   }
 }
 
-template <typename T, int EPI, bool REALC, int NR, int SK, int NAX = 0, int DC = 0>
+template <typename T, int EPI, bool REALC, int NR, int SK, int NAX = 0, int DC = 0, bool HSP = false>
 __device__ __forceinline__ void apply_units(const BatchDev& b, int level, int refine, unsigned long long cond,
                                             const StarParams& stp) {
   __shared__ __align__(16) PlanDev sp;
@@ -132,8 +135,8 @@ __device__ __forceinline__ void apply_units(const BatchDev& b, int level, int re
     const int cl = c - un.chunk0;
     // the unit's own run length (so that its reduction order does not depend on the batch)
     if constexpr (SK != 0) {
-      apply_chunk<T, EPI, REALC, NR, 2, NV, SK, NAX, DC>(sp, scoef, stp, un, cl, D, nrhs, refine, fft_unit, src, dst,
-                                                        F, vt);
+      apply_chunk<T, EPI, REALC, NR, 2, NV, SK, NAX, DC, HSP>(sp, scoef, stp, un, cl, D, nrhs, refine, fft_unit, src,
+                                                             dst, F, vt);
     } else {
       if (un.run == 2)
         apply_chunk<T, EPI, REALC, NR, 2, NV>(sp, scoef, stp, un, cl, D, nrhs, refine, fft_unit, src, dst, F, vt);
@@ -208,10 +211,10 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 3) k_apply(BatchDe
 // stencil waits on the L2 latency of its neighbour reads: the run-time-geometry kernels run four blocks per SM (64
 // registers); the fixed-geometry ones, whose packed stencil with the chunk loop and epilogue spilled at 64 registers,
 // two (up to 128 registers).
-template <typename T, int EPI, bool REALC, int NR, int SK, int NAX = 0, int DC = 0>
+template <typename T, int EPI, bool REALC, int NR, int SK, int NAX = 0, int DC = 0, bool HSP = false>
 __global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : (NAX != 0 ? 2 : 4))
     k_apply_star(BatchDev b, int level, int refine, unsigned long long cond, const __grid_constant__ StarParams st) {
-  apply_units<T, EPI, REALC, NR, SK, NAX, DC>(b, level, refine, cond, st);
+  apply_units<T, EPI, REALC, NR, SK, NAX, DC, HSP>(b, level, refine, cond, st);
 }
 
 // Batch FP32 (h, Q h) apply of a single star-1 unit of a fixed geometry (qp_apply_fixed_batch.cu); false: not one
@@ -231,8 +234,15 @@ static void apply_launch_rc(const BatchDev& b, int level, int refine, unsigned l
     if (st1 && launch_batch_star_fixed(b, level, refine, cond, nblk, smem, *st1, REALC, NR, kind, s)) return;
   }
   if (!st1) k_apply<T, EPI, REALC, NR><<<nblk, BLOCK, smem, s>>>(b, level, refine, cond);
-  else if (kind == QP_COEF_DIAG) k_apply_star<T, EPI, REALC, NR, 2><<<nblk, BLOCK, smem, s>>>(b, level, refine, cond, *st1);
-  else k_apply_star<T, EPI, REALC, NR, 1><<<nblk, BLOCK, smem, s>>>(b, level, refine, cond, *st1);
+  else if (st1->hspec) {
+    if (kind == QP_COEF_DIAG)
+      k_apply_star<T, EPI, REALC, NR, 2, 0, 0, true><<<nblk, BLOCK, smem, s>>>(b, level, refine, cond, *st1);
+    else k_apply_star<T, EPI, REALC, NR, 1, 0, 0, true><<<nblk, BLOCK, smem, s>>>(b, level, refine, cond, *st1);
+  } else if (kind == QP_COEF_DIAG) {
+    k_apply_star<T, EPI, REALC, NR, 2><<<nblk, BLOCK, smem, s>>>(b, level, refine, cond, *st1);
+  } else {
+    k_apply_star<T, EPI, REALC, NR, 1><<<nblk, BLOCK, smem, s>>>(b, level, refine, cond, *st1);
+  }
 }
 
 // st1: the StarParams of the batch's single unit when it is a star-1 plan with an even last axis (kind its
@@ -273,13 +283,13 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 3) k_apply_plain(c
 
 // Plain apply of a star-1 plan with an even last axis: the stencil data as a kernel parameter; one run of two
 // modes per thread.
-template <typename T, bool REALC, int NR, int SK, int NAX = 0, int DC = 0>
+template <typename T, bool REALC, int NR, int SK, int NAX = 0, int DC = 0, bool HSP = false>
 __global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : (NAX != 0 ? 2 : 4))
     k_apply_plain_star(const __grid_constant__ StarParams st, int D, int nrhs, const cplx<T>* h, cplx<T>* w) {
   const int e0 = (blockIdx.x * BLOCK + threadIdx.x) * 2;
   if (e0 >= D) return;
   cplx<T> acc[2][NR];
-  apply_run_star<T, REALC, NR, true, SK == 2, sizeof(T) == 8 ? 1 : 0, NAX, DC>(st, e0, h, D, nrhs, acc);
+  apply_run_star<T, REALC, NR, true, SK == 2, sizeof(T) == 8 ? 1 : 0, NAX, DC, HSP>(st, e0, h, D, nrhs, acc);
 #pragma unroll
   for (int r = 0; r < NR; ++r) {
     if (r < nrhs) {
@@ -301,6 +311,15 @@ static void plain_star_nr(int nrhs, const StarParams& st, int D, const cplx<T>* 
     if (launch_plain_star_fixed(st, REALC, nrhs, SK == 2 ? QP_COEF_DIAG : QP_COEF_SCALAR, D, h, w, s)) return;
   }
   const int nblk = (D / 2 + BLOCK - 1) / BLOCK;
+  if (st.hspec) {
+    switch (nrhs) {
+      case 1: k_apply_plain_star<T, REALC, 1, SK, 0, 0, true><<<nblk, BLOCK, 0, s>>>(st, D, nrhs, h, w); break;
+      case 2: k_apply_plain_star<T, REALC, 2, SK, 0, 0, true><<<nblk, BLOCK, 0, s>>>(st, D, nrhs, h, w); break;
+      case 3: k_apply_plain_star<T, REALC, 3, SK, 0, 0, true><<<nblk, BLOCK, 0, s>>>(st, D, nrhs, h, w); break;
+      default: k_apply_plain_star<T, REALC, 4, SK, 0, 0, true><<<nblk, BLOCK, 0, s>>>(st, D, nrhs, h, w); break;
+    }
+    return;
+  }
   switch (nrhs) {
     case 1: k_apply_plain_star<T, REALC, 1, SK><<<nblk, BLOCK, 0, s>>>(st, D, nrhs, h, w); break;
     case 2: k_apply_plain_star<T, REALC, 2, SK><<<nblk, BLOCK, 0, s>>>(st, D, nrhs, h, w); break;
@@ -321,7 +340,8 @@ static void plain_nr(int nrhs, const PlanDev* plan_dev, int D, const cplx<T>* h,
   }
 }
 
-// The stored FP64 weights of a star-1 plan: one run of two modes per thread, the stencil's own arithmetic.
+// The stored FP64 weights of a star-1 plan: one run of two modes per thread, the stencil's own arithmetic. (The
+// weights do not depend on the storage's edge handling: one instantiation serves both storages.)
 template <bool REALC, bool DIAGK>
 __global__ void __launch_bounds__(BLOCK) k_star_weights(const __grid_constant__ StarParams st, int D, void* out) {
   const int e0 = (blockIdx.x * BLOCK + threadIdx.x) * 2;

@@ -11,7 +11,9 @@ namespace {
 template <int NAX, int DC, bool REALC, int SK>
 void batch_fixed(const BatchDev& b, int level, int refine, unsigned long long cond, int nblk, size_t smem,
                  const StarParams& st, cudaStream_t s) {
-  k_apply_star<float, EPI_DOT_HW, REALC, DC, SK, NAX, DC><<<nblk, BLOCK, smem, s>>>(b, level, refine, cond, st);
+  if (st.hspec)
+    k_apply_star<float, EPI_DOT_HW, REALC, DC, SK, NAX, DC, true><<<nblk, BLOCK, smem, s>>>(b, level, refine, cond, st);
+  else k_apply_star<float, EPI_DOT_HW, REALC, DC, SK, NAX, DC><<<nblk, BLOCK, smem, s>>>(b, level, refine, cond, st);
 }
 
 template <int NAX, int DC>

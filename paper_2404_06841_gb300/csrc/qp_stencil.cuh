@@ -140,13 +140,14 @@ struct HalfEdges {
   bool nyq_row;        // the run's modes have a dropped Nyquist digit
 };
 
+template <bool HSP>
 __device__ __forceinline__ HalfEdges half_edges(const StarParams& sp, const int (&ib)[MAXN], int n, int e0, int ibl) {
   HalfEdges he;
   const int jl = n - 1, Nsl = sp.Nst[jl];
   he.il = e0 + ((ibl == 0) ? Nsl - 1 : -1);
   he.ir = e0 + ((ibl + 2 == Nsl) ? 2 - Nsl : 2);
   he.cl = he.cr = he.zr = he.nyq_row = false;
-  if (sp.hspec) {
+  if (HSP) {
     if (ibl == 0 || ibl + 2 == Nsl) {
       int mr = 0;   // storage index of (-k_0, .., -k_{n-2}, 0)
 #pragma unroll
@@ -173,18 +174,20 @@ __device__ __forceinline__ HalfEdges half_edges(const StarParams& sp, const int 
   return he;
 }
 
-template <bool RO, typename V>
+template <bool RO, bool HSP, typename V>
 __device__ __forceinline__ V ld_edge(const V* p, bool conj, bool zero) {
   V v = ldh<RO>(p);
-  if (conj) v.y = -v.y;
-  if (zero) {
-    v.x = 0;
-    v.y = 0;
+  if (HSP) {
+    if (conj) v.y = -v.y;
+    if (zero) {
+      v.x = 0;
+      v.y = 0;
+    }
   }
   return v;
 }
 
-template <bool REALC, int NR, bool RO, int NAX = 0, int DC = 0>
+template <bool REALC, int NR, bool RO, int NAX = 0, int DC = 0, bool HSP = false>
 __device__ __forceinline__ void apply_run_star_f32(const StarParams& sp, int e0, const float2* h, int D, int nrhs,
                                                    float2 (&acc)[2][NR]) {
   const int d = DC ? DC : sp.d, n = NAX ? NAX : sp.n, jl = n - 1, Nl = sp.N[jl];
@@ -213,7 +216,7 @@ __device__ __forceinline__ void apply_run_star_f32(const StarParams& sp, int e0,
       kl0 = k[j];
     }
   const int kl1 = (2 * (ibl + 1) < Nl) ? ibl + 1 : ibl + 1 - Nl;
-  const HalfEdges he = half_edges(sp, ib, n, e0, ibl);   // k - e_l of the run's first mode, k + e_l of its second
+  const HalfEdges he = half_edges<HSP>(sp, ib, n, e0, ibl);   // k - e_l of the run's first mode, k + e_l of its second
   // broadcast pairs per mode s of the run: (q_a, q_a) and (lambda_a, lambda_a)
   float2 QQ[2][MAXD], LL[2][MAXD];
   {
@@ -300,8 +303,8 @@ __device__ __forceinline__ void apply_run_star_f32(const StarParams& sp, int e0,
         ld_run<RO, float, 2>(hr[r] + e0, v);
         mac(Pa[0][r], Sa[0][r], wm0, true, v[1]);
         mac(Pa[1][r], Sa[1][r], wp1, false, v[0]);
-        mac(Pa[0][r], Sa[0][r], wp0, false, ld_edge<RO>(hr[r] + he.il, he.cl, false));
-        mac(Pa[1][r], Sa[1][r], wm1, true, ld_edge<RO>(hr[r] + he.ir, he.cr, he.zr));
+        mac(Pa[0][r], Sa[0][r], wp0, false, ld_edge<RO, HSP>(hr[r] + he.il, he.cl, false));
+        mac(Pa[1][r], Sa[1][r], wm1, true, ld_edge<RO, HSP>(hr[r] + he.ir, he.cr, he.zr));
       }
     }
   }
@@ -335,8 +338,8 @@ __device__ __forceinline__ void apply_run_star_f32(const StarParams& sp, int e0,
   for (int s = 0; s < 2; ++s)
 #pragma unroll
     for (int r = 0; r < NR; ++r)
-      acc[s][r] = he.nyq_row ? pk(0.f, 0.f)
-                             : (REALC ? Pa[s][r] : pk(Pa[s][r].x - Sa[s][r].y, Pa[s][r].y + Sa[s][r].x));
+      acc[s][r] = (HSP && he.nyq_row) ? pk(0.f, 0.f)
+                                      : (REALC ? Pa[s][r] : pk(Pa[s][r].x - Sa[s][r].y, Pa[s][r].y + Sa[s][r].x));
 }
 
 // WM: 0 the weights are formed here; 1 (T = double) they are read from sp.w64; 2 (T = double) they are formed and
@@ -344,13 +347,15 @@ __device__ __forceinline__ void apply_run_star_f32(const StarParams& sp, int e0,
 // else is done.
 // NAX, DC (0: from sp at run time): the number of axes, every one of them with taps, and d known at compile time,
 // so that the axis loop is straight-line code whose neighbour reads the compiler can issue early.
-// FP32 with formed weights (WM = 0) takes apply_run_star_f32 above.
-template <typename T, bool REALC, int NR, bool RO, bool DIAGK, int WM = 0, int NAX = 0, int DC = 0>
+// FP32 with formed weights (WM = 0) takes apply_run_star_f32 above. HSP: compiled for half-spectrum plans (kernels
+// are instantiated for both and launched by the plan's storage, so the full-spectrum code carries none of the
+// half-spectrum edge handling).
+template <typename T, bool REALC, int NR, bool RO, bool DIAGK, int WM = 0, int NAX = 0, int DC = 0, bool HSP = false>
 __device__ __forceinline__ void apply_run_star(const StarParams& sp, int e0, const cplx<T>* h, int D, int nrhs,
                                                cplx<T> (&acc)[2][NR], void* wout = nullptr) {
   if constexpr (sizeof(T) == 4 && WM == 0) {
-    apply_run_star_f32<REALC, NR, RO, NAX, DC>(sp, e0, reinterpret_cast<const float2*>(h), D, nrhs,
-                                               reinterpret_cast<float2(&)[2][NR]>(acc));
+    apply_run_star_f32<REALC, NR, RO, NAX, DC, HSP>(sp, e0, reinterpret_cast<const float2*>(h), D, nrhs,
+                                                    reinterpret_cast<float2(&)[2][NR]>(acc));
     return;
   } else {
   constexpr int NQ = DIAGK ? MAXD : 1;   // weight terms per mode: q_a (diagonal) or q (scalar)
@@ -380,7 +385,7 @@ __device__ __forceinline__ void apply_run_star(const StarParams& sp, int e0, con
       ibl = ib[j];
       kl0 = k[j];
     }
-  const HalfEdges he = half_edges(sp, ib, n, e0, ibl);   // k - e_l of the run's first mode, k + e_l of its second
+  const HalfEdges he = half_edges<HSP>(sp, ib, n, e0, ibl);   // k - e_l of the run's first mode, k + e_l of its second
   const cplx<T>* hr[NR];
 #pragma unroll
   for (int r = 0; r < NR; ++r) hr[r] = h + (size_t)r * D;
@@ -516,8 +521,8 @@ __device__ __forceinline__ void apply_run_star(const StarParams& sp, int e0, con
           if (has) {
             mac<T, REALC>(a0, wm[0], hv[1]);
             mac<T, REALC>(a1, wp[1], hv[0]);
-            mac<T, REALC>(a0, wp[0], ld_edge<RO>(hr[r] + he.il, he.cl, false));
-            mac<T, REALC>(a1, wm[1], ld_edge<RO>(hr[r] + he.ir, he.cr, he.zr));
+            mac<T, REALC>(a0, wp[0], ld_edge<RO, HSP>(hr[r] + he.il, he.cl, false));
+            mac<T, REALC>(a1, wm[1], ld_edge<RO, HSP>(hr[r] + he.ir, he.cr, he.zr));
           }
           acc[0][r] = a0;
           acc[1][r] = a1;
@@ -556,7 +561,7 @@ __device__ __forceinline__ void apply_run_star(const StarParams& sp, int e0, con
       }
     }
   }
-  if constexpr (WM != 2) {
+  if constexpr (WM != 2 && HSP) {
     if (he.nyq_row) {
 #pragma unroll
       for (int q = 0; q < 2; ++q)
@@ -574,10 +579,16 @@ template <typename T, bool REALC, int NR, bool RO>
 __device__ __noinline__ void star_run_call(const StarParams* st, bool diag, int e0, const cplx<T>* h, int D, int nrhs,
                                            cplx<T>* out) {
   cplx<T> acc[2][NR];
+  const bool hs = st->hspec != 0;
   if constexpr (sizeof(T) == 8) {
     if (st->w64 != nullptr) {
-      if (diag) apply_run_star<T, REALC, NR, RO, true, 1>(*st, e0, h, D, nrhs, acc);
-      else apply_run_star<T, REALC, NR, RO, false, 1>(*st, e0, h, D, nrhs, acc);
+      if (hs) {
+        if (diag) apply_run_star<T, REALC, NR, RO, true, 1, 0, 0, true>(*st, e0, h, D, nrhs, acc);
+        else apply_run_star<T, REALC, NR, RO, false, 1, 0, 0, true>(*st, e0, h, D, nrhs, acc);
+      } else {
+        if (diag) apply_run_star<T, REALC, NR, RO, true, 1>(*st, e0, h, D, nrhs, acc);
+        else apply_run_star<T, REALC, NR, RO, false, 1>(*st, e0, h, D, nrhs, acc);
+      }
 #pragma unroll
       for (int s = 0; s < 2; ++s)
 #pragma unroll
@@ -585,8 +596,13 @@ __device__ __noinline__ void star_run_call(const StarParams* st, bool diag, int 
       return;
     }
   }
-  if (diag) apply_run_star<T, REALC, NR, RO, true>(*st, e0, h, D, nrhs, acc);
-  else apply_run_star<T, REALC, NR, RO, false>(*st, e0, h, D, nrhs, acc);
+  if (hs) {
+    if (diag) apply_run_star<T, REALC, NR, RO, true, 0, 0, 0, true>(*st, e0, h, D, nrhs, acc);
+    else apply_run_star<T, REALC, NR, RO, false, 0, 0, 0, true>(*st, e0, h, D, nrhs, acc);
+  } else {
+    if (diag) apply_run_star<T, REALC, NR, RO, true>(*st, e0, h, D, nrhs, acc);
+    else apply_run_star<T, REALC, NR, RO, false>(*st, e0, h, D, nrhs, acc);
+  }
 #pragma unroll
   for (int s = 0; s < 2; ++s)
 #pragma unroll
