@@ -82,7 +82,9 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_init(BatchDev b, int level, int w
 #pragma unroll
     for (int q = 0; q < 3 * NR; ++q) vt[q] = T(0);
     const int base = (c - un.chunk0) * un.chunk, end = min(base + un.chunk, D);
-    vec_init<T, NR>(un, base, end, D, nrhs, warm != 0, level == LEVEL_FP32, zero_rhs, F, U, r, h, w, M, vt);
+    const bool zu = level == LEVEL_FP32;
+    if (un.hspec) vec_init<T, NR, true>(un, base, end, D, nrhs, warm != 0, zu, zero_rhs, F, U, r, h, w, M, vt);
+    else vec_init<T, NR>(un, base, end, D, nrhs, warm != 0, zu, zero_rhs, F, U, r, h, w, M, vt);
     block_reduce_mixed<T, 3 * NR>(vt, v);
     if (!chunk_arrive<3 * NR>(b, c, u, v)) continue;
     unit_sums<3 * NR>(b, un, v);
@@ -143,7 +145,8 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_update(BatchDev b, int level, uns
 #pragma unroll
     for (int q = 0; q < 2 * NR; ++q) vt[q] = T(0);
     const int base = (c - un.chunk0) * un.chunk, end = min(base + un.chunk, D);
-    vec_update<T, NR>(un, base, end, D, nrhs, done, alpha, r, w, M, vt);
+    if (un.hspec) vec_update<T, NR, true>(un, base, end, D, nrhs, done, alpha, r, w, M, vt);
+    else vec_update<T, NR>(un, base, end, D, nrhs, done, alpha, r, w, M, vt);
     block_reduce_mixed<T, 2 * NR>(vt, v);
     if (!chunk_arrive<2 * NR>(b, c, u, v)) continue;
     unit_sums<2 * NR>(b, un, v);

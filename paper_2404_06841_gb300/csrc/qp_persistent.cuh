@@ -107,7 +107,8 @@ __device__ __forceinline__ void chunk_range(const UnitDev& un, int c, int& base,
 }
 
 // ---- phases over one chunk of modes (thread t handles modes base + t, base + t + BLOCK, ...: the mapping of
-//      the graph-form kernels, so that the per-chunk partial sums are the same)
+//      the graph-form kernels, so that the per-chunk partial sums are the same). The persistent form runs
+//      full-spectrum plans only (half-spectrum solves run as graphs), so its sums carry no mode weights.
 
 // r = F - w (warm) or F, r(0) = 0, h = M r; U = 0 where asked; reduces ||F||^2, (r, M r), ||r||^2.
 template <typename T, int NR>

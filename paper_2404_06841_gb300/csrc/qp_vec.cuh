@@ -63,9 +63,10 @@ __device__ __forceinline__ void vld_real(const T* p, int n, T (&v)[W]) {
 }
 
 // r = F - w (warm: w = Q U) or r = F, with r(0) = 0 and F = 0 for the right-hand sides in zero_rhs; h = M r;
-// U = 0 where zero_u. Per-thread partials vt: ||F||^2, (r, M r), ||r||^2 per right-hand side (each mode weighted
-// by mode_weight: a half-spectrum entry off the plane k_{n-1} = 0 counts for its mirror too).
-template <typename T, int NR>
+// U = 0 where zero_u. Per-thread partials vt: ||F||^2, (r, M r), ||r||^2 per right-hand side. HW (half-spectrum
+// units): each mode weighted by mode_weight, an entry off the plane k_{n-1} = 0 counting for its mirror too; the
+// full-spectrum form has no weights (in FP64 a multiply per term is not free).
+template <typename T, int NR, bool HW = false>
 __device__ __forceinline__ void vec_init(const UnitDev& un, int base, int end, int D, int nrhs, bool warm, bool zero_u,
                                          const int* zero_rhs, const cplx<T>* __restrict__ F, cplx<T>* __restrict__ U,
                                          cplx<T>* __restrict__ r, cplx<T>* __restrict__ h,
@@ -78,7 +79,7 @@ __device__ __forceinline__ void vec_init(const UnitDev& un, int base, int end, i
     vld_real<T, W>(M + e, n, m);
     T wts[W];   // inner-product weights (half-spectrum units: 1 or 2; else 1)
 #pragma unroll
-    for (int s = 0; s < W; ++s) wts[s] = (T)mode_weight(un, e + s);
+    for (int s = 0; s < W; ++s) wts[s] = HW ? (T)mode_weight(un, e + s) : T(1);
     cplx<T> fv[NR][W], wv[NR][W];
 #pragma unroll
     for (int k = 0; k < NR; ++k) {
@@ -119,8 +120,9 @@ __device__ __forceinline__ void vec_init(const UnitDev& un, int base, int end, i
   }
 }
 
-// r -= alpha w for the right-hand sides not done; partials vt: (r, M r), ||r||^2 per right-hand side.
-template <typename T, int NR>
+// r -= alpha w for the right-hand sides not done; partials vt: (r, M r), ||r||^2 per right-hand side (HW: as in
+// vec_init).
+template <typename T, int NR, bool HW = false>
 __device__ __forceinline__ void vec_update(const UnitDev& un, int base, int end, int D, int nrhs, const int* done,
                                            const T* alpha,
                                            cplx<T>* __restrict__ r, const cplx<T>* __restrict__ w,
@@ -133,7 +135,7 @@ __device__ __forceinline__ void vec_update(const UnitDev& un, int base, int end,
     vld_real<T, W>(M + e, n, m);
     T wts[W];
 #pragma unroll
-    for (int s = 0; s < W; ++s) wts[s] = (T)mode_weight(un, e + s);
+    for (int s = 0; s < W; ++s) wts[s] = HW ? (T)mode_weight(un, e + s) : T(1);
     cplx<T> rv[NR][W], wv[NR][W];
 #pragma unroll
     for (int k = 0; k < NR; ++k) {
