@@ -419,8 +419,8 @@ void build_star_weights(qp_plan* p, cudaStream_t s) {
 }
 
 // The same for a plan with general taps (not star-1): its FP64 entries Q_ij per (sorted tap, mode), [ntaps][D], formed
-// by the general stencil's own arithmetic, read by every FP64 apply of the plan (single or batched). Built when the plan
-// has FP64 vectors, stores the full spectrum and the table takes at most a quarter of the free device memory.
+// by the general stencil's own arithmetic, read by every FP64 apply of the plan (single or batched). Built when the
+// plan has FP64 vectors, stores the full spectrum and the table takes at most a quarter of the free device memory.
 int last_axis_run(const qp_plan* p);
 
 void build_gen_weights(qp_plan* p, cudaStream_t s) {
@@ -876,6 +876,8 @@ Entry& get_entry(Solver* sv, const Units& us, const Key& key, cudaStream_t s) {
   bd.nslots = nslots;
   bd.units = (const UnitDev*)up(units.data(), units.size() * sizeof(UnitDev));
   bd.single = nu == 1 ? 1 : 0;
+  bd.hspec_any = 0;
+  for (const UnitDev& x : units) bd.hspec_any |= x.hspec;
   bd.pu = units[0];
   bd.st = sv->st;
   bd.chunk_unit = (const int*)up(chunk_unit.data(), chunk_unit.size() * sizeof(int));

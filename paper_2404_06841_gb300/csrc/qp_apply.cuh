@@ -87,9 +87,152 @@ __device__ __forceinline__ void apply_chunk(const PlanDev& sp, const cplx<T>* sc
   }
 }
 
+// The block that completes a unit's chunks sums them and updates its right-hand sides' solver state (a call of its
+// own: it runs once per unit and launch, and its registers stay out of the chunk loop).
+template <int EPI, int NR, int NV>
+__device__ __noinline__ void unit_finalize(const BatchDev& b, const UnitDev& un, RhsSt* st, int nrhs, int refine,
+                                           unsigned long long cond, double (&v)[NV]) {
+  unit_sums<NV>(b, un, v);
+  for (int r = 0; r < nrhs && r < NR; ++r) {
+    const double s0 = (EPI == EPI_RESIDUAL) ? v[2 * r] : v[r];
+    const double s1 = (EPI == EPI_RESIDUAL) ? v[(2 * r + 1) % NV] : 0.0;
+    if (threadIdx.x == 0) {
+      RhsSt& x = st[r];
+      if (EPI == EPI_DOT_HW) {
+        if (!x.done) {
+          x.hw = s0;
+          if (!(s0 > 0.0) || !isfinite(s0)) {   // (h, Q h) <= 0 or NaN: breakdown
+            x.done = 1;
+            x.status = QP_ERR_BREAKDOWN;
+            count_done(b, 0, 1, cond);           // completing the count here ends the PCG loop
+          } else {
+            x.alpha = x.rz / s0;
+          }
+        }
+      } else if (!refine) {
+        x.orr = s0;
+        x.of2 = s1;
+      } else if (!x.odone) {
+        x.orr = s0;
+        x.of2 = s1;
+        x.outer += 1;
+        x.inner_total += x.iters;
+        const double rel = s1 > 0.0 ? sqrt(s0 / s1) : 0.0;
+        int od = 0, os = QP_ERR_NO_CONVERGENCE;
+        if (s1 == 0.0 || s0 <= b.otol2 * s1) {
+          od = 1;
+          os = QP_OK;
+        } else if (!isfinite(rel)) {
+          od = 1;
+          os = QP_ERR_BREAKDOWN;
+        } else if (rel > 0.9 * x.prev_rel || x.outer > b.max_outer || x.inner_total >= b.maxit) {
+          od = 1;   // stagnation or cap
+        }
+        x.prev_rel = rel;
+        x.inv_scale = sqrt(s0);
+        x.scale = s0 > 0.0 ? 1.0 / x.inv_scale : 0.0;
+        x.ostatus = os;
+        if (od) {
+          x.odone = 1;
+          count_done(b, 1, 1, cond);             // the right-hand side that completes the count ends the loop
+        }
+      }
+    }
+  }
+}
+
+static __device__ PlanDev g_no_plan;   // the plan argument of apply_chunk, which the star-1 stencil does not read
+
+// A batch of one star-1 unit (the star kernels; the unit and its stencil come from the kernel parameters). A block
+// walks its chunks c, c + grid, ... without a block barrier per chunk: each warp keeps its warp sums of the chunk in
+// shared memory, and every 16 chunks (and after its last one) the block combines them per chunk as
+// block_reduce_mixed does and stores the chunk partials, the same values in the same order; the block counts its
+// chunks' arrival once, after its last chunk (the fence and the atomic per chunk cost 10% of the FP32 apply).
+template <typename T, int EPI, bool REALC, int NR, int SK, int NAX, int DC, bool HSP>
+__device__ __forceinline__ void apply_single_star(const BatchDev& b, int level, int refine, unsigned long long cond,
+                                                  const StarParams& stp) {
+  constexpr int NV = (EPI == EPI_RESIDUAL) ? 2 * NR : NR;
+  constexpr int NS = 16, NW = BLOCK / 32;
+  const UnitDev& un = b.pu;
+  RhsSt* st = b.st;
+  const int nrhs = un.nrhs;
+  bool active = false;   // the same for every chunk: only this launch's finalizer changes it, after every chunk
+  for (int r = 0; r < nrhs; ++r) {
+    if (EPI == EPI_DOT_HW) active |= !ld_int(&st[r].done);
+    else if (EPI == EPI_RESIDUAL && refine) active |= !ld_int(&st[r].odone);
+    else active = true;
+  }
+  if (!active) return;
+  const int D = un.D;
+  const cplx<T>* src;
+  cplx<T>* dst;
+  if (level == LEVEL_FP32) {
+    src = reinterpret_cast<const cplx<T>*>(un.h32);
+    dst = reinterpret_cast<cplx<T>*>(un.w32);
+  } else {
+    src = reinterpret_cast<const cplx<T>*>(EPI == EPI_DOT_HW ? (const double2*)un.h : (const double2*)un.U);
+    dst = reinterpret_cast<cplx<T>*>(un.w);
+  }
+  const cplx<T>* F = reinterpret_cast<const cplx<T>*>(un.F);
+  __shared__ double wsum[NS][NV][NW];
+  __shared__ int s_last;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int pend = 0, cfirst = blockIdx.x;
+  unsigned mine = 0;
+  for (int c = blockIdx.x; c < b.nchunks; c += gridDim.x) {
+    T vt[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) vt[q] = T(0);
+    apply_chunk<T, EPI, REALC, NR, 2, NV, SK, NAX, DC, HSP>(g_no_plan, nullptr, stp, un, c - un.chunk0, D,
+                                                           NAX != 0 ? NR : nrhs, refine, false, src, dst, F, vt);
+    if (EPI == EPI_NONE) continue;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      if (sizeof(T) == 4) vt[q] = (T)warp_sum_f((float)vt[q]);
+      else vt[q] = (T)warp_sum((double)vt[q]);
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int q = 0; q < NV; ++q) wsum[pend][q][wid] = (double)vt[q];
+    }
+    ++pend;
+    ++mine;
+    if (pend == NS || c + (int)gridDim.x >= b.nchunks) {
+      __syncthreads();
+      if (wid == 0) {
+        for (int i = 0; i < pend; ++i) {
+#pragma unroll
+          for (int q = 0; q < NV; ++q) {
+            const double x = warp_sum(lane < NW ? wsum[i][q][lane] : 0.0);
+            if (lane == 0) b.partials[(size_t)q * b.nchunks + cfirst + i * (int)gridDim.x] = x;
+          }
+        }
+      }
+      __syncthreads();
+      cfirst += pend * (int)gridDim.x;
+      pend = 0;
+    }
+  }
+  if (EPI == EPI_NONE || mine == 0) return;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = (atomicAdd(&b.ucount[0], mine) + mine == (unsigned)un.nchunk) ? 1 : 0;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double v[NV];
+  unit_finalize<EPI, NR, NV>(b, un, st, nrhs, refine, cond, v);
+  if (threadIdx.x == 0) b.ucount[0] = 0;
+}
+
 template <typename T, int EPI, bool REALC, int NR, int SK, int NAX = 0, int DC = 0, bool HSP = false>
 __device__ __forceinline__ void apply_units(const BatchDev& b, int level, int refine, unsigned long long cond,
                                             const StarParams& stp) {
+  if constexpr (SK != 0) {
+    apply_single_star<T, EPI, REALC, NR, SK, NAX, DC, HSP>(b, level, refine, cond, stp);
+    return;
+  }
   __shared__ __align__(16) PlanDev sp;
   extern __shared__ __align__(16) unsigned char smraw[];
   cplx<T>* scoef = reinterpret_cast<cplx<T>*>(smraw);
@@ -147,53 +290,7 @@ __device__ __forceinline__ void apply_units(const BatchDev& b, int level, int re
     block_reduce_mixed<T, NV>(vt, v);
     if (!chunk_arrive<NV>(b, c, u, v)) continue;
     // this block completes unit u: finalize its right-hand sides
-    unit_sums<NV>(b, un, v);
-    for (int r = 0; r < nrhs && r < NR; ++r) {
-      const double s0 = (EPI == EPI_RESIDUAL) ? v[2 * r] : v[r];
-      const double s1 = (EPI == EPI_RESIDUAL) ? v[(2 * r + 1) % NV] : 0.0;
-      if (threadIdx.x == 0) {
-        RhsSt& x = st[r];
-        if (EPI == EPI_DOT_HW) {
-          if (!x.done) {
-            x.hw = s0;
-            if (!(s0 > 0.0) || !isfinite(s0)) {   // (h, Q h) <= 0 or NaN: breakdown
-              x.done = 1;
-              x.status = QP_ERR_BREAKDOWN;
-              count_done(b, 0, 1, cond);           // completing the count here ends the PCG loop
-            } else {
-              x.alpha = x.rz / s0;
-            }
-          }
-        } else if (!refine) {
-          x.orr = s0;
-          x.of2 = s1;
-        } else if (!x.odone) {
-          x.orr = s0;
-          x.of2 = s1;
-          x.outer += 1;
-          x.inner_total += x.iters;
-          const double rel = s1 > 0.0 ? sqrt(s0 / s1) : 0.0;
-          int od = 0, os = QP_ERR_NO_CONVERGENCE;
-          if (s1 == 0.0 || s0 <= b.otol2 * s1) {
-            od = 1;
-            os = QP_OK;
-          } else if (!isfinite(rel)) {
-            od = 1;
-            os = QP_ERR_BREAKDOWN;
-          } else if (rel > 0.9 * x.prev_rel || x.outer > b.max_outer || x.inner_total >= b.maxit) {
-            od = 1;   // stagnation or cap
-          }
-          x.prev_rel = rel;
-          x.inv_scale = sqrt(s0);
-          x.scale = s0 > 0.0 ? 1.0 / x.inv_scale : 0.0;
-          x.ostatus = os;
-          if (od) {
-            x.odone = 1;
-            count_done(b, 1, 1, cond);             // the right-hand side that completes the count ends the loop
-          }
-        }
-      }
-    }
+    unit_finalize<EPI, NR, NV>(b, un, st, nrhs, refine, cond, v);
     if (threadIdx.x == 0) b.ucount[u] = 0;
   }
 }
@@ -203,7 +300,8 @@ static __device__ StarParams g_no_star;
 
 // Batch apply over every chunk of the batch (plans from the unit table, in shared memory).
 template <typename T, int EPI, bool REALC, int NR>
-__global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 3) k_apply(BatchDev b, int level, int refine, unsigned long long cond) {
+__global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 3)
+    k_apply(const __grid_constant__ BatchDev b, int level, int refine, unsigned long long cond) {
   apply_units<T, EPI, REALC, NR, 0>(b, level, refine, cond, g_no_star);
 }
 
@@ -213,7 +311,8 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 3) k_apply(BatchDe
 // two (up to 128 registers).
 template <typename T, int EPI, bool REALC, int NR, int SK, int NAX = 0, int DC = 0, bool HSP = false>
 __global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : (NAX != 0 ? 2 : 4))
-    k_apply_star(BatchDev b, int level, int refine, unsigned long long cond, const __grid_constant__ StarParams st) {
+    k_apply_star(const __grid_constant__ BatchDev b, int level, int refine, unsigned long long cond,
+                 const __grid_constant__ StarParams st) {
   apply_units<T, EPI, REALC, NR, SK, NAX, DC, HSP>(b, level, refine, cond, st);
 }
 
@@ -283,23 +382,35 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : 3) k_apply_plain(c
 
 // Plain apply of a star-1 plan with an even last axis: the stencil data as a kernel parameter; one run of two
 // modes per thread.
+// Blocks per SM of the star-1 plain kernels (their launch bounds) and the grid that keeps exactly those resident.
+template <typename T, int NAX> __host__ __device__ constexpr int plain_star_bps() {
+  return sizeof(T) == 8 ? 2 : (NAX != 0 ? 2 : 4);
+}
+template <typename T, int NAX> inline int plain_star_grid(int D) {
+  return (int)std::min<long long>(((long long)D / 2 + BLOCK - 1) / BLOCK, 152LL * plain_star_bps<T, NAX>());
+}
+
+// The resident blocks sweep the modes together: block b takes the 512-mode segments b, b + grid, b + 2 grid, ...
+// (thread t the run of two modes at 2t), so that at any time they work in one window of the vectors and the
+// stencil's reads along the outer axes hit L2; no block is started per segment.
 template <typename T, bool REALC, int NR, int SK, int NAX = 0, int DC = 0, bool HSP = false>
-__global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 2 : (NAX != 0 ? 2 : 4))
+__global__ void __launch_bounds__(BLOCK, plain_star_bps<T, NAX>())
     k_apply_plain_star(const __grid_constant__ StarParams st, int D, int nrhs, const cplx<T>* h, cplx<T>* w) {
-  const int e0 = (blockIdx.x * BLOCK + threadIdx.x) * 2;
-  if (e0 >= D) return;
-  cplx<T> acc[2][NR];
-  apply_run_star<T, REALC, NR, true, SK == 2, sizeof(T) == 8 ? 1 : 0, NAX, DC, HSP>(st, e0, h, D, nrhs, acc);
+  const int step = (int)gridDim.x * BLOCK * 2;
+  for (int e0 = (blockIdx.x * BLOCK + threadIdx.x) * 2; e0 < D; e0 += step) {
+    cplx<T> acc[2][NR];
+    apply_run_star<T, REALC, NR, true, SK == 2, sizeof(T) == 8 ? 1 : 0, NAX, DC, HSP>(st, e0, h, D, nrhs, acc);
 #pragma unroll
-  for (int r = 0; r < NR; ++r) {
-    if (r < nrhs) {
-      cplx<T>* o = w + (size_t)r * D + e0;
-      if (sizeof(T) == 4) {
-        *reinterpret_cast<float4*>(o) = make_float4((float)acc[0][r].x, (float)acc[0][r].y, (float)acc[1][r].x,
-                                                    (float)acc[1][r].y);
-      } else {
-        o[0] = acc[0][r];
-        o[1] = acc[1][r];
+    for (int r = 0; r < NR; ++r) {
+      if (r < nrhs) {
+        cplx<T>* o = w + (size_t)r * D + e0;
+        if (sizeof(T) == 4) {
+          *reinterpret_cast<float4*>(o) = make_float4((float)acc[0][r].x, (float)acc[0][r].y, (float)acc[1][r].x,
+                                                      (float)acc[1][r].y);
+        } else {
+          o[0] = acc[0][r];
+          o[1] = acc[1][r];
+        }
       }
     }
   }
@@ -310,7 +421,7 @@ static void plain_star_nr(int nrhs, const StarParams& st, int D, const cplx<T>* 
   if constexpr (sizeof(T) == 4) {
     if (launch_plain_star_fixed(st, REALC, nrhs, SK == 2 ? QP_COEF_DIAG : QP_COEF_SCALAR, D, h, w, s)) return;
   }
-  const int nblk = (D / 2 + BLOCK - 1) / BLOCK;
+  const int nblk = plain_star_grid<T, 0>(D);
   if (st.hspec) {
     switch (nrhs) {
       case 1: k_apply_plain_star<T, REALC, 1, SK, 0, 0, true><<<nblk, BLOCK, 0, s>>>(st, D, nrhs, h, w); break;

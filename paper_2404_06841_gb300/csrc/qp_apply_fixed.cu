@@ -12,7 +12,7 @@ namespace {
 
 template <int NAX, int DC, bool REALC, int SK>
 void plain_fixed(const StarParams& st, int nrhs, int D, const float2* h, float2* w, cudaStream_t s) {
-  const int nblk = (D / 2 + BLOCK - 1) / BLOCK;
+  const int nblk = plain_star_grid<float, NAX>(D);
   if (st.hspec) k_apply_plain_star<float, REALC, DC, SK, NAX, DC, true><<<nblk, BLOCK, 0, s>>>(st, D, nrhs, h, w);
   else k_apply_plain_star<float, REALC, DC, SK, NAX, DC><<<nblk, BLOCK, 0, s>>>(st, D, nrhs, h, w);
 }

@@ -8,9 +8,12 @@ namespace qp {
 
 namespace {
 
+// One resident block per slot (two per SM), each walking the chunks c, c + grid, ...: chunk c + k grid belongs to
+// sweep wave k, so the resident blocks go through the waves in order; the per-chunk sums are those of any grid.
 template <int NAX, int DC, bool REALC, int SK>
 void batch_fixed(const BatchDev& b, int level, int refine, unsigned long long cond, int nblk, size_t smem,
                  const StarParams& st, cudaStream_t s) {
+  nblk = std::min(nblk, sweep_chunks<float>());
   if (st.hspec)
     k_apply_star<float, EPI_DOT_HW, REALC, DC, SK, NAX, DC, true><<<nblk, BLOCK, smem, s>>>(b, level, refine, cond, st);
   else k_apply_star<float, EPI_DOT_HW, REALC, DC, SK, NAX, DC><<<nblk, BLOCK, smem, s>>>(b, level, refine, cond, st);

@@ -279,7 +279,7 @@ struct RhsSt {
 };
 
 struct BatchDev {
-  int nunits, nchunks, nslots, pad0_;
+  int nunits, nchunks, nslots, hspec_any;   // hspec_any: some unit has half-spectrum storage
   int single, pad_[3];                  // single: one unit, whose description is "pu" (kernel parameter)
   UnitDev pu;
   const UnitDev* units;

@@ -61,7 +61,9 @@ template <> __device__ __forceinline__ const float* vM<float>(const UnitDev& u) 
 
 // r = F - w (warm start: w = Q U) or r = F, r(0) = 0, h = M r; FP32 level: U32 = 0, and right-hand sides that
 // already meet the outer tolerance start from F = 0. Reduces ||F||^2, (r, M r), ||r||^2.
-template <typename T, int NR>
+// HW: compiled for batches with half-spectrum units (their sums weighted per mode); the other batches take the
+// form without weights, which keeps its registers and occupancy.
+template <typename T, int NR, bool HW>
 __global__ void __launch_bounds__(BLOCK) k_pcg_init(BatchDev b, int level, int warm, unsigned long long cond) {
   for (int c = blockIdx.x; c < b.nchunks; c += gridDim.x) {
     const int u = unit_of_chunk(b, c);
@@ -83,7 +85,7 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_init(BatchDev b, int level, int w
     for (int q = 0; q < 3 * NR; ++q) vt[q] = T(0);
     const int base = (c - un.chunk0) * un.chunk, end = min(base + un.chunk, D);
     const bool zu = level == LEVEL_FP32;
-    if (un.hspec) vec_init<T, NR, true>(un, base, end, D, nrhs, warm != 0, zu, zero_rhs, F, U, r, h, w, M, vt);
+    if (HW && un.hspec) vec_init<T, NR, true>(un, base, end, D, nrhs, warm != 0, zu, zero_rhs, F, U, r, h, w, M, vt);
     else vec_init<T, NR>(un, base, end, D, nrhs, warm != 0, zu, zero_rhs, F, U, r, h, w, M, vt);
     block_reduce_mixed<T, 3 * NR>(vt, v);
     if (!chunk_arrive<3 * NR>(b, c, u, v)) continue;
@@ -120,7 +122,7 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_init(BatchDev b, int level, int w
 
 // alpha step on the residual, and the reductions for beta and the convergence test (U is updated by
 // k_pcg_hupdate, which reads h anyway).
-template <typename T, int NR>
+template <typename T, int NR, bool HW>
 __global__ void __launch_bounds__(BLOCK) k_pcg_update(BatchDev b, int level, unsigned long long cond) {
   for (int c = blockIdx.x; c < b.nchunks; c += gridDim.x) {
     const int u = unit_of_chunk(b, c);
@@ -145,7 +147,7 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_update(BatchDev b, int level, uns
 #pragma unroll
     for (int q = 0; q < 2 * NR; ++q) vt[q] = T(0);
     const int base = (c - un.chunk0) * un.chunk, end = min(base + un.chunk, D);
-    if (un.hspec) vec_update<T, NR, true>(un, base, end, D, nrhs, done, alpha, r, w, M, vt);
+    if (HW && un.hspec) vec_update<T, NR, true>(un, base, end, D, nrhs, done, alpha, r, w, M, vt);
     else vec_update<T, NR>(un, base, end, D, nrhs, done, alpha, r, w, M, vt);
     block_reduce_mixed<T, 2 * NR>(vt, v);
     if (!chunk_arrive<2 * NR>(b, c, u, v)) continue;
@@ -276,19 +278,33 @@ __global__ void __launch_bounds__(BLOCK) k_refine_accum(BatchDev b) {
 
 void launch_pcg_init(const BatchDev& b, int maxr, int level, bool warm, unsigned long long cond, int nblk,
                      cudaStream_t s) {
-#define QP_CALL(NR)                                                                                  \
-  if (level == LEVEL_FP32) k_pcg_init<float, NR><<<nblk, BLOCK, 0, s>>>(b, level, warm ? 1 : 0, cond); \
-  else k_pcg_init<double, NR><<<nblk, BLOCK, 0, s>>>(b, level, warm ? 1 : 0, cond)
+#define QP_CALL2(NR, HW)                                                                                  \
+  if (level == LEVEL_FP32) k_pcg_init<float, NR, HW><<<nblk, BLOCK, 0, s>>>(b, level, warm ? 1 : 0, cond); \
+  else k_pcg_init<double, NR, HW><<<nblk, BLOCK, 0, s>>>(b, level, warm ? 1 : 0, cond)
+#define QP_CALL(NR)            \
+  if (b.hspec_any) {           \
+    QP_CALL2(NR, true);        \
+  } else {                     \
+    QP_CALL2(NR, false);       \
+  }
   QP_NR_SWITCH(maxr, QP_CALL)
 #undef QP_CALL
+#undef QP_CALL2
   count_launch();
 }
 void launch_pcg_update(const BatchDev& b, int maxr, int level, unsigned long long cond, int nblk, cudaStream_t s) {
-#define QP_CALL(NR)                                                                      \
-  if (level == LEVEL_FP32) k_pcg_update<float, NR><<<nblk, BLOCK, 0, s>>>(b, level, cond); \
-  else k_pcg_update<double, NR><<<nblk, BLOCK, 0, s>>>(b, level, cond)
+#define QP_CALL2(NR, HW)                                                                      \
+  if (level == LEVEL_FP32) k_pcg_update<float, NR, HW><<<nblk, BLOCK, 0, s>>>(b, level, cond); \
+  else k_pcg_update<double, NR, HW><<<nblk, BLOCK, 0, s>>>(b, level, cond)
+#define QP_CALL(NR)            \
+  if (b.hspec_any) {           \
+    QP_CALL2(NR, true);        \
+  } else {                     \
+    QP_CALL2(NR, false);       \
+  }
   QP_NR_SWITCH(maxr, QP_CALL)
 #undef QP_CALL
+#undef QP_CALL2
   count_launch();
 }
 void launch_pcg_hupdate(const BatchDev& b, int maxr, int level, int nblk, cudaStream_t s) {
