@@ -128,7 +128,10 @@ def test_fixed_geometry_plain_apply_is_the_general_one(qp, d, n, N, kind, real):
 
 @pytest.mark.parametrize("d,n,N,kind,real", [(1, 2, (5, 8), "scalar", False), (2, 4, (6, 5, 4, 8), "diag", True),
                                              (3, 6, (4, 3, 4, 5, 4, 6), "diag", False),
-                                             (2, 4, (4, 6, 5, 4), "scalar", False)])
+                                             (2, 4, (4, 6, 5, 4), "scalar", False),
+                                             # 32^4: 1,024 chunks, so the FP32 batch kernel with the geometry
+                                             # compiled in walks several chunks per block (grid of resident blocks)
+                                             (2, 4, (32, 32, 32, 32), "diag", False)])
 def test_fixed_geometry_solves_are_the_general_ones(qp, d, n, N, kind, real):
     """Every axis with taps and d right-hand sides: the persistent solve and the graph form's FP32 batch apply take
     the kernels with the geometry compiled in; with d + 1 right-hand sides the general ones run. Each right-hand
