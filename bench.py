@@ -126,12 +126,12 @@ def fft_apply_bytes(d, ncomp, nrhs, D, es):
 TRAFFIC = {
     # cfg4: the FP32 (h, Q h) batch apply of the refinement solve (k_apply_star, geometry compiled in), captured at
     # N = 14 (7.53 M modes; h and w exceed L2), scaled by 16^6 / 14^6
-    ("apply32", "cfg4"): int((211.67e6 + 156.21e6) * (16 ** 6 / 14 ** 6)),
+    ("apply32", "cfg4"): int((210870912 + 152987392) * (16 ** 6 / 14 ** 6)),
     # cfg1: one solve (33 iterations, 2 correctors) in k_pcg_persistent; vectors and stored weights stay in L2
     ("k_pcg_persistent", "cfg1"): 9572352 + 236032,
     # cfg4: k_apply_plain_star (geometry compiled in) captured at N = 14 (7.53 M modes; h and w exceed L2), scaled
     # by 16^6 / 14^6
-    ("k_apply_plain", "cfg4"): int((207640320 + 153260032) * (16 ** 6 / 14 ** 6)),
+    ("k_apply_plain", "cfg4"): int((212182400 + 153766528) * (16 ** 6 / 14 ** 6)),
     # cfg2: the three fused passes of one FP32 apply (the gradient fields stay in L2 between passes)
     ("k_fft_group", "cfg2"): 16874752 + 9472 + 46255616 + 0 + 33646848 + 0,
 }
