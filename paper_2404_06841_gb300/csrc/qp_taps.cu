@@ -93,7 +93,7 @@ __device__ __forceinline__ void lambda_shift(const PlanDev& p, const int (&ib)[M
 
 // Jacobi diagonal q(k) = lambda(k)^T A~_0 lambda(k) and the Frobenius-optimal diagonal q(k) / ||Q e_k||^2
 // (eq. preconditioner) with ||Q e_k||^2 = sum_t |lambda(k +N m_t)^T C_t lambda(k)|^2 (O(gD), Sec. 4.3).
-// Stored as M (z = M r), M(0) = 0. out[0] = min over k != 0 of |lambda(k)|^2, out[1] = min q / |lambda|^2.
+// Stored as M (z = M r), M(0) = 0. out[0] = min over k != 0 of |lambda(k)|^2, out[1] = min over those k of q(k).
 // with_frob = 0: the Jacobi diagonal only (the Frobenius one costs a weight per tap and mode: built on first use).
 __global__ void __launch_bounds__(BLOCK) k_diag(const PlanDev* plan, int D, double* jac, double* frob, float* jac32,
                                                 float* frob32, double* partials, unsigned* counter, double* out,
@@ -108,10 +108,15 @@ __global__ void __launch_bounds__(BLOCK) k_diag(const PlanDev* plan, int D, doub
     int ib[MAXN], k[MAXN];
     mode_digits(sp, e, ib, k);
     double lk[MAXD] = {0, 0, 0};
-    for (int a = 0; a < d; ++a)
-      for (int j = 0; j < sp.n; ++j) lk[a] = fma(sp.P[a][j], (double)k[j], lk[a]);
+#pragma unroll
+    for (int a = 0; a < MAXD; ++a)
+#pragma unroll
+      for (int j = 0; j < MAXN; ++j)
+        if (a < d && j < sp.n) lk[a] = fma(sp.P[a][j], (double)k[j], lk[a]);
     double l2sum = 0.0;
-    for (int a = 0; a < d; ++a) l2sum += lk[a] * lk[a];
+#pragma unroll
+    for (int a = 0; a < MAXD; ++a)
+      if (a < d) l2sum += lk[a] * lk[a];
     const double q = weight_general<double>(sp.kind, d, scoef, lk, lk).x;
     double cn = 0.0;
     for (int t = 0; with_frob && t < sp.ntaps; ++t) {
@@ -127,7 +132,7 @@ __global__ void __launch_bounds__(BLOCK) k_diag(const PlanDev* plan, int D, doub
       mj = q != 0.0 ? 1.0 / q : 0.0;
       mf = cn > 0.0 ? q / cn : 0.0;
       red[0] = fmin(red[0], l2sum);
-      red[1] = fmin(red[1], l2sum > 0.0 ? q / l2sum : -1.0);
+      red[1] = fmin(red[1], l2sum > 0.0 ? q : -1.0);   // q(k) > 0 at every k != 0 (only its sign is used)
     }
     jac[e] = mj;
     jac32[e] = (float)mj;
