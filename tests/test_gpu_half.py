@@ -163,3 +163,30 @@ def test_large_form_half_spectrum_against_golden(qp):
     ref = np.array(gold["astar_re"])
     assert np.abs(A.real - ref).max() <= 1e-10 * np.abs(ref).max(), A.real - ref
     qp.qp_plan_destroy(plan)
+
+
+@pytest.mark.parametrize("mode", ["fp64", "refine"])
+def test_half_plans_in_a_batch(qp, mode):
+    """A batch mixing half-spectrum plans (star-1 and general taps) with a full one: every plan's a* equals its
+    own solve bit for bit (a unit reduces in the same order alone or batched; the vector passes weigh the half
+    units' modes and not the full unit's) and the oracle's value for its scheme."""
+    insts = [W.random_star_instance(2, 4, (6, 4, 6, 8), "diag", seed=71),
+             W.random_instance(2, 3, (6, 4, 10), "sym", "taps", seed=72, radius=1),
+             W.random_star_instance(1, 2, (16, 12), "scalar", seed=73)]
+    spectra = [qp.QP_SPECTRUM_HALF, qp.QP_SPECTRUM_HALF, qp.QP_SPECTRUM_FULL]
+    m = qp.QP_MODE_FP64 if mode == "fp64" else qp.QP_MODE_FP32_REFINE
+    plans = [qp.plan_from_instance(i, spectrum=sp) for i, sp in zip(insts, spectra)]
+    batch = qp.qp_batch_create(plans)
+    As, infos = qp.qp_batch_homogenized(batch, tol=1e-11, mode=m, maxit=2000)
+    assert all(i["status"] == "QP_OK" and i["rel_residual"] <= 1e-11 for i in infos), infos
+    for inst, sp, plan, A in zip(insts, spectra, plans, As):
+        A1, _ = qp.qp_homogenized(plan, tol=1e-11, mode=m, maxit=2000)
+        assert np.array_equal(A, A1.real), inst.name
+        if sp == qp.QP_SPECTRUM_HALF:
+            A_ref, *_ = O.homogenized_nyquist_free(inst, tol=1e-13)
+        else:
+            A_ref, *_ = O.homogenized(inst, tol=1e-13)
+        assert np.abs(A - A_ref).max() <= 1e-10 * np.abs(A_ref).max(), inst.name
+    qp.qp_batch_destroy(batch)
+    for p in plans:
+        qp.qp_plan_destroy(p)
