@@ -837,9 +837,10 @@ Entry& get_entry(Solver* sv, const Units& us, const Key& key, cudaStream_t s) {
     x.plan = p->pd;
     x.D = p->D;
     x.nrhs = us.nrhs[u];
-    // one chunk per block, blocks dispatched in index order so that the resident blocks cover a contiguous
-    // window of modes (neighbour reads along outer axes then hit L2); the chunk depends on D only
-    // (chunk_modes), so the reduction order of a unit does not depend on its batch
+    // chunks dispatched in index order (one block per chunk, or for the FP32 star-1 batch kernel a grid of the
+    // resident blocks walking c, c + grid, ...) so that the resident blocks cover a contiguous window of modes
+    // (neighbour reads along outer axes then hit L2); the chunk depends on D only (chunk_modes), so the
+    // reduction order of a unit does not depend on its batch or on which block walks the chunk
     const int64_t chunk = chunk_modes(p->D);
     x.chunk = (int)chunk;
     x.run = last_axis_run(p);
