@@ -277,7 +277,8 @@ uint64_t qp_launch_count(void);
  * same shape are not re-timed. Schedules differ only in the rounding order of the transforms.
  * qp_set_fft_autotune(0): later plans take the balanced-split heuristic instead (process-wide; cached choices
  * still apply). qp_fft_schedule: the schedule in use for precision (QP_FP64 / QP_FP32): its candidate index
- * (-1: the heuristic's), the number of candidates, its timed ms per apply (-1 if untimed) and a description
+ * (-1: the heuristic's), the number of candidates, its timed ms per apply (the timing of the plan that chose it
+ * when the choice came from the cache; -1 if untimed) and a description
  * (text, text_len bytes with the terminating 0; any output may be NULL). qp_fft_set_schedule: use candidate
  * index (0 .. count - 1) from now on. Both return QP_ERR_UNSUPPORTED for a taps-backend plan. With the autotuner off,
  * QP_BACKEND_AUTO also stops timing the stencil against the FFT backend for tap coefficients (taps are kept). */

@@ -390,6 +390,9 @@ struct GroupPass {
   int M, I, L, R, TS, ntile;
   long long O;
   int tiles_o, tiles_i;
+  // aff: the array index of tile element idx + BLOCK is that of idx plus dlin for every idx of the tile, so a
+  // thread's elements idx = t, t + BLOCK, ... sit at lin(t) + u dlin (no per-element division)
+  int aff, dlin;
   size_t smem;
 };
 
@@ -1056,6 +1059,9 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 1 : 2) k_fft_group(con
     const int pos = q - l * gp.M;
     return ((base_o + l) * gp.M + pos) * gp.I + i0 + r;
   };
+  // the index of this thread's u-th element (idx = threadIdx.x + u BLOCK)
+  const int lin0 = lin(threadIdx.x);
+  auto lin_u = [&](int u, int idx) -> int { return gp.aff ? lin0 + u * gp.dlin : lin(idx); };
   const int ntile = (MODE == GP_PLAIN) ? 1 : d;
 
   // ---- load the tiles: lambda_b h (gradient) or the stored fields, GP_BATCH loads in flight per thread
@@ -1067,7 +1073,7 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 1 : 2) k_fft_group(con
 #pragma unroll
       for (int u = 0; u < NB; ++u) {
         const int idx = threadIdx.x + (u0 + u) * BLOCK;
-        ev[u] = idx < TS ? lin(idx) : 0;
+        ev[u] = idx < TS ? lin_u(u0 + u, idx) : 0;
         if (idx < TS) hv[u] = h[(size_t)y * D + ev[u]];
       }
 #pragma unroll
@@ -1093,7 +1099,7 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 1 : 2) k_fft_group(con
       for (int u = 0; u < NE; ++u) {
         const int idx = threadIdx.x + (u0 + u) * BLOCK;
         if (idx < TS) {
-          const int e = lin(idx);
+          const int e = lin_u(u0 + u, idx);
 #pragma unroll
           for (int b = 0; b < MAXD; ++b)
             if (b < ntile) v[u][b] = src0[(size_t)b * fstride + e];
@@ -1123,7 +1129,7 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 1 : 2) k_fft_group(con
 #pragma unroll
       for (int u = 0; u < CB; ++u) {
         const int idx = threadIdx.x + (u0 + u) * BLOCK;
-        const int e = idx < TS ? lin(idx) : 0;
+        const int e = idx < TS ? lin_u(u0 + u, idx) : 0;
 #pragma unroll
         for (int c = 0; c < MAXC; ++c) cv[u][c] = (idx < TS && c < nc) ? coef[(size_t)c * D + e] : T(0);
       }
@@ -1162,7 +1168,7 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 1 : 2) k_fft_group(con
     for (int u = 0; u < GP_EPT; ++u) {
       const int idx = threadIdx.x + u * BLOCK;
       if (idx >= TS) break;
-      const int e = lin(idx);
+      const int e = lin_u(u, idx);
       T lk[MAXD];
       lam_tab<T>(sp, tab, e, lk);
       cplx<T> acc = mk<T>(0, 0);
@@ -1183,7 +1189,7 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 1 : 2) k_fft_group(con
     for (int u = 0; u < GP_EPT; ++u) {
       const int idx = threadIdx.x + u * BLOCK;
       if (idx >= TS) break;
-      const int e = lin(idx);
+      const int e = lin_u(u, idx);
 #pragma unroll
       for (int b = 0; b < MAXD; ++b)
         if (b < ntile) dst0[(size_t)b * fstride + e] = tiles[(size_t)b * TSP + tphys(idx)];
@@ -1247,6 +1253,19 @@ static bool make_pass(const PlanDev& pd, int j0, int ng, int mode, int sign, int
   }
   gp.tiles_i = (int)(I / gp.R);
   gp.tiles_o = (int)(O / gp.L);
+  {
+    // affine walk of a thread's tile elements: checked for every element of a tile (the tile's offsets add
+    // a constant, so one tile decides)
+    auto lin = [&](long long idx) {
+      const long long q = idx / gp.R, r = idx % gp.R, l = q / gp.M, pos = q % gp.M;
+      return (l * gp.M + pos) * (long long)gp.I + r;
+    };
+    gp.aff = gp.TS > BLOCK ? 1 : 0;
+    const long long dl = gp.TS > BLOCK ? lin(BLOCK) - lin(0) : 0;
+    for (long long idx = 0; gp.aff && idx + BLOCK < gp.TS; ++idx)
+      if (lin(idx + BLOCK) - lin(idx) != dl) gp.aff = 0;
+    gp.dlin = gp.aff ? (int)dl : 0;
+  }
   gp.smem = (size_t)((gp.TS - 1) + ((gp.TS - 1) >> 5) + 1) * esize * gp.ntile;
   return (long long)gp.tiles_o * gp.tiles_i < (1ll << 31);
 }
@@ -1462,7 +1481,9 @@ void fft_apply(FftPlan* f, const PlanDev& pd, const PlanDev* pdp, const cplx<T>*
 
 namespace {
 std::mutex g_tune_mu;
-std::map<std::string, int> g_tune_cache;   // geometry and precision -> chosen candidate
+// geometry and precision -> chosen candidate and every candidate's timing (ms per apply), so that a plan served
+// from the cache reports the same schedule and timings as the plan that was timed
+std::map<std::string, std::pair<int, std::vector<float>>> g_tune_cache;
 std::atomic<int> g_autotune{1};
 }  // namespace
 
@@ -1480,8 +1501,10 @@ static void tune_precision(FftPlan* f, const PlanDev& pd, const PlanDev* pdp, cu
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
-    if (it != g_tune_cache.end() && it->second < (int)ss.cand.size()) {
-      ss.chosen = it->second;
+    if (it != g_tune_cache.end() && it->second.first < (int)ss.cand.size() &&
+        it->second.second.size() == ss.cand.size()) {
+      ss.chosen = it->second.first;
+      ss.ms = it->second.second;
       use = ss.cand[ss.chosen];
       return;
     }
@@ -1538,7 +1561,7 @@ static void tune_precision(FftPlan* f, const PlanDev& pd, const PlanDev* pdp, cu
   ss.chosen = best;
   use = ss.cand[best];
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_tune_cache[key] = best;
+  g_tune_cache[key] = {best, ss.ms};
 }
 
 void fft_autotune(FftPlan* f, const PlanDev& pd, const PlanDev* pdp, cudaStream_t s) {

@@ -56,7 +56,7 @@ def test_choice_is_cached_per_geometry_and_autotune_can_be_switched_off(qp):
     s1 = qp.qp_fft_schedule(p1, qp.QP_FP32)
     p2 = qp.plan_from_instance(inst, max_rhs=2)        # same geometry: the cached choice, not re-timed
     s2 = qp.qp_fft_schedule(p2, qp.QP_FP32)
-    assert s2["index"] == s1["index"] and s2["ms"] == -1.0
+    assert s2["index"] == s1["index"] and s2["ms"] == s1["ms"]   # the first plan's timing, carried by the cache
     qp.qp_set_fft_autotune(False)
     try:
         other = W.random_instance(2, 4, (8, 6, 4, 4), "sym", "grid", seed=62, nonlinear=True)
