@@ -283,6 +283,15 @@ uint64_t qp_launch_count(void);
  * index (0 .. count - 1) from now on. Both return QP_ERR_UNSUPPORTED for a taps-backend plan. With the autotuner off,
  * QP_BACKEND_AUTO also stops timing the stencil against the FFT backend for tap coefficients (taps are kept). */
 qp_status qp_set_fft_autotune(int enabled);
+/* The autotuner's process-wide cache of FFT schedules (chosen candidate and every candidate's timing per geometry,
+ * coefficient kind, max_rhs and precision) to and from a text file, so that a later process on the same kind of GPU
+ * reuses the choices instead of timing again: save writes every entry (entries: how many; QP_ERR_INVALID_ARG when
+ * the file cannot be written); load merges the file's entries into the cache (QP_ERR_INVALID_ARG for an unreadable
+ * or malformed file, QP_ERR_UNSUPPORTED when it was written on another GPU model; nothing is merged then). A loaded
+ * entry applies to later plans of its shape whose candidate list has the same length. clear empties the cache. */
+qp_status qp_fft_tune_cache_save(const char* path, int* entries);
+qp_status qp_fft_tune_cache_load(const char* path, int* entries);
+qp_status qp_fft_tune_cache_clear(void);
 qp_status qp_fft_schedule(const qp_plan* plan, int precision, int* index, int* count, double* ms, char* text,
                           int text_len);
 qp_status qp_fft_set_schedule(qp_plan* plan, int precision, int index);

@@ -40,7 +40,8 @@ EXPORTS = ("qp_plan_create", "qp_plan_destroy", "qp_plan_query", "qp_apply_stiff
            "qp_batch_homogenized", "qp_batch_destroy", "qp_last_error", "qp_launch_count",
            "qp_pcg_solve_taps_static", "qp_set_barrier_timeout", "qp_l2qp_error", "qp_plan_diagonal",
            "qp_set_fft_autotune", "qp_fft_schedule", "qp_fft_set_schedule", "qp_memory_pool_stats",
-           "qp_set_memory_cache", "qp_set_phase_timing", "qp_phase_times")
+           "qp_set_memory_cache", "qp_set_phase_timing", "qp_phase_times", "qp_fft_tune_cache_save",
+           "qp_fft_tune_cache_load", "qp_fft_tune_cache_clear")
 PHASES = ("apply32", "update32", "hupdate32", "init32", "refine", "apply64", "update64", "hupdate64", "init64",
           "residual64", "other")
 
@@ -106,6 +107,9 @@ def load_library(path: str = LIB_PATH):
         "qp_l2qp_error": [vp, i, vp, vp, dp, vp],
         "qp_plan_diagonal": [vp, i, vp, vp],
         "qp_set_fft_autotune": [i],
+        "qp_fft_tune_cache_save": [C.c_char_p, C.POINTER(C.c_int)],
+        "qp_fft_tune_cache_load": [C.c_char_p, C.POINTER(C.c_int)],
+        "qp_fft_tune_cache_clear": [],
         "qp_fft_schedule": [vp, i, ip, ip, dp, C.c_char_p, i],
         "qp_fft_set_schedule": [vp, i, i],
         "qp_memory_pool_stats": [C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_uint64)],
@@ -397,6 +401,25 @@ def qp_fft_schedule(plan: Plan, precision=QP_FP32) -> dict:
     buf = C.create_string_buffer(256)
     _check(_lib.qp_fft_schedule(plan.handle, int(precision), C.byref(idx), C.byref(cnt), C.byref(ms), buf, 256))
     return {"index": idx.value, "count": cnt.value, "ms": ms.value, "text": buf.value.decode()}
+
+
+def qp_fft_tune_cache_save(path: str) -> int:
+    """Writes the autotuner's schedule cache to a text file; returns the entries written."""
+    n = C.c_int(0)
+    _check(_lib.qp_fft_tune_cache_save(str(path).encode(), C.byref(n)))
+    return n.value
+
+
+def qp_fft_tune_cache_load(path: str) -> int:
+    """Merges a schedule cache file (written on the same GPU model) into the process's cache; returns its entries."""
+    n = C.c_int(0)
+    _check(_lib.qp_fft_tune_cache_load(str(path).encode(), C.byref(n)))
+    return n.value
+
+
+def qp_fft_tune_cache_clear() -> None:
+    """Empties the autotuner's schedule cache (later plans are timed again, or take the heuristic when off)."""
+    _check(_lib.qp_fft_tune_cache_clear())
 
 
 def qp_fft_set_schedule(plan: Plan, precision, index: int) -> None:

@@ -1156,6 +1156,31 @@ qp_status qp_l2qp_error(qp_plan* p, int nrhs, const void* U, const void* Uref, d
   API_END
 }
 
+qp_status qp_fft_tune_cache_save(const char* path, int* entries) {
+  API_BEGIN
+  if (!path) raise(QP_ERR_INVALID_ARG, "path must be non-null");
+  const int n = fft_tune_cache_save(path);
+  if (n < 0) raise(QP_ERR_INVALID_ARG, std::string("cannot write the tuning cache to ") + path);
+  if (entries) *entries = n;
+  API_END
+}
+
+qp_status qp_fft_tune_cache_load(const char* path, int* entries) {
+  API_BEGIN
+  if (!path) raise(QP_ERR_INVALID_ARG, "path must be non-null");
+  const int n = fft_tune_cache_load(path);
+  if (n == -2) raise(QP_ERR_UNSUPPORTED, std::string("the tuning cache ") + path + " was timed on another GPU");
+  if (n < 0) raise(QP_ERR_INVALID_ARG, std::string("cannot read a tuning cache from ") + path);
+  if (entries) *entries = n;
+  API_END
+}
+
+qp_status qp_fft_tune_cache_clear(void) {
+  API_BEGIN
+  fft_tune_cache_clear();
+  API_END
+}
+
 qp_status qp_set_fft_autotune(int enabled) {
   API_BEGIN
   fft_set_autotune(enabled != 0);

@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -1562,6 +1563,75 @@ static void tune_precision(FftPlan* f, const PlanDev& pd, const PlanDev* pdp, cu
   use = ss.cand[best];
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune_cache[key] = {best, ss.ms};
+}
+
+// The tuning cache in a text file, for later processes on the same kind of GPU: a header line with the format
+// version and the device name, then one line per entry: key, chosen candidate, candidate count, their timings.
+static std::string device_name() {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  cudaDeviceProp prop;
+  CK(cudaGetDeviceProperties(&prop, dev));
+  std::string name = prop.name;
+  for (char& c : name)
+    if (c == ' ' || c == '\t' || c == '\n') c = '_';
+  return name;
+}
+
+int fft_tune_cache_save(const char* path) {
+  const std::string dev = device_name();
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  FILE* fp = std::fopen(path, "w");
+  if (!fp) return -1;
+  std::fprintf(fp, "qp-fft-tune-cache 1 %s\n", dev.c_str());
+  int n = 0;
+  for (const auto& kv : g_tune_cache) {
+    std::fprintf(fp, "%s %d %zu", kv.first.c_str(), kv.second.first, kv.second.second.size());
+    for (float ms : kv.second.second) std::fprintf(fp, " %.9g", (double)ms);
+    std::fprintf(fp, "\n");
+    ++n;
+  }
+  const bool ok = std::fclose(fp) == 0;
+  return ok ? n : -1;
+}
+
+int fft_tune_cache_load(const char* path) {
+  const std::string dev = device_name();
+  FILE* fp = std::fopen(path, "r");
+  if (!fp) return -1;
+  std::vector<std::pair<std::string, std::pair<int, std::vector<float>>>> entries;
+  char head[64] = {}, name[256] = {};
+  int version = 0;
+  bool ok = std::fscanf(fp, "%63s %d %255s", head, &version, name) == 3 && std::string(head) == "qp-fft-tune-cache" &&
+            version == 1;
+  if (ok && dev != name) {
+    std::fclose(fp);
+    return -2;   // timed on another kind of GPU
+  }
+  while (ok) {
+    char key[256] = {};
+    int chosen = 0;
+    unsigned long cnt = 0;
+    const int got = std::fscanf(fp, "%255s %d %lu", key, &chosen, &cnt);
+    if (got == EOF) break;
+    if (got != 3 || cnt > 100000 || chosen < 0 || (unsigned long)chosen >= cnt) {
+      ok = false;
+      break;
+    }
+    std::vector<float> ms(cnt);
+    for (unsigned long i = 0; ok && i < cnt; ++i) ok = std::fscanf(fp, "%f", &ms[i]) == 1;
+    if (ok) entries.push_back({key, {chosen, ms}});
+  }
+  std::fclose(fp);
+  if (!ok) return -1;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (auto& e : entries) g_tune_cache[e.first] = e.second;
+  return (int)entries.size();
+}
+
+void fft_tune_cache_clear() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache.clear();
 }
 
 void fft_autotune(FftPlan* f, const PlanDev& pd, const PlanDev* pdp, cudaStream_t s) {

@@ -32,6 +32,11 @@ void fft_apply(FftPlan* f, const PlanDev& pd, const PlanDev* pdp, const cplx<T>*
 // (fft_set_autotune(false)): the balanced-split heuristic.
 void fft_autotune(FftPlan* f, const PlanDev& pd, const PlanDev* pdp, cudaStream_t s);
 void fft_set_autotune(bool on);
+// The process's tuning cache to and from a text file (entries written / loaded; -1: I/O or format error; load: -2
+// when the file was written on another kind of GPU), and its clearing.
+int fft_tune_cache_save(const char* path);
+int fft_tune_cache_load(const char* path);
+void fft_tune_cache_clear();
 bool fft_autotune_on();
 int fft_schedule_count(const FftPlan* f, bool fp64);
 // the schedule in use: its candidate index (-1: the heuristic's, untimed), description and timed ms per apply

@@ -104,3 +104,34 @@ def test_auto_backend_takes_the_fft_for_a_dense_tap_list(qp):
 def test_auto_backend_keeps_the_stencil_for_few_taps(qp):
     for inst in (W.cfg1(), W.random_instance(2, 4, (16, 16, 16, 16), "sym", "taps", seed=72, nmodes=20)):
         assert qp.qp_plan_query(qp.plan_from_instance(inst))["backend"] == "taps"
+
+
+def test_tuning_cache_file_round_trip(qp, tmp_path):
+    """The schedule cache saved to a file and loaded by a later plan's process state: with the autotuner off and
+    the in-memory cache cleared, a plan takes the heuristic (index -1); after loading the file it takes the timed
+    choice with its timing. A malformed file is rejected and merges nothing."""
+    inst = W.random_instance(2, 4, (6, 8, 4, 6), "diag", "grid", seed=62, nonlinear=True)
+    p1 = qp.plan_from_instance(inst, max_rhs=2)
+    s1 = qp.qp_fft_schedule(p1, qp.QP_FP32)
+    path = tmp_path / "fft_tune.txt"
+    assert qp.qp_fft_tune_cache_save(str(path)) >= 1
+    assert path.read_text().startswith("qp-fft-tune-cache 1 ")
+    bad = tmp_path / "bad.txt"
+    bad.write_text("not a cache\n")
+    try:
+        qp.qp_fft_tune_cache_clear()
+        qp.qp_set_fft_autotune(False)
+        p2 = qp.plan_from_instance(inst, max_rhs=2)
+        assert qp.qp_fft_schedule(p2, qp.QP_FP32)["index"] == -1
+        with pytest.raises(qp.QPError) as ei:
+            qp.qp_fft_tune_cache_load(str(bad))
+        assert ei.value.status == qp.QP_ERR_INVALID_ARG
+        assert qp.qp_fft_tune_cache_load(str(path)) >= 1
+        p3 = qp.plan_from_instance(inst, max_rhs=2)
+        s3 = qp.qp_fft_schedule(p3, qp.QP_FP32)
+        assert s3["index"] == s1["index"] and s3["ms"] == pytest.approx(s1["ms"], rel=1e-6)
+        for p in (p2, p3):
+            qp.qp_plan_destroy(p)
+    finally:
+        qp.qp_set_fft_autotune(True)
+    qp.qp_plan_destroy(p1)
