@@ -268,7 +268,7 @@ const char* qp_last_error(void);
 /* Number of CUDA kernels this library has launched in this process so far (all threads, all plans). */
 uint64_t qp_launch_count(void);
 
-/* FFT-backend apply schedules (the spec autotuner; not in the paper, which has no FFT backend on a GPU).
+/* FFT-backend apply schedules (an autotuner of this library; not in the paper, which has no FFT backend on a GPU).
  * The apply runs its n-dim transforms as passes over groups of consecutive axes staged in shared-memory tiles.
  * At plan creation every feasible schedule (one group, every split into two or three groups, each at tile
  * budgets of 48, 100 and 200 KB) and the per-axis path are timed on this GPU (CUDA events on the plan's
