@@ -66,6 +66,11 @@ def test_apply_full_size_sampled_cfg4(qp):
         got = w[r].cpu().numpy().astype(np.complex128)[flat]
         scale = np.abs(ref).max()
         assert np.abs(got - ref).max() <= 2e-6 * scale
+    # two right-hand sides take the run-time-geometry kernel (its grid of resident blocks walks 54 segments per
+    # block here): bit for bit the compiled-in geometry's values
+    w2 = torch.empty((2, D), dtype=torch.complex64, device="cuda")
+    qp.qp_apply_stiffness(plan, h[:2].contiguous(), w2, qp.QP_FP32, nrhs=2)
+    assert torch.equal(w2, w[:2])
 
 
 def test_refinement_solve_of_a_unit_in_two_waves(qp):
