@@ -13,7 +13,7 @@ namespace qp {
 // SK: the stencil's data source: 0 the plan in shared memory (apply_run), 1 / 2 the star-1 stencil of a scalar /
 // diagonal coefficient from st (a kernel parameter).
 template <typename T, int EPI, bool REALC, int NR, int RUN, int NV, int SK = 0, int NAX = 0, int DC = 0,
-          bool HSP = false>
+          bool HSP = false, int NG = 0>
 __device__ __forceinline__ void apply_chunk(const PlanDev& sp, const cplx<T>* scoef, const StarParams& st,
                                             const UnitDev& un, int cl, int D, int nrhs, int refine, bool fft_unit,
                                             const cplx<T>* src, cplx<T>* dst, const cplx<T>* F, T (&vt)[NV]) {
@@ -38,7 +38,7 @@ __device__ __forceinline__ void apply_chunk(const PlanDev& sp, const cplx<T>* sc
       // FP64: the plan's stored weights; FP32: formed
       apply_run_star<T, REALC, NR, true, SK == 2, sizeof(T) == 8 ? 1 : 0, NAX, DC, HSP>(st, e0, src, D, nrhs, acc);
     } else {
-      apply_run<T, REALC, NR, RUN>(sp, scoef, e0, src, D, nrhs, acc);
+      apply_run<T, REALC, NR, RUN, true, true, 0, NG>(sp, scoef, e0, src, D, nrhs, acc);
     }
     if constexpr (RUN == 2 && sizeof(T) == 4 && EPI != EPI_RESIDUAL) {
       // FP32 runs of two: one 16-byte store (and load of h) per right-hand side; the sums in the order below
@@ -283,10 +283,19 @@ __device__ __forceinline__ void apply_units(const BatchDev& b, int level, int re
       apply_chunk<T, EPI, REALC, NR, 2, NV, SK, NAX, DC, HSP>(sp, scoef, stp, un, cl, D, nrhs, refine, fft_unit, src,
                                                              dst, F, vt);
     } else {
-      if (un.run == 2)
-        apply_chunk<T, EPI, REALC, NR, 2, NV>(sp, scoef, stp, un, cl, D, nrhs, refine, fft_unit, src, dst, F, vt);
-      else
+      // the common axis counts compiled in (the same arithmetic; fewer per-axis tests)
+      if (un.run == 2) {
+        if (sp.n == 2)
+          apply_chunk<T, EPI, REALC, NR, 2, NV, 0, 0, 0, false, 2>(sp, scoef, stp, un, cl, D, nrhs, refine, fft_unit,
+                                                                  src, dst, F, vt);
+        else if (sp.n == 4)
+          apply_chunk<T, EPI, REALC, NR, 2, NV, 0, 0, 0, false, 4>(sp, scoef, stp, un, cl, D, nrhs, refine, fft_unit,
+                                                                  src, dst, F, vt);
+        else
+          apply_chunk<T, EPI, REALC, NR, 2, NV>(sp, scoef, stp, un, cl, D, nrhs, refine, fft_unit, src, dst, F, vt);
+      } else {
         apply_chunk<T, EPI, REALC, NR, 1, NV>(sp, scoef, stp, un, cl, D, nrhs, refine, fft_unit, src, dst, F, vt);
+      }
     }
     if (EPI == EPI_NONE) continue;
     block_reduce_mixed<T, NV>(vt, v);

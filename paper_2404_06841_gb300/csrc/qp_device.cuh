@@ -86,11 +86,13 @@ __device__ __forceinline__ uint32_t fdiv(uint32_t x, const FastDiv& f) {
 
 // Storage digits ibar_j of linear index e (last axis fastest) and the signed modes k_j. (A half-spectrum plan's
 // last-axis digit is k_{n-1} itself: 0 <= ibar < ceil(N/2), so the signed rule returns it unchanged.)
+// NG: the number of axes when the caller compiles it in (0: the plan's, at run time).
+template <int NG = 0>
 __device__ __forceinline__ void mode_digits(const PlanDev& p, int e, int (&ib)[MAXN], int (&k)[MAXN]) {
   uint32_t x = (uint32_t)e;
 #pragma unroll
   for (int j = MAXN - 1; j >= 0; --j) {
-    if (j < p.n) {
+    if (j < (NG ? NG : p.n)) {
       const uint32_t q = fdiv(x, p.div[j]);
       ib[j] = (int)(x - q * (uint32_t)p.Nst[j]);
       k[j] = (2 * ib[j] < p.N[j]) ? ib[j] : ib[j] - p.N[j];

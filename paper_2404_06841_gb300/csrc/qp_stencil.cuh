@@ -696,7 +696,9 @@ __device__ __forceinline__ void wgen_store(void* out, int t, int e, int D, doubl
 // WM (general taps; T = double): 0 the weights are formed; 1 they are read from p.wgen (chosen at run time when the
 // plan stores them); 2 they are formed and written to wout, nothing else is done (the stencil's own arithmetic, so
 // stored and formed weights agree bit for bit).
-template <typename T, bool REALC, int NR, int RUN, bool RO = true, bool STAR = true, int WM = 0>
+// NG: the plan's number of axes compiled in (the batch kernels dispatch the common ones; 0: read at run time). The
+// per-axis loops then stop at the plan's axes instead of testing every axis up to MAXN; the arithmetic is the same.
+template <typename T, bool REALC, int NR, int RUN, bool RO = true, bool STAR = true, int WM = 0, int NG = 0>
 __device__ __forceinline__ void apply_run(const PlanDev& p, const cplx<T>* __restrict__ sc, int e0,
                                           const cplx<T>* h, int D, int nrhs, cplx<T> (&acc)[RUN][NR],
                                           void* wout = nullptr) {
@@ -712,7 +714,7 @@ __device__ __forceinline__ void apply_run(const PlanDev& p, const cplx<T>* __res
   }
   if constexpr (sizeof(T) == 8 && WM == 0) {
     if (p.wgen) {
-      apply_run<T, REALC, NR, RUN, RO, STAR, 1>(p, sc, e0, h, D, nrhs, acc);
+      apply_run<T, REALC, NR, RUN, RO, STAR, 1, NG>(p, sc, e0, h, D, nrhs, acc);
       return;
     }
   }
@@ -727,8 +729,8 @@ __device__ __forceinline__ void apply_run(const PlanDev& p, const cplx<T>* __res
     }
   };
   int ib[MAXN], k[MAXN];
-  mode_digits(p, e0, ib, k);
-  const int d = p.d, kind = p.kind, nc = p.ncomp, n = p.n;
+  mode_digits<NG>(p, e0, ib, k);
+  const int d = p.d, kind = p.kind, nc = p.ncomp, n = NG ? NG : p.n;
   const int jl = n - 1, Nl = p.N[jl];
   const int ibl = e0 - (int)fdiv((uint32_t)e0, p.div[jl]) * Nl;   // digit of the last axis (kept in registers)
   const bool scalar = (kind == QP_COEF_SCALAR);
