@@ -121,10 +121,13 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_init(BatchDev b, int level, int w
 }
 
 // alpha step on the residual, and the reductions for beta and the convergence test (U is updated by
-// k_pcg_hupdate, which reads h anyway).
+// k_pcg_hupdate, which reads h anyway). The chunks go in descending order: the apply before it ends its sweep at the
+// top of the vectors, whose Q h is then still in L2, and the h-update after it starts at the bottom, where this
+// pass has just written r (a chunk's partial sums do not depend on the order).
 template <typename T, int NR, bool HW>
 __global__ void __launch_bounds__(BLOCK) k_pcg_update(BatchDev b, int level, unsigned long long cond) {
-  for (int c = blockIdx.x; c < b.nchunks; c += gridDim.x) {
+  for (int ci = blockIdx.x; ci < b.nchunks; ci += gridDim.x) {
+    const int c = b.nchunks - 1 - ci;
     const int u = unit_of_chunk(b, c);
     const UnitDev& un = unit_at(b, u);
     RhsSt* st = b.st + (size_t)u * MAXR;
