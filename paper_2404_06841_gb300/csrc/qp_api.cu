@@ -877,6 +877,12 @@ Entry& get_entry(Solver* sv, const Units& us, const Key& key, cudaStream_t s) {
   bd.nslots = nslots;
   bd.units = (const UnitDev*)up(units.data(), units.size() * sizeof(UnitDev));
   bd.single = nu == 1 ? 1 : 0;
+  {
+    // the FP32 apply of a single star-1 unit (even last axis) sweeps upwards, the general batch kernel downwards
+    const qp_plan* p0 = nu == 1 ? us.plans[0] : nullptr;
+    const bool star = p0 && p0->backend == QP_BACKEND_TAPS && p0->host_pd.star1 && last_axis_run(p0) == 2;
+    bd.apply_down = star ? 0 : 1;
+  }
   bd.hspec_any = 0;
   for (const UnitDev& x : units) bd.hspec_any |= x.hspec;
   bd.pu = units[0];

@@ -239,7 +239,10 @@ __device__ __forceinline__ void apply_units(const BatchDev& b, int level, int re
   extern __shared__ __align__(16) unsigned char smraw[];
   cplx<T>* scoef = reinterpret_cast<cplx<T>*>(smraw);
   const PlanDev* cur = nullptr;
-  for (int c = blockIdx.x; c < b.nchunks; c += gridDim.x) {
+  // chunks in descending order: the batch's last units first (a batch lists its plans in order, and the large units
+  // that come last then do not form the tail of the launch); a chunk's sums do not depend on the order
+  for (int ci = blockIdx.x; ci < b.nchunks; ci += gridDim.x) {
+    const int c = b.nchunks - 1 - ci;
     // a star-1 kernel runs a batch of one unit: its description straight from the kernel parameter
     const int u = SK != 0 ? 0 : unit_of_chunk(b, c);
     const UnitDev& un = SK != 0 ? b.pu : unit_at(b, u);

@@ -280,7 +280,8 @@ struct RhsSt {
 
 struct BatchDev {
   int nunits, nchunks, nslots, hspec_any;   // hspec_any: some unit has half-spectrum storage
-  int single, pad_[3];                  // single: one unit, whose description is "pu" (kernel parameter)
+  int single, apply_down, pad_[2];      // single: one unit, whose description is "pu" (kernel parameter);
+                                        // apply_down: the batch's apply walks its chunks downwards (general kernel)
   UnitDev pu;
   const UnitDev* units;
   RhsSt* st;                            // [nunits * MAXR]

@@ -121,13 +121,13 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_init(BatchDev b, int level, int w
 }
 
 // alpha step on the residual, and the reductions for beta and the convergence test (U is updated by
-// k_pcg_hupdate, which reads h anyway). The chunks go in descending order: the apply before it ends its sweep at the
-// top of the vectors, whose Q h is then still in L2, and the h-update after it starts at the bottom, where this
-// pass has just written r (a chunk's partial sums do not depend on the order).
+// k_pcg_hupdate, which reads h anyway). The chunks go against the apply's direction (downwards after the single
+// star-1 apply, upwards after the general batch apply): the pass starts where the apply ended, whose Q h is then
+// still in L2 (a chunk's partial sums do not depend on the order).
 template <typename T, int NR, bool HW>
 __global__ void __launch_bounds__(BLOCK) k_pcg_update(BatchDev b, int level, unsigned long long cond) {
   for (int ci = blockIdx.x; ci < b.nchunks; ci += gridDim.x) {
-    const int c = b.nchunks - 1 - ci;
+    const int c = b.apply_down ? ci : b.nchunks - 1 - ci;
     const int u = unit_of_chunk(b, c);
     const UnitDev& un = unit_at(b, u);
     RhsSt* st = b.st + (size_t)u * MAXR;
@@ -189,10 +189,12 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_update(BatchDev b, int level, uns
 
 // U += alpha h for the right-hand sides active in this iteration (those that converged in it included), then
 // h = M r + beta h for those still running. The last block of a unit clears the pending U updates of its
-// converged right-hand sides.
+// converged right-hand sides. The chunks go in the apply's direction, against the update pass before it, so that
+// this pass starts where the update ended (its r still in L2).
 template <typename T, int NR>
 __global__ void __launch_bounds__(BLOCK) k_pcg_hupdate(BatchDev b, int level) {
-  for (int c = blockIdx.x; c < b.nchunks; c += gridDim.x) {
+  for (int ci = blockIdx.x; ci < b.nchunks; ci += gridDim.x) {
+    const int c = b.apply_down ? b.nchunks - 1 - ci : ci;
     const int u = unit_of_chunk(b, c);
     const UnitDev& un = unit_at(b, u);
     RhsSt* st = b.st + (size_t)u * MAXR;
