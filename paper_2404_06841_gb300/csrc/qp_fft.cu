@@ -386,7 +386,7 @@ struct GroupPass {
   int ng, j0;               // axes j0 .. j0 + ng - 1
   int Ng[MAXN], sg[MAXN];   // their sizes; stride of each in the group position (product of later group axes)
   int nhi[MAXN];            // M / (Ng * sg): group positions above each axis
-  FastDiv fR, fM;           // tile element -> (l, pos, r)
+  FastDiv fR;               // tile element -> (l M + pos, r)
   FastDiv fsg[MAXN], fnhi[MAXN];
   int M, I, L, R, TS, ntile;
   long long O;
@@ -1052,17 +1052,18 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 8 ? 1 : 2) k_fft_group(con
   const int to = blockIdx.x / gp.tiles_i, ti = blockIdx.x - to * gp.tiles_i;
   const int base_o = to * gp.L, i0 = ti * gp.R;
   const int y = blockIdx.y;
-  // linear index in the array of tile element idx
+  // linear index in the array of tile element idx = (l M + pos) R + r: ((base_o + l) M + pos) I + i0 + r, where
+  // l M + pos is idx / R itself
   auto lin = [&](int idx) -> int {
     const int q = fdivi(idx, gp.fR);
     const int r = idx - q * gp.R;
-    const int l = fdivi(q, gp.fM);
-    const int pos = q - l * gp.M;
-    return ((base_o + l) * gp.M + pos) * gp.I + i0 + r;
+    return (base_o * gp.M + q) * gp.I + i0 + r;
   };
-  // the index of this thread's u-th element (idx = threadIdx.x + u BLOCK)
-  const int lin0 = lin(threadIdx.x);
-  auto lin_u = [&](int u, int idx) -> int { return gp.aff ? lin0 + u * gp.dlin : lin(idx); };
+  // the index of this thread's u-th element (idx = threadIdx.x + u BLOCK); the one-group pass keeps the division
+  // (its registers are taken by the whole transform)
+  constexpr bool WALK = MODE != GP_SINGLE;
+  const int lin0 = WALK ? lin(threadIdx.x) : 0;
+  auto lin_u = [&](int u, int idx) -> int { return (WALK && gp.aff) ? lin0 + u * gp.dlin : lin(idx); };
   const int ntile = (MODE == GP_PLAIN) ? 1 : d;
 
   // ---- load the tiles: lambda_b h (gradient) or the stored fields, GP_BATCH loads in flight per thread
@@ -1247,26 +1248,16 @@ static bool make_pass(const PlanDev& pd, int j0, int ng, int mode, int sign, int
   }
   gp.TS = gp.L * gp.M * gp.R;
   gp.fR = make_fastdiv((uint32_t)gp.R);
-  gp.fM = make_fastdiv((uint32_t)gp.M);
   for (int t = 0; t < ng; ++t) {
     gp.fsg[t] = make_fastdiv((uint32_t)gp.sg[t]);
     gp.fnhi[t] = make_fastdiv((uint32_t)gp.nhi[t]);
   }
   gp.tiles_i = (int)(I / gp.R);
   gp.tiles_o = (int)(O / gp.L);
-  {
-    // affine walk of a thread's tile elements: checked for every element of a tile (the tile's offsets add
-    // a constant, so one tile decides)
-    auto lin = [&](long long idx) {
-      const long long q = idx / gp.R, r = idx % gp.R, l = q / gp.M, pos = q % gp.M;
-      return (l * gp.M + pos) * (long long)gp.I + r;
-    };
-    gp.aff = gp.TS > BLOCK ? 1 : 0;
-    const long long dl = gp.TS > BLOCK ? lin(BLOCK) - lin(0) : 0;
-    for (long long idx = 0; gp.aff && idx + BLOCK < gp.TS; ++idx)
-      if (lin(idx + BLOCK) - lin(idx) != dl) gp.aff = 0;
-    gp.dlin = gp.aff ? (int)dl : 0;
-  }
+  // the array index of tile element idx is (idx / R) I + idx % R plus the tile's offset, so a step of BLOCK
+  // elements is a constant (BLOCK / R) I whenever R divides BLOCK
+  gp.aff = (gp.TS > BLOCK && BLOCK % gp.R == 0) ? 1 : 0;
+  gp.dlin = gp.aff ? (BLOCK / gp.R) * gp.I : 0;
   gp.smem = (size_t)((gp.TS - 1) + ((gp.TS - 1) >> 5) + 1) * esize * gp.ntile;
   return (long long)gp.tiles_o * gp.tiles_i < (1ll << 31);
 }
