@@ -131,7 +131,12 @@ def test_fixed_geometry_plain_apply_is_the_general_one(qp, d, n, N, kind, real):
                                              (2, 4, (4, 6, 5, 4), "scalar", False),
                                              # 32^4: 1,024 chunks, so the FP32 batch kernel with the geometry
                                              # compiled in walks several chunks per block (grid of resident blocks)
-                                             (2, 4, (32, 32, 32, 32), "diag", False)])
+                                             (2, 4, (32, 32, 32, 32), "diag", False),
+                                             # six axes and more chunks than resident blocks: the FP32 batch kernel
+                                             # with the geometry compiled in walks chunks of contiguous runs (1,024
+                                             # chunks of 1,024 modes) and sweep waves (1,152 chunks of 2,048 modes)
+                                             (3, 6, (8, 8, 8, 8, 8, 32), "diag", False),
+                                             (3, 6, (8, 8, 8, 8, 8, 72), "diag", True)])
 def test_fixed_geometry_solves_are_the_general_ones(qp, d, n, N, kind, real):
     """Every axis with taps and d right-hand sides: the persistent solve and the graph form's FP32 batch apply take
     the kernels with the geometry compiled in; with d + 1 right-hand sides the general ones run. Each right-hand
