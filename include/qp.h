@@ -252,7 +252,7 @@ qp_status qp_set_memory_cache(int64_t bytes);
  *   QP_PHASE_HUPDATE32 / HUPDATE64: the new search direction h = M r + beta h (and the U update);
  *   QP_PHASE_INIT32 / INIT64: the PCG initialisation of a (inner) solve;
  *   QP_PHASE_RESIDUAL64: FP64 applies of U (true residuals, warm starts);
- *   QP_PHASE_REFINE: the refinement steps (scaled FP32 right-hand side, U += c / scale);
+ *   QP_PHASE_REFINE: the refinement steps (FP32 right-hand side 2^-e r with 2^e <= ||r|| < 2^(e+1), U += 2^e c);
  *   QP_PHASE_OTHER: zeroing and state resets.
  * qp_set_phase_timing(enabled) also clears the totals. qp_phase_times: for phases 0 .. count - 1 the summed
  * milliseconds (ms) and the number of timed groups (launches); either output may be NULL. Process-wide. */

@@ -129,8 +129,7 @@ __device__ __noinline__ void unit_finalize(const BatchDev& b, const UnitDev& un,
           od = 1;   // stagnation or cap
         }
         x.prev_rel = rel;
-        x.inv_scale = sqrt(s0);
-        x.scale = s0 > 0.0 ? 1.0 / x.inv_scale : 0.0;
+        refine_scale(s0, x.scale, x.inv_scale);
         x.ostatus = os;
         if (od) {
           x.odone = 1;

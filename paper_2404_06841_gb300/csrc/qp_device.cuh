@@ -4,6 +4,7 @@
 
 #include <cfloat>
 
+#include "qp_convert.cuh"
 #include "qp_internal.cuh"
 
 namespace qp {

@@ -230,7 +230,11 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_hupdate(BatchDev b, int level) {
   }
 }
 
-// Refinement: F32 = scale * (F - Q64 U64) for the right-hand sides still refining (scale = 1 / ||F - Q U||).
+// Elements a thread of the refinement passes has in flight: their loads are issued before any of their stores.
+constexpr int REFINE_ILP = 4;
+
+// Refinement: F32 = 2^-e (F - Q64 U64) for the right-hand sides still refining (2^e <= ||F - Q U|| < 2^(e+1), the
+// inverse of the right-hand side's scale): narrow_pow2, no FP64 arithmetic.
 __global__ void __launch_bounds__(BLOCK) k_refine_prep(BatchDev b) {
   for (int c = blockIdx.x; c < b.nchunks; c += gridDim.x) {
     const int u = unit_of_chunk(b, c);
@@ -240,17 +244,23 @@ __global__ void __launch_bounds__(BLOCK) k_refine_prep(BatchDev b) {
     const int base = (c - un.chunk0) * un.chunk, end = min(base + un.chunk, D);
     for (int k = 0; k < nrhs; ++k) {
       if (ld_int(&st[k].odone)) continue;
-      const double sc = __ldcg(&st[k].scale);
-      for (int e = base + threadIdx.x; e < end; e += BLOCK) {
-        const size_t o = (size_t)k * D + e;
-        const double2 v = un.w[o];
-        un.F32[o] = make_float2((float)(v.x * sc), (float)(v.y * sc));
+      const int ex = pow2_exponent(__ldcg(&st[k].inv_scale));
+      const double2* w = un.w + (size_t)k * D;
+      float2* f = un.F32 + (size_t)k * D;
+      for (int e0 = base + threadIdx.x; e0 < end; e0 += REFINE_ILP * BLOCK) {
+        double2 v[REFINE_ILP];
+#pragma unroll
+        for (int i = 0; i < REFINE_ILP; ++i)
+          if (e0 + i * BLOCK < end) v[i] = w[e0 + i * BLOCK];
+#pragma unroll
+        for (int i = 0; i < REFINE_ILP; ++i)
+          if (e0 + i * BLOCK < end) f[e0 + i * BLOCK] = make_float2(narrow_pow2(v[i].x, ex), narrow_pow2(v[i].y, ex));
       }
     }
   }
 }
 
-// Refinement: U64 += c32 / scale for the right-hand sides still refining.
+// Refinement: U64 += 2^e c32 for the right-hand sides still refining (widen_pow2: exact, one FP64 add per value).
 __global__ void __launch_bounds__(BLOCK) k_refine_accum(BatchDev b) {
   for (int c = blockIdx.x; c < b.nchunks; c += gridDim.x) {
     const int u = unit_of_chunk(b, c);
@@ -260,14 +270,27 @@ __global__ void __launch_bounds__(BLOCK) k_refine_accum(BatchDev b) {
     const int base = (c - un.chunk0) * un.chunk, end = min(base + un.chunk, D);
     for (int k = 0; k < nrhs; ++k) {
       if (ld_int(&st[k].odone)) continue;
-      const double inv = __ldcg(&st[k].inv_scale);
-      for (int e = base + threadIdx.x; e < end; e += BLOCK) {
-        const size_t o = (size_t)k * D + e;
-        const float2 cv = un.U32[o];
-        double2 uv = un.U[o];
-        uv.x = fma((double)cv.x, inv, uv.x);
-        uv.y = fma((double)cv.y, inv, uv.y);
-        un.U[o] = uv;
+      const int ex = pow2_exponent(__ldcg(&st[k].inv_scale));
+      const float2* c32 = un.U32 + (size_t)k * D;
+      double2* U = un.U + (size_t)k * D;
+      for (int e0 = base + threadIdx.x; e0 < end; e0 += REFINE_ILP * BLOCK) {
+        float2 cv[REFINE_ILP];
+        double2 uv[REFINE_ILP];
+#pragma unroll
+        for (int i = 0; i < REFINE_ILP; ++i) {
+          if (e0 + i * BLOCK < end) {
+            cv[i] = c32[e0 + i * BLOCK];
+            uv[i] = U[e0 + i * BLOCK];
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < REFINE_ILP; ++i) {
+          if (e0 + i * BLOCK < end) {
+            uv[i].x += widen_pow2(cv[i].x, ex);
+            uv[i].y += widen_pow2(cv[i].y, ex);
+            U[e0 + i * BLOCK] = uv[i];
+          }
+        }
       }
     }
   }

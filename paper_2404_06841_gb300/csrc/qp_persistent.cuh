@@ -457,8 +457,7 @@ __global__ void __launch_bounds__(BLOCK, NR >= 3 ? 1 : 2) k_pcg_persistent(const
             od = 1;   // stagnation or cap
           }
           x.prev_rel = rel;
-          x.inv_scale = sqrt(s0);
-          x.scale = s0 > 0.0 ? 1.0 / x.inv_scale : 0.0;
+          refine_scale(s0, x.scale, x.inv_scale);
           x.ostatus = os;
           if (od) x.odone = 1;
         }
@@ -469,17 +468,17 @@ __global__ void __launch_bounds__(BLOCK, NR >= 3 ? 1 : 2) k_pcg_persistent(const
       bool all = true;
       for (int k = 0; k < nrhs && k < NR; ++k) all = all && s_zero[k];
       if (all) break;
-      // F32 = r64 / |r64| for the right-hand sides still refining
+      // F32 = r64 2^-e (2^e <= |r64| < 2^(e+1)) for the right-hand sides still refining
       for (int c = blockIdx.x; c < b.nchunks; c += gridDim.x) {
         int base, end;
         chunk_range(un, c, base, end);
         for (int k = 0; k < nrhs; ++k) {
           if (s_zero[k]) continue;
-          const double sc = ls[k].scale;
+          const int ex = pow2_exponent(ls[k].inv_scale);
           for (int e = base + threadIdx.x; e < end; e += BLOCK) {
             const size_t o = (size_t)k * D + e;
             const double2 wv = un.w[o];
-            un.F32[o] = make_float2((float)(wv.x * sc), (float)(wv.y * sc));
+            un.F32[o] = make_float2(narrow_pow2(wv.x, ex), narrow_pow2(wv.y, ex));
           }
         }
       }
@@ -488,19 +487,19 @@ __global__ void __launch_bounds__(BLOCK, NR >= 3 ? 1 : 2) k_pcg_persistent(const
       __syncthreads();
       if (!(ok = pcg_solve_block<float, REALC, NR, SK, NAX, DC>(a, un, sp, sc32, false, true, ls, s_zero, b.tol2, b.maxit)))
         break;
-      // U64 += |r64| c32 for the right-hand sides still refining
+      // U64 += 2^e c32 for the right-hand sides still refining
       for (int c = blockIdx.x; c < b.nchunks; c += gridDim.x) {
         int base, end;
         chunk_range(un, c, base, end);
         for (int k = 0; k < nrhs; ++k) {
           if (s_zero[k]) continue;
-          const double inv = ls[k].inv_scale;
+          const int ex = pow2_exponent(ls[k].inv_scale);
           for (int e = base + threadIdx.x; e < end; e += BLOCK) {
             const size_t o = (size_t)k * D + e;
             const float2 cv = un.U32[o];
             double2 uv = un.U[o];
-            uv.x = fma((double)cv.x, inv, uv.x);
-            uv.y = fma((double)cv.y, inv, uv.y);
+            uv.x += widen_pow2(cv.x, ex);
+            uv.y += widen_pow2(cv.y, ex);
             un.U[o] = uv;
           }
         }
