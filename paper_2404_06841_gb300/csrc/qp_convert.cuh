@@ -11,8 +11,10 @@
 
 #ifdef __CUDACC__
 #define QP_HD __host__ __device__ __forceinline__
+#define QP_HD_COLD static __host__ __device__ __noinline__
 #else
 #define QP_HD inline
+#define QP_HD_COLD static __attribute__((noinline))
 #endif
 
 namespace qp {
@@ -75,6 +77,12 @@ QP_HD void refine_scale(double s0, double& scale, double& inv) {
   scale = pow2(-e);
 }
 
+// The FP64 expressions themselves, for the cases below that the bit manipulation leaves out: calls of their own,
+// so that the compiler keeps them behind a branch instead of evaluating them for every value (inlined, the
+// widening's FP64 multiply and conversion ran unconditionally and bound its pass again).
+QP_HD_COLD float narrow_pow2_slow(double x, int e) { return (float)(x * pow2(-e)); }
+QP_HD_COLD double widen_pow2_slow(float c, int e) { return (double)c * pow2(e); }
+
 // (float)(x 2^-e), round to nearest even. The 53-bit significand keeps its top 24 bits (hidden bit included); the
 // 29 bits below decide the rounding, with ties to the even neighbour.
 QP_HD float narrow_pow2(double x, int e) {
@@ -84,7 +92,7 @@ QP_HD float narrow_pow2(double x, int e) {
   const int ex = (int)((hi >> 20) & 0x7ffu);
   if (ex == 0 && (hi & 0xfffffu) == 0 && lo == 0) return f32_from(sign);   // signed zero
   const int fe = ex - 1023 - e + 127;                                      // the FP32 biased exponent
-  if (ex == 0 || ex == 0x7ff || fe < 1 || fe > 253) return (float)(x * pow2(-e));
+  if (ex == 0 || ex == 0x7ff || fe < 1 || fe > 253) return narrow_pow2_slow(x, e);
   uint32_t m = ((hi & 0xfffffu) << 3) | (lo >> 29);                      // 23 fraction bits
   const uint32_t rem = lo & 0x1fffffffu, half = 0x10000000u;
   uint32_t r = ((uint32_t)fe << 23) | m;
@@ -100,7 +108,7 @@ QP_HD double widen_pow2(float c, int e) {
   const uint32_t m = u & 0x7fffffu;
   if (fe == 0 && m == 0) return f64_from(sign);                             // signed zero
   const int de = fe - 127 + e + 1023;                                       // the FP64 biased exponent
-  if (fe == 0 || fe == 255 || de < 1 || de > 2046) return (double)c * pow2(e);
+  if (fe == 0 || fe == 255 || de < 1 || de > 2046) return widen_pow2_slow(c, e);
   return f64_from(sign | ((uint64_t)de << 52) | ((uint64_t)m << 29));
 }
 
