@@ -133,7 +133,7 @@ TRAFFIC = {
     # by 16^6 / 14^6
     ("k_apply_plain", "cfg4"): int((212182400 + 153766528) * (16 ** 6 / 14 ** 6)),
     # cfg2: the three fused passes of one FP32 apply (the gradient fields stay in L2 between passes)
-    ("k_fft_group", "cfg2"): 16939776 + 72192 + 46237696 + 0 + 33663232 + 6656,
+    ("k_fft_group", "cfg2"): 16941568 + 77568 + 46253824 + 0 + 33648384 + 256,
 }
 
 
