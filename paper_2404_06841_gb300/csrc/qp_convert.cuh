@@ -1,10 +1,10 @@
 // Conversions between the FP64 vectors of the refinement loop and its FP32 inner vectors, scaled by a power of two
 // 2^-e (the refinement's scale, near 1 / ||r||): with a power of two the scaling is exact, so the narrowing
 // (float)(x 2^-e) is one rounding and the widening (double)c 2^e is exact. Both are done on the bit patterns with
-// integer instructions (the FP64 pipe of a GB300 SM issues about two FP64 operations per clock, which bounded these
-// passes at 16^6, two multiplies and two conversions per element); the cases the bit manipulation does not cover
-// (FP64 subnormals, infinities and NaNs, exponents outside the normal range) take the FP64 expression, which gives
-// the same value.
+// integer instructions, because a GB300 SM issues only about two FP64 operations per clock: an FP64 multiply and an
+// FP64 conversion per value made the two refinement passes FP64-bound instead of bandwidth-bound. The cases the bit
+// manipulation does not cover (FP64 subnormals, infinities and NaNs, exponents outside the normal range) take the
+// FP64 expression, which gives the same value.
 #pragma once
 
 #include <cstdint>
