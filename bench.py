@@ -126,7 +126,7 @@ def fft_apply_bytes(d, ncomp, nrhs, D, es):
 TRAFFIC = {
     # cfg4: the FP32 (h, Q h) batch apply of the refinement solve (k_apply_star, geometry compiled in), captured at
     # N = 14 (7.53 M modes; h and w exceed L2), scaled by 16^6 / 14^6
-    ("apply32", "cfg4"): int((210870912 + 152987392) * (16 ** 6 / 14 ** 6)),
+    ("apply32", "cfg4"): int((211014912 + 153146624) * (16 ** 6 / 14 ** 6)),
     # cfg1: one solve (33 iterations, 2 correctors) in k_pcg_persistent; vectors and stored weights stay in L2
     ("k_pcg_persistent", "cfg1"): 9733376 + 243712,
     # cfg4: k_apply_plain_star (geometry compiled in) captured at N = 14 (7.53 M modes; h and w exceed L2), scaled
